@@ -1,0 +1,168 @@
+"""Python access to the FP64 CPU oracle (chem_oracle.c).
+
+TEST INFRASTRUCTURE: imported only by the tests, by the package smoke check and
+by the benchmark's CPU-baseline / reference leg.  The CUDA library never
+imports, links or calls it.  It computes the plain per-cell, per-reaction
+definition of the net production rates (Eqs. 1-3, 5, 7, 8, 10 and Sec. 2.4).
+
+Mechanisms are any object with the array attributes of
+``paper_2008_08483_gb300.synth.Mechanism``; only the data is shared.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "chem_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+R_CGS = 8.31446261815324e7
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (IEEE double, no contraction, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                        "-fno-fast-math", "-o", tmp, _SRC, "-lm", "-lpthread"], check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Mech(C.Structure):
+    _fields_ = [("ns", C.c_int), ("nr", C.c_int),
+                ("W", C.c_void_p), ("nu_f", C.c_void_p), ("nu_r", C.c_void_p),
+                ("arrh", C.c_void_p), ("kind", C.c_void_p), ("rev", C.c_void_p),
+                ("eff", C.c_void_p), ("arrh_low", C.c_void_p), ("troe", C.c_void_p),
+                ("nasa", C.c_void_p), ("t_mid", C.c_double), ("p_ref", C.c_double)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            P = C.c_void_p
+            lib.orc_thermo.argtypes = [P, C.c_double, P, P, P, P]
+            lib.orc_concentrations.argtypes = [P, C.c_double, C.c_double, P, P]
+            lib.orc_troe_F.argtypes = [P, C.c_double, C.c_double]
+            lib.orc_troe_F.restype = C.c_double
+            lib.orc_cell_detail.argtypes = [P, C.c_double, P, P, P, P, P, P, P, P, P, P]
+            for f in (lib.orc_source_term_tpy, lib.orc_source_term_tc):
+                f.restype = C.c_int
+            lib.orc_source_term_tpy.argtypes = [P, C.c_int64, P, P, P, C.c_int64, P, C.c_int64,
+                                                C.c_int]
+            lib.orc_source_term_tc.argtypes = [P, C.c_int64, P, P, C.c_int64, P, C.c_int64,
+                                               C.c_int]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class OracleMechanism:
+    """Holds contiguous copies of a mechanism's arrays and the C view of them."""
+
+    def __init__(self, mech):
+        self.ns = int(mech.nu_f.shape[1])
+        self.nr = int(mech.nu_f.shape[0])
+        self._keep = dict(
+            W=np.ascontiguousarray(mech.mol_weight, np.float64),
+            nu_f=np.ascontiguousarray(mech.nu_f, np.int32),
+            nu_r=np.ascontiguousarray(mech.nu_r, np.int32),
+            arrh=np.ascontiguousarray(mech.arrh, np.float64),
+            kind=np.ascontiguousarray(mech.kind, np.int32),
+            rev=np.ascontiguousarray(mech.reversible, np.int32),
+            eff=np.ascontiguousarray(mech.eff, np.float64),
+            arrh_low=np.ascontiguousarray(mech.arrh_low, np.float64),
+            troe=np.ascontiguousarray(mech.troe, np.float64),
+            nasa=np.ascontiguousarray(mech.nasa7, np.float64),
+        )
+        k = self._keep
+        self.c = _Mech(self.ns, self.nr, *(_ptr(k[n]).value for n in (
+            "W", "nu_f", "nu_r", "arrh", "kind", "rev", "eff", "arrh_low", "troe", "nasa")),
+            float(mech.t_mid), float(mech.p_ref))
+        self.ref = C.byref(self.c)
+
+
+def _om(mech):
+    return mech if isinstance(mech, OracleMechanism) else OracleMechanism(mech)
+
+
+def default_threads() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def thermo(mech, T: float):
+    """(cp/R, h/RT, s/R, g/RT) per species at temperature T (NASA-7, Eq. 10)."""
+    om = _om(mech)
+    out = [np.zeros(om.ns) for _ in range(4)]
+    _load().orc_thermo(om.ref, float(T), *(_ptr(a) for a in out))
+    return tuple(out)
+
+
+def concentrations(mech, T: float, P: float, Y) -> np.ndarray:
+    om = _om(mech)
+    Y = np.ascontiguousarray(Y, np.float64)
+    out = np.zeros(om.ns)
+    _load().orc_concentrations(om.ref, float(T), float(P), _ptr(Y), _ptr(out))
+    return out
+
+
+def troe_F(troe_params, T: float, Pr: float) -> float:
+    tp = np.ascontiguousarray(troe_params, np.float64)
+    return float(_load().orc_troe_F(_ptr(tp), float(T), float(Pr)))
+
+
+def cell_detail(mech, T: float, C_):
+    """Per-reaction intermediates for one cell at (T, C): dict of arrays."""
+    om = _om(mech)
+    Cc = np.ascontiguousarray(C_, np.float64)
+    names = ("lnkf", "lnKc", "M", "kf", "kr", "qf", "qr")
+    out = {n: np.zeros(om.nr) for n in names}
+    out["omega"] = np.zeros(om.ns)
+    g = np.zeros(om.ns)
+    _load().orc_cell_detail(om.ref, float(T), _ptr(Cc), _ptr(g),
+                            *(_ptr(out[n]) for n in names), _ptr(out["omega"]))
+    return out
+
+
+def source_term(mech, T, P, Y, nthreads: int | None = None) -> np.ndarray:
+    """omega [n, ns] (mol/(cm^3 s)) from T [n] (K), P [n] (dyn/cm^2), Y [n, ns]."""
+    om = _om(mech)
+    T = np.ascontiguousarray(T, np.float64)
+    P = np.ascontiguousarray(P, np.float64)
+    Y = np.ascontiguousarray(Y, np.float64)
+    n = T.shape[0]
+    out = np.zeros((n, om.ns))
+    rc = _load().orc_source_term_tpy(om.ref, n, _ptr(T), _ptr(P), _ptr(Y), Y.shape[1],
+                                     _ptr(out), om.ns, nthreads or default_threads())
+    if rc != 0:
+        raise RuntimeError("oracle source term failed")
+    return out
+
+
+def source_term_tc(mech, T, Cc, nthreads: int | None = None) -> np.ndarray:
+    """omega [n, ns] from T [n] and concentrations C [n, ns] (mol/cm^3)."""
+    om = _om(mech)
+    T = np.ascontiguousarray(T, np.float64)
+    Cc = np.ascontiguousarray(Cc, np.float64)
+    n = T.shape[0]
+    out = np.zeros((n, om.ns))
+    rc = _load().orc_source_term_tc(om.ref, n, _ptr(T), _ptr(Cc), Cc.shape[1], _ptr(out),
+                                    om.ns, nthreads or default_threads())
+    if rc != 0:
+        raise RuntimeError("oracle source term failed")
+    return out
