@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark of the batched chemical source term on one GB300 (or N replicas).
+
+One step = one evaluation of the whole source-term path (features, Arrhenius layer,
+folded Gibbs layer / ln K_c, third-body and falloff factors, both stoichiometric
+contractions, exp, omega) for 2^20 cells of the 53-species / 325-reaction synthetic
+GRI-size mechanism, inputs resident in HBM.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank evaluates its own 2^20 cells (weak scaling, no collective on
+the data path); the timing is the max over ranks.  `--impl reference` times the FP64
+CPU oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "source-term cells/s at 53sp/325rx, split-BF16 vs FP64 at stated err; p99 latency"
+UNIT = "cells/s"
+SIZE, MECH_SEED, STATE_SEED = "gri_53_325", 1, 1234
+N_CELLS = 1 << 20
+WORKLOAD = ("53 species / 325 reactions synthetic GRI-size mechanism (30 third-body, 25 Troe), "
+            "2^20 cells, T~U[800,2800] K, P~logU[1,50] atm, fuel/air/product mixtures")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"samples": 0, "note": "nvidia-smi unavailable"}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws, device):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_inputs(rank, n=N_CELLS):
+    from paper_2008_08483_gb300 import synth
+    mech = synth.make_mechanism(SIZE, seed=MECH_SEED)
+    T, P, Y = synth.make_states(mech, n, seed=STATE_SEED + rank)
+    return mech, T, P, Y
+
+
+def config(precision_name, n_cells, ws):
+    return {"workload": WORKLOAD, "mechanism": f"{SIZE} seed {MECH_SEED}", "n_species": 53,
+            "n_reactions": 325, "cells_per_gpu": n_cells, "precision": precision_name,
+            "state_seed": STATE_SEED, "parallelism": "replicas" if ws > 1 else "single GPU",
+            "l2_policy": "inputs larger than L2 (T, P, Y = 231 MB fp32 per step vs 129 MB L2)"}
+
+
+# ---------------------------------------------------------------------------------------
+# CPU oracle (the reference arm and the cpu_baseline leg)
+# ---------------------------------------------------------------------------------------
+
+def oracle_rate(mech, T, P, Y, budget_s=10.0, min_cells=2048):
+    """Time the FP64 oracle on the host cores on a bounded sample of the workload."""
+    from oracle import oracle as O
+    om = O.OracleMechanism(mech)
+    nth = O.default_threads()
+    done, t_used, chunk, outs, idxs = 0, 0.0, 2048, [], []
+    while (t_used < budget_s or done < min_cells) and done < len(T):
+        lo, hi = done, min(len(T), done + chunk)
+        t0 = time.perf_counter()
+        outs.append(O.source_term(om, T[lo:hi], P[lo:hi], Y[lo:hi], nthreads=nth))
+        t_used += time.perf_counter() - t0
+        idxs.append(np.arange(lo, hi))
+        done = hi
+        chunk = min(chunk * 2, 1 << 16)
+    return done / t_used, done, t_used, nth, np.concatenate(idxs), np.concatenate(outs)
+
+
+def run_reference(args):
+    ws, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return
+    mech, T, P, Y = make_inputs(0)
+    from oracle import oracle as O
+    om = O.OracleMechanism(mech)
+    nth = O.default_threads()
+    # calibrate so the whole run stays within about a minute
+    t0 = time.perf_counter()
+    O.source_term(om, T[:1024], P[:1024], Y[:1024], nthreads=nth)
+    rate = 1024 / max(time.perf_counter() - t0, 1e-6)
+    per_step = max(256, int(rate * 60.0 / max(1, args.steps + args.warmup)))
+    per_step = min(per_step, N_CELLS)
+    for w in range(args.warmup):
+        lo = (w * per_step) % (N_CELLS - per_step + 1)
+        O.source_term(om, T[lo:lo + per_step], P[lo:lo + per_step], Y[lo:lo + per_step], nthreads=nth)
+    times = []
+    for s in range(args.steps):
+        lo = ((s + args.warmup) * per_step) % (N_CELLS - per_step + 1)
+        t0 = time.perf_counter()
+        O.source_term(om, T[lo:lo + per_step], P[lo:lo + per_step], Y[lo:lo + per_step], nthreads=nth)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = per_step * args.steps / tot
+    sample = f"{per_step} cells of the 2^20-cell workload per step (contiguous slices)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config("fp64 CPU oracle", per_step, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nth, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------
+
+def time_device(fn, steps, warmup, stream, ws, device):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = e0.elapsed_time(e1)
+    return max_over_ranks(ms, ws, device) / steps
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "split_bf16", "fp32", "fp64"])
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--no-extras", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    from paper_2008_08483_gb300 import build as B
+    from paper_2008_08483_gb300 import chem
+
+    ws, rank, local = dist_setup()
+    B.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    mech, T, P, Y = make_inputs(rank)
+    h = chem.Mechanism(mech)
+    ns = mech.n_species
+    stream = torch.cuda.current_stream()
+
+    dev32 = [torch.as_tensor(a, dtype=torch.float32).to(dev) for a in (T, P, Y)]
+    out32 = torch.empty((N_CELLS, ns), dtype=torch.float32, device=dev)
+
+    # headline path: split BF16 on tensor cores when built, else FP32
+    prec_name = args.precision
+    if prec_name == "auto":
+        try:
+            chem.source_term(h, *(t[:256] for t in dev32), chem.SPLIT_BF16)
+            prec_name = "split_bf16"
+        except chem.ChemError as e:
+            if e.status != 4:
+                raise
+            prec_name = "fp32"
+    prec = chem.PRECISIONS[prec_name]
+    if prec == chem.FP64:
+        dev_in = [torch.as_tensor(a, dtype=torch.float64).to(dev) for a in (T, P, Y)]
+        out = torch.empty((N_CELLS, ns), dtype=torch.float64, device=dev)
+    else:
+        dev_in, out = dev32, out32
+
+    def step():
+        chem.source_term(h, *dev_in, prec, out=out, stream=stream)
+
+    # timed region (headline), with clock samples and the launch count
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device() if ws == 1 else local)
+    clocks.start()
+    time.sleep(0.3)
+    n0 = chem.kernel_launch_count()
+    ms = time_device(step, args.steps, 0, stream, ws, dev)
+    launches = chem.kernel_launch_count() - n0
+    clk = clocks.stop()
+    value = ws * N_CELLS / (ms * 1e-3)
+
+    # roofline of the dominant (only) kernel: algorithmic bytes / launch duration
+    elt = 8 if prec == chem.FP64 else 4
+    bytes_per_cell = elt * (2 + 2 * ns)
+    hbm, src = peaks()
+    achieved = bytes_per_cell * N_CELLS / (ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None,
+            "peak_source": f"{src} hbm_gbs", "bytes_per_cell": bytes_per_cell,
+            "kernel": f"source term ({prec_name})"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"split_bf16": "bf16", "fp32": "f32", "fp64": "f64"}[prec_name],
+            "data": "synthetic", "config": config(prec_name, N_CELLS, ws),
+            "roofline": roof, "clocks": clk, "gpu_launches": int(launches)}
+
+    # end to end through the C ABI with pinned host buffers
+    hostT = torch.as_tensor(T, dtype=dev_in[0].dtype).pin_memory()
+    hostP = torch.as_tensor(P, dtype=dev_in[0].dtype).pin_memory()
+    hostY = torch.as_tensor(Y, dtype=dev_in[0].dtype).pin_memory()
+    hostO = torch.empty((N_CELLS, ns), dtype=dev_in[0].dtype).pin_memory()
+    chunk = 1 << 17
+    wsb = chem.host_workspace_bytes(h, chunk, ns, prec)
+    work = torch.empty(wsb, dtype=torch.uint8, device=dev)
+
+    def e2e_step():
+        chem.source_term_host(h, hostT, hostP, hostY, hostO, prec, work, chunk, stream=stream)
+
+    k_e2e = max(3, min(args.steps, 20))
+    ms_e2e = time_device(e2e_step, k_e2e, 2, stream, ws, dev)
+    line["e2e"] = {"value": ws * N_CELLS / (ms_e2e * 1e-3), "unit": UNIT,
+                   "h2d_bytes_per_step": int(elt * N_CELLS * (2 + ns)),
+                   "d2h_bytes_per_step": int(elt * N_CELLS * ns), "chunk_cells": chunk,
+                   "ms_per_step": ms_e2e}
+
+    if rank == 0 and not args.no_extras:
+        # the other precision paths, same workload (secondary numbers)
+        paths = {}
+        outs = {}
+        for name in ("fp64", "fp32", "split_bf16"):
+            p = chem.PRECISIONS[name]
+            if p == chem.FP64:
+                din = [torch.as_tensor(a, dtype=torch.float64).to(dev) for a in (T, P, Y)]
+                o = torch.empty((N_CELLS, ns), dtype=torch.float64, device=dev)
+            else:
+                din, o = dev32, torch.empty_like(out32)
+            try:
+                fn = (lambda din=din, o=o, p=p: chem.source_term(h, *din, p, out=o, stream=stream))
+                ms_p = time_device(fn, 5 if p == chem.FP64 else 20, 2, stream, 1, dev)
+            except chem.ChemError as e:
+                paths[name] = {"status": str(e)}
+                continue
+            paths[name] = {"cells_per_s": N_CELLS / (ms_p * 1e-3), "ms_per_call": ms_p}
+            outs[name] = o
+            del din
+        # cpu_baseline leg: the oracle on a bounded sample, and each path's error on it
+        rate, ncells, secs, nth, idx, ref = oracle_rate(mech, T.astype(np.float64),
+                                                        P.astype(np.float64),
+                                                        Y.astype(np.float64), args.cpu_budget)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": nth, "kind": "oracle",
+                                "sample": f"first {ncells} cells of the workload ({secs:.1f} s)"}
+        sub = idx[:4096]
+        ref_sub = ref[:4096]
+        for name, o in outs.items():
+            w = o[torch.as_tensor(sub, device=dev)].double().cpu().numpy()
+            if name != "fp64":
+                # FP32-input paths are compared on their own rounded inputs
+                from oracle import oracle as O
+                ref_use = O.source_term(mech, T[sub].astype(np.float32).astype(np.float64),
+                                        P[sub].astype(np.float32).astype(np.float64),
+                                        Y[sub].astype(np.float32).astype(np.float64))
+            else:
+                ref_use = ref_sub
+            err = np.abs(w - ref_use).max(1) / np.abs(ref_use).max(1)
+            paths[name]["err_cell_max"] = float(err.max())
+            paths[name]["err_cell_p999"] = float(np.quantile(err, 0.999))
+            paths[name]["err_global"] = float(np.abs(w - ref_use).max() / np.abs(ref_use).max())
+        if "fp64" in paths and "cells_per_s" in paths.get(prec_name, {}):
+            paths["speedup_vs_fp64"] = paths[prec_name]["cells_per_s"] / paths["fp64"]["cells_per_s"]
+        line["paths"] = paths
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * chem.h -- C ABI of the GB300 batched chemical source-term library.
+ *
+ * The library evaluates the net species production rates of a batch of
+ * reacting cells, with the cell count as the leading dimension, as in
+ * "A Neural Network Inspired Formulation of Chemical Kinetics" (Barwey & Raman):
+ *
+ *   omega_ik = sum_j nu_kj q_net,ij                                  (Eq. 2)
+ *   q_net,ij = exp(sum_k nu'_kj ln C_ik + ln k_f,ij)
+ *            - exp(sum_k nu''_kj ln C_ik + ln k_r,ij)                (Eqs. 3-4)
+ *   ln k_f,ij = ln A_j + b_j ln T_i - (E_j/R) / T_i                  (Eqs. 5-6)
+ *   ln k_r,ij = ln k_f,ij - ln K_c,ij                                (Eq. 7)
+ *   ln K_c,ij = -sum_k nu_kj g_k(T_i)/(R T_i)
+ *             + (sum_k nu_kj) ln(p_ref / (R T_i))                    (Eqs. 8-11)
+ *   g_k/(R T) from two-range NASA-7 polynomials                      (Eq. 10)
+ *   third-body concentration M_ij = sum_k eff_kj C_ik multiplies k_f and k_r;
+ *   falloff reactions (Lindemann, Troe) use M in the reduced pressure;
+ *   irreversible reactions have k_r = 0                              (Sec. 2.4)
+ *
+ * Units are cgs throughout: mol, cm^3, s, K, erg, dyn/cm^2.
+ * R = 8.31446261815324e7 erg/(mol K).  omega is in mol/(cm^3 s).
+ *
+ * Conventions shared by every entry point:
+ *  - Array arguments of the compute calls are DEVICE pointers owned by the
+ *    caller, unless the function name ends in _host.  The library never frees
+ *    caller memory.
+ *  - Row-major, cell-major layouts: Y[i * ldY + k] is species k of cell i.
+ *    Leading dimensions count elements and must be >= n_species.
+ *  - Element type follows the precision: CHEM_FP64 -> double,
+ *    CHEM_FP32 and CHEM_SPLIT_BF16 -> float.
+ *  - Work is enqueued on the given CUDA stream (cudaStream_t passed as void*;
+ *    NULL is the legacy default stream) and runs asynchronously; argument
+ *    errors are reported synchronously before anything is enqueued.
+ *  - Every call returns a chem_status; on failure chem_last_error() gives a
+ *    message for the calling thread.
+ *  - Negative mass fractions count as zero.  A cell whose mass fractions are
+ *    all zero has all concentrations zero.
+ */
+#ifndef CHEM_H
+#define CHEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CHEM_ABI_VERSION 1
+
+typedef enum {
+    CHEM_OK = 0,
+    CHEM_EINVAL = 1,        /* invalid argument or descriptor */
+    CHEM_ENOMEM = 2,        /* device or host allocation failed */
+    CHEM_ECUDA = 3,         /* CUDA launch or runtime error (text in chem_last_error) */
+    CHEM_EUNSUPPORTED = 4,  /* valid request outside what this build supports */
+    CHEM_EBUSY = 5,
+    CHEM_ETIMEOUT = 6,
+    CHEM_ENOTREADY = 7,
+    CHEM_ENONCONV = 8
+} chem_status;
+
+typedef enum {
+    CHEM_FP64 = 0,          /* double I/O and arithmetic (SIMT) */
+    CHEM_FP32 = 1,          /* float I/O; SIMT float arithmetic with double-float
+                               exponent assembly */
+    CHEM_SPLIT_BF16 = 2     /* float I/O; both stoichiometric contractions on tcgen05
+                               tensor cores: log2 X split into three BF16 terms,
+                               q_net into two, FP32 accumulation in tensor memory */
+} chem_precision;
+
+/* Reaction kinds (chem_mech_desc.kind). */
+enum { CHEM_RXN_ELEMENTARY = 0, CHEM_RXN_THIRD_BODY = 1, CHEM_RXN_LINDEMANN = 2,
+       CHEM_RXN_TROE = 3 };
+
+/*
+ * Mechanism descriptor (Eq. 1 and Sec. 2.4).  All pointers are HOST pointers
+ * read during chem_mechanism_load only; the library copies what it needs.
+ */
+typedef struct {
+    int32_t n_species;        /* N_S >= 1 */
+    int32_t n_reactions;      /* N_R >= 1 */
+    int32_t n_elements;       /* >= 0; 0 skips the element-balance check */
+    const int32_t *elem_comp; /* [n_species][n_elements] atom counts, or NULL */
+    const double *mol_weight; /* [n_species] g/mol, > 0 */
+    const int32_t *nu_f;      /* [n_reactions][n_species] reactant coefficients nu' >= 0 */
+    const int32_t *nu_r;      /* [n_reactions][n_species] product coefficients nu'' >= 0 */
+    const double *arrh;       /* [n_reactions][3] ln A (cgs), b, E/R (K); for falloff
+                                 reactions the high-pressure limit */
+    const int32_t *kind;      /* [n_reactions] CHEM_RXN_* */
+    const int32_t *reversible;/* [n_reactions] 1 reversible, 0 irreversible */
+    const double *eff;        /* [n_reactions][n_species] third-body efficiencies, or
+                                 NULL for all 1; read for kinds 1-3 only */
+    const double *arrh_low;   /* [n_reactions][3] low-pressure ln A0, b0, E0/R for kinds
+                                 2-3 (may be NULL when there are none) */
+    const double *troe;       /* [n_reactions][4] alpha, T***, T*, T** for kind 3;
+                                 T*** > 0 and T* > 0; T** <= 0 means the term is absent */
+    const double *nasa7;      /* [n_species][2][7] NASA-7 a1..a7: set 0 for T < t_mid,
+                                 set 1 for T >= t_mid */
+    double t_mid;             /* K, > 0 */
+    double p_ref;             /* standard pressure of the thermo data, dyn/cm^2 (1 bar =
+                                 1e6 in the paper, Eq. 8) */
+} chem_mech_desc;
+
+typedef struct chem_mech chem_mech;   /* opaque; immutable after load */
+
+/* ABI version of the loaded library (CHEM_ABI_VERSION). */
+int32_t chem_abi_version(void);
+
+/*
+ * Validate a descriptor and build the device-resident tables on the current
+ * CUDA device.  Checks: sizes, coefficient ranges (0..127, at most 8 species
+ * with nonzero coefficient per side, at least one reactant), element balance
+ * when elem_comp is given, positive weights, Troe temperatures, t_mid, p_ref.
+ * The FP64 tables fold the Gibbs layer through the net stoichiometry in double
+ * precision (Eqs. 9-11).  On success *out owns host and device memory until
+ * chem_mechanism_free.  Errors: CHEM_EINVAL (bad descriptor, message names the
+ * reaction), CHEM_ENOMEM, CHEM_ECUDA.  Synchronous.
+ */
+chem_status chem_mechanism_load(const chem_mech_desc *desc, chem_mech **out);
+
+/* Release a mechanism (NULL is accepted).  Synchronises the device first. */
+chem_status chem_mechanism_free(chem_mech *mech);
+
+/* Sizes of a loaded mechanism; any output pointer may be NULL. */
+chem_status chem_mechanism_info(const chem_mech *mech, int32_t *n_species,
+                                int32_t *n_reactions, size_t *device_bytes);
+
+/*
+ * Net production rates omega[n_cells][ldO] from cell states: T[n_cells] (K),
+ * P[n_cells] (dyn/cm^2), Y[n_cells][ldY] mass fractions (Eqs. 2-11, Sec. 2.4).
+ * Concentrations: C_k = rho Y_k / W_k with rho = P Wbar / (R T).
+ * Device pointers; element type double for CHEM_FP64, float otherwise.  Columns
+ * n_species..ldO-1 of omega are not written.  n_cells == 0 is a no-op.
+ * Errors: CHEM_EINVAL (NULL pointers with n_cells > 0, n_cells < 0,
+ * ldY/ldO < n_species, mechanism loaded on another device), CHEM_EUNSUPPORTED
+ * (precision not built for this mechanism size), CHEM_ECUDA (launch failure).
+ * Asynchronous on `stream`.
+ */
+chem_status chem_source_term(const chem_mech *mech, int64_t n_cells, const void *T,
+                             const void *P, const void *Y, int64_t ldY, void *omega,
+                             int64_t ldO, chem_precision precision, void *stream);
+
+/*
+ * Device workspace (bytes) that chem_source_term_host needs for a given chunk size:
+ * two stages of T, P, Y and omega rows of chunk_cells cells each.
+ */
+size_t chem_source_term_host_workspace(const chem_mech *mech, int64_t chunk_cells,
+                                       int64_t ldY, chem_precision precision);
+
+/*
+ * chem_source_term with HOST arrays (same layouts and element types): the cells are
+ * processed in chunks of chunk_cells; each chunk is copied host->device, evaluated and
+ * copied back, with the copies of one chunk overlapping the kernel of the next on two
+ * library-owned streams.  Host arrays should be page-locked for the copies to overlap.
+ * `workspace` is caller-owned device memory of at least
+ * chem_source_term_host_workspace(mech, chunk_cells, ldY, precision) bytes, 256-byte
+ * aligned; the library allocates nothing per call.  The work is ordered after prior work
+ * on `stream`, and `stream` waits for all of it, so synchronising `stream` makes omega
+ * valid on the host.  Errors: as chem_source_term, plus CHEM_EINVAL for a NULL or
+ * undersized workspace or chunk_cells < 1.
+ */
+chem_status chem_source_term_host(const chem_mech *mech, int64_t n_cells, const void *T,
+                                  const void *P, const void *Y, int64_t ldY, void *omega,
+                                  int64_t ldO, chem_precision precision, int64_t chunk_cells,
+                                  void *workspace, size_t workspace_bytes, void *stream);
+
+/* Number of kernels this library has launched in the process so far. */
+uint64_t chem_kernel_launch_count(void);
+
+/* Message of the last failed call on the calling thread ("" if none). */
+const char *chem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHEM_H */

@@ -1,0 +1,184 @@
+"""Thin Python binding of the C ABI in include/chem.h (argument marshalling only).
+
+Every computation runs in the CUDA library libchemgb300.so; this module only
+converts arguments.  It raises ChemError if the library has not been built: there
+is no fallback path.  PyTorch provides device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libchemgb300.so")
+
+FP64, FP32, SPLIT_BF16 = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "split_bf16": SPLIT_BF16}
+
+STATUS = {0: "CHEM_OK", 1: "CHEM_EINVAL", 2: "CHEM_ENOMEM", 3: "CHEM_ECUDA",
+          4: "CHEM_EUNSUPPORTED", 5: "CHEM_EBUSY", 6: "CHEM_ETIMEOUT", 7: "CHEM_ENOTREADY",
+          8: "CHEM_ENONCONV"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class ChemError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Desc(C.Structure):
+    _fields_ = [("n_species", C.c_int32), ("n_reactions", C.c_int32), ("n_elements", C.c_int32),
+                ("elem_comp", C.c_void_p), ("mol_weight", C.c_void_p), ("nu_f", C.c_void_p),
+                ("nu_r", C.c_void_p), ("arrh", C.c_void_p), ("kind", C.c_void_p),
+                ("reversible", C.c_void_p), ("eff", C.c_void_p), ("arrh_low", C.c_void_p),
+                ("troe", C.c_void_p), ("nasa7", C.c_void_p), ("t_mid", C.c_double),
+                ("p_ref", C.c_double)]
+
+
+def lib():
+    """The loaded CUDA library (raises ChemError if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ChemError(3, f"CUDA library {LIB_PATH} is not built; run "
+                                   "__graft_entry__.build() or paper_2008_08483_gb300/build.py")
+            L = C.CDLL(LIB_PATH)
+            P, I64, I32 = C.c_void_p, C.c_int64, C.c_int32
+            L.chem_abi_version.restype = I32
+            L.chem_last_error.restype = C.c_char_p
+            L.chem_kernel_launch_count.restype = C.c_uint64
+            L.chem_mechanism_load.argtypes = [C.POINTER(_Desc), C.POINTER(P)]
+            L.chem_mechanism_free.argtypes = [P]
+            L.chem_mechanism_info.argtypes = [P, C.POINTER(I32), C.POINTER(I32),
+                                              C.POINTER(C.c_size_t)]
+            L.chem_source_term.argtypes = [P, I64, P, P, P, I64, P, I64, C.c_int, P]
+            L.chem_source_term_host_workspace.argtypes = [P, I64, I64, C.c_int]
+            L.chem_source_term_host_workspace.restype = C.c_size_t
+            L.chem_source_term_host.argtypes = [P, I64, P, P, P, I64, P, I64, C.c_int, I64, P,
+                                                C.c_size_t, P]
+            for f in (L.chem_mechanism_load, L.chem_mechanism_free, L.chem_mechanism_info,
+                      L.chem_source_term, L.chem_source_term_host):
+                f.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise ChemError(rc, lib().chem_last_error().decode(errors="replace"))
+
+
+def abi_version() -> int:
+    return int(lib().chem_abi_version())
+
+
+def kernel_launch_count() -> int:
+    return int(lib().chem_kernel_launch_count())
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+class Mechanism:
+    """A mechanism loaded on the current CUDA device (chem_mechanism_load)."""
+
+    def __init__(self, desc):
+        keep = dict(
+            elem_comp=np.ascontiguousarray(desc.elem_comp, np.int32),
+            mol_weight=np.ascontiguousarray(desc.mol_weight, np.float64),
+            nu_f=np.ascontiguousarray(desc.nu_f, np.int32),
+            nu_r=np.ascontiguousarray(desc.nu_r, np.int32),
+            arrh=np.ascontiguousarray(desc.arrh, np.float64),
+            kind=np.ascontiguousarray(desc.kind, np.int32),
+            reversible=np.ascontiguousarray(desc.reversible, np.int32),
+            eff=np.ascontiguousarray(desc.eff, np.float64),
+            arrh_low=np.ascontiguousarray(desc.arrh_low, np.float64),
+            troe=np.ascontiguousarray(desc.troe, np.float64),
+            nasa7=np.ascontiguousarray(desc.nasa7, np.float64),
+        )
+        ns, nr = keep["nu_f"].shape[1], keep["nu_f"].shape[0]
+        ne = keep["elem_comp"].shape[1] if keep["elem_comp"].ndim == 2 else 0
+        d = _Desc(ns, nr, ne, *(_ptr(keep[k]).value for k in (
+            "elem_comp", "mol_weight", "nu_f", "nu_r", "arrh", "kind", "reversible", "eff",
+            "arrh_low", "troe", "nasa7")), float(desc.t_mid), float(desc.p_ref))
+        h = C.c_void_p()
+        _check(lib().chem_mechanism_load(C.byref(d), C.byref(h)))
+        self._h = h
+        self.n_species, self.n_reactions = ns, nr
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ChemError(1, "mechanism was freed")
+        return self._h
+
+    def info(self):
+        ns, nr, nb = C.c_int32(), C.c_int32(), C.c_size_t()
+        _check(lib().chem_mechanism_info(self.handle, C.byref(ns), C.byref(nr), C.byref(nb)))
+        return {"n_species": ns.value, "n_reactions": nr.value, "device_bytes": nb.value}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _check(lib().chem_mechanism_free(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dtype(precision):
+    import torch
+    return torch.float64 if precision == FP64 else torch.float32
+
+
+def source_term(mech: Mechanism, T, P, Y, precision: int = SPLIT_BF16, out=None, stream=None):
+    """omega [n, ns] from CUDA tensors T [n], P [n], Y [n, ldY] (chem_source_term)."""
+    import torch
+    dt = _dtype(precision)
+    n = T.shape[0]
+    for name, t in (("T", T), ("P", P), ("Y", Y)):
+        if not t.is_cuda or t.dtype != dt:
+            raise ChemError(1, f"{name} must be a CUDA {dt} tensor")
+    if T.stride(0) != 1 or P.stride(0) != 1 or Y.dim() != 2 or Y.stride(1) != 1:
+        raise ChemError(1, "T, P must be contiguous and Y row-major with unit column stride")
+    if out is None:
+        out = torch.empty((n, mech.n_species), dtype=dt, device=T.device)
+    _check(lib().chem_source_term(mech.handle, n, T.data_ptr(), P.data_ptr(), Y.data_ptr(),
+                                  Y.stride(0), out.data_ptr(), out.stride(0), int(precision),
+                                  _stream_ptr(stream)))
+    return out
+
+
+def host_workspace_bytes(mech: Mechanism, chunk_cells: int, ldY: int, precision: int) -> int:
+    return int(lib().chem_source_term_host_workspace(mech.handle, chunk_cells, ldY,
+                                                     int(precision)))
+
+
+def source_term_host(mech: Mechanism, T, P, Y, out, precision: int, workspace, chunk_cells: int,
+                     stream=None):
+    """chem_source_term_host: T, P, Y, out are host tensors (page-locked for overlap),
+    workspace a CUDA byte tensor of at least host_workspace_bytes()."""
+    n = T.shape[0]
+    _check(lib().chem_source_term_host(mech.handle, n, T.data_ptr(), P.data_ptr(), Y.data_ptr(),
+                                       Y.stride(0), out.data_ptr(), out.stride(0), int(precision),
+                                       int(chunk_cells), workspace.data_ptr(),
+                                       workspace.numel() * workspace.element_size(),
+                                       _stream_ptr(stream)))
+    return out

@@ -1,0 +1,105 @@
+// chem_internal.h -- device table layouts and shared declarations of the library.
+// Included by the library's own translation units only.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+
+#include "chem.h"
+
+namespace chem {
+
+constexpr int kMaxSide = 8;                       // species per reaction side (SIMT tables)
+constexpr int kMaxSpecies = 1024;
+constexpr int kMaxReactions = 65536;
+constexpr double kR = 8.31446261815324e7;         // erg / (mol K)
+constexpr double kLog2e = 1.44269504088896340736;
+constexpr double kLn2 = 0.69314718055994530942;
+
+// One reaction for the FP64 SIMT path.  Natural-log units.  Every thread of a warp
+// reads the same record, so the loads are broadcasts.
+struct alignas(16) RxnF64 {
+    double lnA, b, EoR;          // ln k_inf = lnA + b ln T - EoR / T            (Eq. 6)
+    double kc[2][7];             // ln K_c per T range on [1, ln T, tau, tau^2, tau^3, tau^4, 1/T],
+                                 // tau = T / 1000, folded from NASA-7 through nu (Eqs. 9-11)
+    double low[3];               // ln k0 = low0 + low1 ln T - low2 / T           (falloff)
+    double troe[5];              // 1 - alpha, alpha, 1/T***, 1/T*, T** (<= 0: absent)
+    int32_t kind, rev;
+    int32_t tb_begin, tb_end;    // third-body list range (kinds 1-3)
+    int32_t nf, nr;              // species on each side
+    uint16_t spf[kMaxSide], spr[kMaxSide];
+    uint8_t nuf[kMaxSide], nur[kMaxSide];
+};
+
+// One reaction for the FP32 SIMT path.  log2 units; double-float (hi, lo) coefficients
+// for the large-magnitude parts of the exponent.
+struct alignas(16) RxnF32 {
+    float2 kf[3];                // log2 k_inf on [1, log2 T, 1/T]
+    float2 k0[3];                // log2 k0 on [1, log2 T, 1/T]
+    float troe[5];               // 1 - alpha, alpha, 1/T***, 1/T*, T**
+    int32_t kind, rev;
+    int32_t tb_begin, tb_end;
+    int32_t nf, nr, dnu;         // dnu = sum_k nu_kj
+    int32_t ordf, ordr;          // reaction orders sum nu', sum nu''
+    uint16_t spf[kMaxSide], spr[kMaxSide];
+    uint8_t nuf[kMaxSide], nur[kMaxSide];
+};
+
+// Per species: -g_k/(RT) in log2 units on [1, log2 T, tau, tau^2, tau^3, tau^4, 1/T] as
+// double-float pairs, for each T range (FP32 path Gibbs layer, Eq. 10).
+struct alignas(16) SpecF32 {
+    float2 gl[2][7];
+    float invW;
+    float pad[3];
+};
+
+struct MechViewF64 {
+    int ns, nr;
+    const RxnF64 *rxn;
+    const uint16_t *tb_sp;       // third-body species lists
+    const double *tb_e;          // efficiency - 1 for listed species
+    const double *invW;          // [ns] 1 / W_k
+    double t_mid;
+};
+
+struct MechViewF32 {
+    int ns, nr;
+    const RxnF32 *rxn;
+    const SpecF32 *spec;
+    const uint16_t *tb_sp;
+    const float *tb_e;
+    float t_mid;
+    float2 lg2_pref_R;           // log2(p_ref / R), double-float
+};
+
+}  // namespace chem
+
+// The opaque handle of the C ABI.
+struct chem_mech {
+    int ns, nr, device;
+    double t_mid, p_ref;
+    size_t device_bytes;
+    void *d_blob;
+    chem::MechViewF64 v64;
+    chem::MechViewF32 v32;
+    bool have_bf16;
+    void *bf16;                  // split-BF16 tables (tensor-core path), see kern_bf16.cu
+};
+
+namespace chem {
+
+chem_status set_error(chem_status st, const char *fmt, ...);
+void clear_error();
+extern std::atomic<uint64_t> g_launches;
+
+chem_status launch_source_fp64(const chem_mech *m, int64_t n, const double *T, const double *P,
+                               const double *Y, int64_t ldY, double *om, int64_t ldO,
+                               cudaStream_t s);
+chem_status launch_source_fp32(const chem_mech *m, int64_t n, const float *T, const float *P,
+                               const float *Y, int64_t ldY, float *om, int64_t ldO,
+                               cudaStream_t s);
+
+}  // namespace chem

@@ -1,0 +1,366 @@
+// chem_mech.cu -- mechanism validation, load-time preprocessing and device upload.
+//
+// Load-time work (all in double precision on the host):
+//  * sparse per-reaction species lists for the SIMT paths;
+//  * the Arrhenius layer coefficients (Eq. 6) in natural-log (FP64 path) and log2
+//    double-float (FP32 path) form;
+//  * the Gibbs layer (Eq. 10) folded through the net stoichiometry (Eq. 11): the
+//    coefficients of ln K_c on [1, ln T, tau, ..., tau^4, 1/T] per temperature range,
+//    where the species cancellation of sum_k nu_kj g_k happens in double precision;
+//  * third-body efficiency lists (efficiency - 1 for the species that differ from 1,
+//    since M = sum_k eff_k C_k = c_tot + sum_k (eff_k - 1) C_k, Sec. 2.4).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "chem_internal.h"
+
+namespace chem {
+
+std::atomic<uint64_t> g_launches{0};
+
+static thread_local std::string t_err;
+
+chem_status set_error(chem_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return st;
+}
+
+void clear_error() { t_err.clear(); }
+
+const char *last_error() { return t_err.c_str(); }
+
+static float2 dsplit(double x)
+{
+    float h = (float)x;
+    float l = (float)(x - (double)h);
+    return make_float2(h, l);
+}
+
+void bf16_free_tables(void *p);
+chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d);
+
+}  // namespace chem
+
+using namespace chem;
+
+extern "C" int32_t chem_abi_version(void) { return CHEM_ABI_VERSION; }
+
+extern "C" const char *chem_last_error(void) { return chem::last_error(); }
+
+extern "C" uint64_t chem_kernel_launch_count(void) { return g_launches.load(); }
+
+static chem_status validate(const chem_mech_desc *d)
+{
+    if (!d) return set_error(CHEM_EINVAL, "descriptor is NULL");
+    const int ns = d->n_species, nr = d->n_reactions;
+    if (ns < 1 || ns > kMaxSpecies)
+        return set_error(CHEM_EINVAL, "n_species=%d outside [1, %d]", ns, kMaxSpecies);
+    if (nr < 1 || nr > kMaxReactions)
+        return set_error(CHEM_EINVAL, "n_reactions=%d outside [1, %d]", nr, kMaxReactions);
+    if (d->n_elements < 0) return set_error(CHEM_EINVAL, "n_elements < 0");
+    if (!d->mol_weight || !d->nu_f || !d->nu_r || !d->arrh || !d->kind || !d->reversible ||
+        !d->nasa7)
+        return set_error(CHEM_EINVAL, "required descriptor array is NULL");
+    if (d->n_elements > 0 && !d->elem_comp)
+        return set_error(CHEM_EINVAL, "n_elements > 0 but elem_comp is NULL");
+    if (!(d->t_mid > 0.0) || !isfinite(d->t_mid)) return set_error(CHEM_EINVAL, "t_mid must be > 0");
+    if (!(d->p_ref > 0.0) || !isfinite(d->p_ref)) return set_error(CHEM_EINVAL, "p_ref must be > 0");
+    for (int k = 0; k < ns; ++k) {
+        if (!(d->mol_weight[k] > 0.0) || !isfinite(d->mol_weight[k]))
+            return set_error(CHEM_EINVAL, "mol_weight[%d] must be finite and > 0", k);
+        for (int c = 0; c < 14; ++c)
+            if (!isfinite(d->nasa7[(size_t)k * 14 + c]))
+                return set_error(CHEM_EINVAL, "nasa7 of species %d is not finite", k);
+    }
+    for (int j = 0; j < nr; ++j) {
+        int nfs = 0, nrs = 0;
+        for (int k = 0; k < ns; ++k) {
+            int a = d->nu_f[(size_t)j * ns + k], b = d->nu_r[(size_t)j * ns + k];
+            if (a < 0 || a > 127 || b < 0 || b > 127)
+                return set_error(CHEM_EINVAL, "reaction %d: coefficient outside [0, 127]", j);
+            nfs += a > 0;
+            nrs += b > 0;
+        }
+        if (nfs < 1 || nrs < 1)
+            return set_error(CHEM_EINVAL, "reaction %d: needs at least one reactant and product", j);
+        if (nfs > kMaxSide || nrs > kMaxSide)
+            return set_error(CHEM_EINVAL, "reaction %d: more than %d species on a side", j,
+                             kMaxSide);
+        for (int c = 0; c < 3; ++c)
+            if (!isfinite(d->arrh[(size_t)j * 3 + c]))
+                return set_error(CHEM_EINVAL, "reaction %d: Arrhenius parameters not finite", j);
+        int kd = d->kind[j];
+        if (kd < 0 || kd > 3) return set_error(CHEM_EINVAL, "reaction %d: kind %d", j, kd);
+        if (d->reversible[j] != 0 && d->reversible[j] != 1)
+            return set_error(CHEM_EINVAL, "reaction %d: reversible must be 0 or 1", j);
+        if (kd >= 1 && d->eff) {
+            for (int k = 0; k < ns; ++k) {
+                double e = d->eff[(size_t)j * ns + k];
+                if (!isfinite(e) || e < 0.0)
+                    return set_error(CHEM_EINVAL, "reaction %d: efficiency must be finite, >= 0", j);
+            }
+        }
+        if (kd >= 2) {
+            if (!d->arrh_low)
+                return set_error(CHEM_EINVAL, "reaction %d: falloff without arrh_low", j);
+            for (int c = 0; c < 3; ++c)
+                if (!isfinite(d->arrh_low[(size_t)j * 3 + c]))
+                    return set_error(CHEM_EINVAL, "reaction %d: arrh_low not finite", j);
+        }
+        if (kd == 3) {
+            if (!d->troe) return set_error(CHEM_EINVAL, "reaction %d: Troe without troe", j);
+            const double *t = d->troe + (size_t)j * 4;
+            if (!isfinite(t[0]) || !(t[1] > 0.0) || !(t[2] > 0.0) || !isfinite(t[1]) ||
+                !isfinite(t[2]) || !isfinite(t[3]))
+                return set_error(CHEM_EINVAL, "reaction %d: Troe needs finite alpha, T***>0, T*>0",
+                                 j);
+        }
+        if (d->n_elements > 0) {
+            for (int e = 0; e < d->n_elements; ++e) {
+                long long bal = 0;
+                for (int k = 0; k < ns; ++k) {
+                    long long nu = (long long)d->nu_r[(size_t)j * ns + k] -
+                                   d->nu_f[(size_t)j * ns + k];
+                    bal += nu * d->elem_comp[(size_t)k * d->n_elements + e];
+                }
+                if (bal != 0)
+                    return set_error(CHEM_EINVAL, "reaction %d is not balanced in element %d", j, e);
+            }
+        }
+    }
+    return CHEM_OK;
+}
+
+// ln K_c coefficients of reaction j, temperature range r, on [1, ln T, tau, tau^2, tau^3,
+// tau^4, 1/T] (tau = T/1000).  With g/(RT) = a1 (1 - ln T) - a2 T/2 - a3 T^2/6 - a4 T^3/12
+// - a5 T^4/20 + a6/T - a7 and ln K_c = -sum_k nu_k g_k/(RT) + dnu (ln(p_ref/R) - ln T).
+static void fold_kc(const chem_mech_desc *d, int j, int r, double out[7])
+{
+    const int ns = d->n_species;
+    double c[7] = {0, 0, 0, 0, 0, 0, 0};
+    long dnu = 0;
+    for (int k = 0; k < ns; ++k) {
+        int nu = d->nu_r[(size_t)j * ns + k] - d->nu_f[(size_t)j * ns + k];
+        if (!nu) continue;
+        const double *a = d->nasa7 + (size_t)k * 14 + (size_t)r * 7;
+        c[0] += -nu * (a[0] - a[6]);
+        c[1] += nu * a[0];
+        c[2] += nu * a[1] / 2.0 * 1e3;
+        c[3] += nu * a[2] / 6.0 * 1e6;
+        c[4] += nu * a[3] / 12.0 * 1e9;
+        c[5] += nu * a[4] / 20.0 * 1e12;
+        c[6] += -nu * a[5];
+        dnu += nu;
+    }
+    c[0] += (double)dnu * log(d->p_ref / kR);
+    c[1] -= (double)dnu;
+    for (int m = 0; m < 7; ++m) out[m] = c[m];
+}
+
+extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **out)
+{
+    clear_error();
+    if (!out) return set_error(CHEM_EINVAL, "out is NULL");
+    *out = nullptr;
+    chem_status st = validate(d);
+    if (st != CHEM_OK) return st;
+    const int ns = d->n_species, nr = d->n_reactions;
+
+    std::vector<RxnF64> r64(nr);
+    std::vector<RxnF32> r32(nr);
+    std::vector<SpecF32> s32(ns);
+    std::vector<uint16_t> tb_sp;
+    std::vector<double> tb_e64;
+    std::vector<float> tb_e32;
+    std::vector<double> invW(ns);
+    for (int k = 0; k < ns; ++k) invW[k] = 1.0 / d->mol_weight[k];
+
+    for (int j = 0; j < nr; ++j) {
+        RxnF64 &a = r64[j];
+        RxnF32 &b = r32[j];
+        memset(&a, 0, sizeof a);
+        memset(&b, 0, sizeof b);
+        const double *ar = d->arrh + (size_t)j * 3;
+        a.lnA = ar[0];
+        a.b = ar[1];
+        a.EoR = ar[2];
+        b.kf[0] = dsplit(ar[0] * kLog2e);
+        b.kf[1] = dsplit(ar[1]);
+        b.kf[2] = dsplit(-ar[2] * kLog2e);
+        for (int r = 0; r < 2; ++r) fold_kc(d, j, r, a.kc[r]);
+        a.kind = b.kind = d->kind[j];
+        a.rev = b.rev = d->reversible[j];
+        int nf = 0, nrr = 0, ordf = 0, ordr = 0;
+        for (int k = 0; k < ns; ++k) {
+            int f = d->nu_f[(size_t)j * ns + k], p = d->nu_r[(size_t)j * ns + k];
+            if (f) {
+                a.spf[nf] = b.spf[nf] = (uint16_t)k;
+                a.nuf[nf] = b.nuf[nf] = (uint8_t)f;
+                ++nf;
+                ordf += f;
+            }
+            if (p) {
+                a.spr[nrr] = b.spr[nrr] = (uint16_t)k;
+                a.nur[nrr] = b.nur[nrr] = (uint8_t)p;
+                ++nrr;
+                ordr += p;
+            }
+        }
+        a.nf = b.nf = nf;
+        a.nr = b.nr = nrr;
+        b.ordf = ordf;
+        b.ordr = ordr;
+        b.dnu = ordr - ordf;
+        a.tb_begin = b.tb_begin = (int32_t)tb_sp.size();
+        if (a.kind >= 1) {
+            for (int k = 0; k < ns; ++k) {
+                double e = d->eff ? d->eff[(size_t)j * ns + k] : 1.0;
+                if (e != 1.0) {
+                    tb_sp.push_back((uint16_t)k);
+                    tb_e64.push_back(e - 1.0);
+                    tb_e32.push_back((float)(e - 1.0));
+                }
+            }
+        }
+        a.tb_end = b.tb_end = (int32_t)tb_sp.size();
+        if (a.kind >= 2) {
+            const double *al = d->arrh_low + (size_t)j * 3;
+            a.low[0] = al[0];
+            a.low[1] = al[1];
+            a.low[2] = al[2];
+            b.k0[0] = dsplit(al[0] * kLog2e);
+            b.k0[1] = dsplit(al[1]);
+            b.k0[2] = dsplit(-al[2] * kLog2e);
+        }
+        if (a.kind == 3) {
+            const double *t = d->troe + (size_t)j * 4;
+            double tr[5] = {1.0 - t[0], t[0], 1.0 / t[1], 1.0 / t[2], t[3]};
+            for (int c = 0; c < 5; ++c) {
+                a.troe[c] = tr[c];
+                b.troe[c] = (float)tr[c];
+            }
+        }
+    }
+    // FP32 Gibbs layer: -g_k/(RT) in log2 units on [1, log2 T, tau, tau^2, tau^3, tau^4, 1/T]
+    for (int k = 0; k < ns; ++k) {
+        memset(&s32[k], 0, sizeof s32[k]);
+        s32[k].invW = (float)invW[k];
+        for (int r = 0; r < 2; ++r) {
+            const double *a = d->nasa7 + (size_t)k * 14 + (size_t)r * 7;
+            double c[7] = {(-(a[0] - a[6])) * kLog2e, a[0], a[1] / 2.0 * 1e3 * kLog2e,
+                           a[2] / 6.0 * 1e6 * kLog2e, a[3] / 12.0 * 1e9 * kLog2e,
+                           a[4] / 20.0 * 1e12 * kLog2e, -a[5] * kLog2e};
+            for (int m = 0; m < 7; ++m) s32[k].gl[r][m] = dsplit(c[m]);
+        }
+    }
+
+    // one device blob
+    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t o_r64 = 0;
+    size_t o_r32 = align(o_r64 + sizeof(RxnF64) * nr);
+    size_t o_s32 = align(o_r32 + sizeof(RxnF32) * nr);
+    size_t o_tbsp = align(o_s32 + sizeof(SpecF32) * ns);
+    size_t ntb = tb_sp.size() ? tb_sp.size() : 1;
+    size_t o_tbe64 = align(o_tbsp + sizeof(uint16_t) * ntb);
+    size_t o_tbe32 = align(o_tbe64 + sizeof(double) * ntb);
+    size_t o_invw = align(o_tbe32 + sizeof(float) * ntb);
+    size_t total = align(o_invw + sizeof(double) * ns);
+    std::vector<unsigned char> h(total, 0);
+    memcpy(h.data() + o_r64, r64.data(), sizeof(RxnF64) * nr);
+    memcpy(h.data() + o_r32, r32.data(), sizeof(RxnF32) * nr);
+    memcpy(h.data() + o_s32, s32.data(), sizeof(SpecF32) * ns);
+    if (!tb_sp.empty()) {
+        memcpy(h.data() + o_tbsp, tb_sp.data(), sizeof(uint16_t) * tb_sp.size());
+        memcpy(h.data() + o_tbe64, tb_e64.data(), sizeof(double) * tb_e64.size());
+        memcpy(h.data() + o_tbe32, tb_e32.data(), sizeof(float) * tb_e32.size());
+    }
+    memcpy(h.data() + o_invw, invW.data(), sizeof(double) * ns);
+
+    chem_mech *m = new (std::nothrow) chem_mech();
+    if (!m) return set_error(CHEM_ENOMEM, "host allocation failed");
+    m->ns = ns;
+    m->nr = nr;
+    m->t_mid = d->t_mid;
+    m->p_ref = d->p_ref;
+    m->have_bf16 = false;
+    m->bf16 = nullptr;
+    if (cudaGetDevice(&m->device) != cudaSuccess) {
+        delete m;
+        return set_error(CHEM_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    cudaError_t e = cudaMalloc(&m->d_blob, total);
+    if (e != cudaSuccess) {
+        delete m;
+        return set_error(CHEM_ENOMEM, "cudaMalloc(%zu): %s", total, cudaGetErrorString(e));
+    }
+    e = cudaMemcpy(m->d_blob, h.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(m->d_blob);
+        delete m;
+        return set_error(CHEM_ECUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
+    }
+    m->device_bytes = total;
+    unsigned char *base = (unsigned char *)m->d_blob;
+    m->v64.ns = ns;
+    m->v64.nr = nr;
+    m->v64.rxn = (const RxnF64 *)(base + o_r64);
+    m->v64.tb_sp = (const uint16_t *)(base + o_tbsp);
+    m->v64.tb_e = (const double *)(base + o_tbe64);
+    m->v64.invW = (const double *)(base + o_invw);
+    m->v64.t_mid = d->t_mid;
+    m->v32.ns = ns;
+    m->v32.nr = nr;
+    m->v32.rxn = (const RxnF32 *)(base + o_r32);
+    m->v32.spec = (const SpecF32 *)(base + o_s32);
+    m->v32.tb_sp = (const uint16_t *)(base + o_tbsp);
+    m->v32.tb_e = (const float *)(base + o_tbe32);
+    m->v32.t_mid = (float)d->t_mid;
+    m->v32.lg2_pref_R = dsplit(log2(d->p_ref / kR));
+
+    st = bf16_build_tables(m, d);
+    if (st != CHEM_OK && st != CHEM_EUNSUPPORTED) {
+        cudaFree(m->d_blob);
+        delete m;
+        return st;
+    }
+    clear_error();
+    *out = m;
+    return CHEM_OK;
+}
+
+extern "C" chem_status chem_mechanism_free(chem_mech *m)
+{
+    clear_error();
+    if (!m) return CHEM_OK;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != m->device) cudaSetDevice(m->device);
+    cudaDeviceSynchronize();
+    if (m->bf16) bf16_free_tables(m->bf16);
+    cudaError_t e = cudaFree(m->d_blob);
+    if (cur >= 0 && cur != m->device) cudaSetDevice(cur);
+    delete m;
+    if (e != cudaSuccess) return set_error(CHEM_ECUDA, "cudaFree: %s", cudaGetErrorString(e));
+    return CHEM_OK;
+}
+
+extern "C" chem_status chem_mechanism_info(const chem_mech *m, int32_t *ns, int32_t *nr,
+                                           size_t *bytes)
+{
+    clear_error();
+    if (!m) return set_error(CHEM_EINVAL, "mechanism is NULL");
+    if (ns) *ns = m->ns;
+    if (nr) *nr = m->nr;
+    if (bytes) *bytes = m->device_bytes;
+    return CHEM_OK;
+}

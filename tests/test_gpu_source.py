@@ -1,0 +1,166 @@
+"""Parity of the CUDA source-term paths with the FP64 CPU oracle, element by element,
+through the C ABI.
+
+Error measure: per cell, max_k |omega_gpu - omega_oracle| / max_k |omega_oracle|.
+Bars: 1e-10 for FP64, 1e-5 for FP32, 1e-4 for split BF16.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2008_08483_gb300 import build as B
+from paper_2008_08483_gb300 import chem, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {chem.FP64: 1e-10, chem.FP32: 1e-5, chem.SPLIT_BF16: 1e-4}
+STATES = {  # (state kind, T range, P range in atm) of each workload
+    "h2air_9_21": ("dirichlet", (1000.0, 2500.0), (1.0, 1.0)),
+    "gri_53_325": ("mixture", (800.0, 2800.0), (1.0, 50.0)),
+    "heavy_160_1000": ("mixture", (700.0, 2600.0), (1.0, 100.0)),
+}
+
+
+@pytest.fixture(scope="module")
+def dev():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    B.build()
+    return torch.device("cuda:0")
+
+
+_mechs = {}
+
+
+def loaded(size, seed=1, **kw):
+    key = (size, seed, tuple(sorted(kw.items())))
+    if key not in _mechs:
+        m = synth.make_mechanism(size, seed=seed, **kw)
+        _mechs[key] = (m, chem.Mechanism(m), O.OracleMechanism(m))
+    return _mechs[key]
+
+
+def states(m, size, n, seed=1234):
+    kind, Tr, Pr = STATES[size]
+    return synth.make_states(m, n, seed=seed, kind=kind, T_range=Tr, P_atm=Pr)
+
+
+def run(h, T, P, Y, prec, dev, ldY=None, ldO=None):
+    dt = torch.float64 if prec == chem.FP64 else torch.float32
+    n, ns = Y.shape
+    ldY = ldY or ns
+    ldO = ldO or ns
+    Yb = torch.zeros((n, ldY), dtype=dt, device=dev)
+    Yb[:, :ns] = torch.as_tensor(Y, dtype=dt)
+    ob = torch.full((n, ldO), 12345.0, dtype=dt, device=dev)
+    chem.source_term(h, torch.as_tensor(T, dtype=dt, device=dev),
+                     torch.as_tensor(P, dtype=dt, device=dev), Yb[:, :ns], prec,
+                     out=ob[:, :ns])
+    torch.cuda.synchronize()
+    o = ob.cpu().numpy().astype(np.float64)
+    return o[:, :ns], o[:, ns:]
+
+
+def cell_err(w, ref):
+    return np.abs(w - ref).max(1) / np.abs(ref).max(1)
+
+
+def as_prec(x, prec):
+    """The inputs as the path sees them (FP32 paths read float copies)."""
+    return np.asarray(x, np.float32).astype(np.float64) if prec != chem.FP64 else x
+
+
+PATHS = [chem.FP64, chem.FP32]
+
+
+@pytest.mark.parametrize("prec", PATHS)
+@pytest.mark.parametrize("size,n", [("h2air_9_21", 1024), ("gri_53_325", 5 * 64 + 37),
+                                    ("heavy_160_1000", 3 * 32 + 5)])
+def test_parity_with_oracle(dev, prec, size, n):
+    m, h, om = loaded(size)
+    T, P, Y = states(m, size, n, seed=77)
+    T, P, Y = as_prec(T, prec), as_prec(P, prec), as_prec(Y, prec)
+    ref = O.source_term(om, T, P, Y)
+    w, _ = run(h, T, P, Y, prec, dev)
+    err = cell_err(w, ref)
+    assert err.max() <= TOL[prec], f"worst cell {err.argmax()} err {err.max():.3e}"
+
+
+@pytest.mark.parametrize("prec", PATHS)
+def test_all_reaction_kinds(dev, prec):
+    """Lindemann, Troe, third-body and irreversible reactions together."""
+    m, h, om = loaded("gri_53_325", seed=5, n_lindemann=6, n_irreversible=25)
+    assert set(np.unique(m.kind)) == {0, 1, 2, 3} and (m.reversible == 0).sum() == 25
+    T, P, Y = states(m, "gri_53_325", 300, seed=3)
+    T, P, Y = as_prec(T, prec), as_prec(P, prec), as_prec(Y, prec)
+    ref = O.source_term(om, T, P, Y)
+    w, _ = run(h, T, P, Y, prec, dev)
+    assert cell_err(w, ref).max() <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PATHS)
+def test_conservation_of_gpu_output(dev, prec):
+    m, h, om = loaded("gri_53_325")
+    T, P, Y = states(m, "gri_53_325", 500, seed=4)
+    w, _ = run(h, T, P, Y, prec, dev)
+    mass = np.abs(w @ m.mol_weight) / (np.abs(w) @ m.mol_weight)
+    E = m.elem_comp.astype(float)
+    el = np.abs(w @ E) / np.maximum(np.abs(w) @ E, 1e-300)
+    bar = 1e-12 if prec == chem.FP64 else 1e-6
+    assert mass.max() < bar and el.max() < bar
+
+
+@pytest.mark.parametrize("prec", PATHS)
+def test_edge_cases(dev, prec):
+    m, h, om = loaded("h2air_9_21")
+    ns = m.n_species
+    T, P, Y = states(m, "h2air_9_21", 70, seed=9)
+    Y = Y.copy()
+    Y[3, 2] = 0.0                      # an absent species
+    Y[5, 4] = -1e-3                    # a negative mass fraction counts as zero
+    Y[7, :] = 0.0                      # an all-zero row: every concentration is zero
+    T, P, Y = as_prec(T, prec), as_prec(P, prec), as_prec(Y, prec)
+    ref = O.source_term(om, T, P, Y)
+    # padded leading dimensions; the padding columns of omega are not written
+    w, pad = run(h, T, P, Y, prec, dev, ldY=ns + 3, ldO=ns + 5)
+    assert np.all(pad == 12345.0)
+    live = np.ones(len(T), bool)
+    live[7] = False
+    assert cell_err(w[live], ref[live]).max() <= TOL[prec]
+    assert np.all(ref[7] == 0.0) and np.all(np.abs(w[7]) < 1e-30)
+    # zero cells: a no-op
+    dt = torch.float64 if prec == chem.FP64 else torch.float32
+    e = torch.empty((0,), dtype=dt, device=dev)
+    chem.source_term(h, e, e, torch.empty((0, ns), dtype=dt, device=dev), prec)
+
+
+def test_argument_errors(dev):
+    m, h, om = loaded("h2air_9_21")
+    T = torch.ones(4, dtype=torch.float64, device=dev)
+    Y = torch.ones((4, m.n_species), dtype=torch.float64, device=dev)
+    L = chem.lib()
+    import ctypes as C
+    rc = L.chem_source_term(h.handle, 4, T.data_ptr(), T.data_ptr(), Y.data_ptr(),
+                            m.n_species - 1, Y.data_ptr(), m.n_species, 0, None)
+    assert rc == 1 and b"ldY" in L.chem_last_error()
+    rc = L.chem_source_term(h.handle, -1, T.data_ptr(), T.data_ptr(), Y.data_ptr(),
+                            m.n_species, Y.data_ptr(), m.n_species, 0, None)
+    assert rc == 1
+    rc = L.chem_source_term(h.handle, 4, T.data_ptr(), T.data_ptr(), Y.data_ptr(),
+                            m.n_species, Y.data_ptr(), m.n_species, 9, None)
+    assert rc == 1
+
+
+@pytest.mark.parametrize("prec", PATHS)
+def test_full_size_sampled(dev, prec):
+    """53 species / 325 reactions at 2^20 cells, the benchmark's launch: sampled cells
+    against the oracle."""
+    m, h, om = loaded("gri_53_325")
+    n = 1 << 20
+    T, P, Y = states(m, "gri_53_325", n, seed=1234)
+    T, P, Y = as_prec(T, prec), as_prec(P, prec), as_prec(Y, prec)
+    w, _ = run(h, T, P, Y, prec, dev)
+    idx = synth.subset_indices(n, 4096)
+    idx = np.concatenate([idx, [0, n - 1]])
+    ref = O.source_term(om, T[idx], P[idx], Y[idx])
+    assert cell_err(w[idx], ref).max() <= TOL[prec]
