@@ -225,7 +225,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "split_bf16", "fp32", "fp64"])
     ap.add_argument("--cpu-budget", type=float, default=10.0)
-    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the secondary precision paths and the CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -299,6 +301,24 @@ def main():
             "roofline": roof, "clocks": clk, "gpu_launches": int(launches)}
 
     # end to end through the C ABI with pinned host buffers
+    if args.no_e2e:
+        line["e2e"] = None
+    else:
+        measure_e2e(line, h, T, P, Y, dev_in, prec, ns, elt, ws, dev, stream, args)
+
+    if rank == 0 and not args.no_extras:
+        extras(line, h, mech, T, P, Y, dev, dev32, out32, ns, prec_name, stream, args)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def measure_e2e(line, h, T, P, Y, dev_in, prec, ns, elt, ws, dev, stream, args):
+    import torch
+    from paper_2008_08483_gb300 import chem
     hostT = torch.as_tensor(T, dtype=dev_in[0].dtype).pin_memory()
     hostP = torch.as_tensor(P, dtype=dev_in[0].dtype).pin_memory()
     hostY = torch.as_tensor(Y, dtype=dev_in[0].dtype).pin_memory()
@@ -317,57 +337,54 @@ def main():
                    "d2h_bytes_per_step": int(elt * N_CELLS * ns), "chunk_cells": chunk,
                    "ms_per_step": ms_e2e}
 
-    if rank == 0 and not args.no_extras:
-        # the other precision paths, same workload (secondary numbers)
-        paths = {}
-        outs = {}
-        for name in ("fp64", "fp32", "split_bf16"):
-            p = chem.PRECISIONS[name]
-            if p == chem.FP64:
-                din = [torch.as_tensor(a, dtype=torch.float64).to(dev) for a in (T, P, Y)]
-                o = torch.empty((N_CELLS, ns), dtype=torch.float64, device=dev)
-            else:
-                din, o = dev32, torch.empty_like(out32)
-            try:
-                fn = (lambda din=din, o=o, p=p: chem.source_term(h, *din, p, out=o, stream=stream))
-                ms_p = time_device(fn, 5 if p == chem.FP64 else 20, 2, stream, 1, dev)
-            except chem.ChemError as e:
-                paths[name] = {"status": str(e)}
-                continue
-            paths[name] = {"cells_per_s": N_CELLS / (ms_p * 1e-3), "ms_per_call": ms_p}
-            outs[name] = o
-            del din
-        # cpu_baseline leg: the oracle on a bounded sample, and each path's error on it
-        rate, ncells, secs, nth, idx, ref = oracle_rate(mech, T.astype(np.float64),
-                                                        P.astype(np.float64),
-                                                        Y.astype(np.float64), args.cpu_budget)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": nth, "kind": "oracle",
-                                "sample": f"first {ncells} cells of the workload ({secs:.1f} s)"}
-        sub = idx[:4096]
-        ref_sub = ref[:4096]
-        for name, o in outs.items():
-            w = o[torch.as_tensor(sub, device=dev)].double().cpu().numpy()
-            if name != "fp64":
-                # FP32-input paths are compared on their own rounded inputs
-                from oracle import oracle as O
-                ref_use = O.source_term(mech, T[sub].astype(np.float32).astype(np.float64),
-                                        P[sub].astype(np.float32).astype(np.float64),
-                                        Y[sub].astype(np.float32).astype(np.float64))
-            else:
-                ref_use = ref_sub
-            err = np.abs(w - ref_use).max(1) / np.abs(ref_use).max(1)
-            paths[name]["err_cell_max"] = float(err.max())
-            paths[name]["err_cell_p999"] = float(np.quantile(err, 0.999))
-            paths[name]["err_global"] = float(np.abs(w - ref_use).max() / np.abs(ref_use).max())
-        if "fp64" in paths and "cells_per_s" in paths.get(prec_name, {}):
-            paths["speedup_vs_fp64"] = paths[prec_name]["cells_per_s"] / paths["fp64"]["cells_per_s"]
-        line["paths"] = paths
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    h.close()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+
+def extras(line, h, mech, T, P, Y, dev, dev32, out32, ns, prec_name, stream, args):
+    import torch
+    from paper_2008_08483_gb300 import chem
+    # the other precision paths, same workload (secondary numbers)
+    paths = {}
+    outs = {}
+    for name in ("fp64", "fp32", "split_bf16"):
+        p = chem.PRECISIONS[name]
+        if p == chem.FP64:
+            din = [torch.as_tensor(a, dtype=torch.float64).to(dev) for a in (T, P, Y)]
+            o = torch.empty((N_CELLS, ns), dtype=torch.float64, device=dev)
+        else:
+            din, o = dev32, torch.empty_like(out32)
+        try:
+            fn = (lambda din=din, o=o, p=p: chem.source_term(h, *din, p, out=o, stream=stream))
+            ms_p = time_device(fn, 5 if p == chem.FP64 else 20, 2, stream, 1, dev)
+        except chem.ChemError as e:
+            paths[name] = {"status": str(e)}
+            continue
+        paths[name] = {"cells_per_s": N_CELLS / (ms_p * 1e-3), "ms_per_call": ms_p}
+        outs[name] = o
+        del din
+    # cpu_baseline leg: the oracle on a bounded sample, and each path's error on it
+    rate, ncells, secs, nth, idx, ref = oracle_rate(mech, T.astype(np.float64),
+                                                    P.astype(np.float64),
+                                                    Y.astype(np.float64), args.cpu_budget)
+    line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": nth, "kind": "oracle",
+                            "sample": f"first {ncells} cells of the workload ({secs:.1f} s)"}
+    sub = idx[:4096]
+    ref_sub = ref[:4096]
+    for name, o in outs.items():
+        w = o[torch.as_tensor(sub, device=dev)].double().cpu().numpy()
+        if name != "fp64":
+            # FP32-input paths are compared on their own rounded inputs
+            from oracle import oracle as O
+            ref_use = O.source_term(mech, T[sub].astype(np.float32).astype(np.float64),
+                                    P[sub].astype(np.float32).astype(np.float64),
+                                    Y[sub].astype(np.float32).astype(np.float64))
+        else:
+            ref_use = ref_sub
+        err = np.abs(w - ref_use).max(1) / np.abs(ref_use).max(1)
+        paths[name]["err_cell_max"] = float(err.max())
+        paths[name]["err_cell_p999"] = float(np.quantile(err, 0.999))
+        paths[name]["err_global"] = float(np.abs(w - ref_use).max() / np.abs(ref_use).max())
+    if "fp64" in paths and "cells_per_s" in paths.get(prec_name, {}):
+        paths["speedup_vs_fp64"] = paths[prec_name]["cells_per_s"] / paths["fp64"]["cells_per_s"]
+    line["paths"] = paths
 
 
 if __name__ == "__main__":

@@ -165,6 +165,14 @@ chem_status chem_source_term_host(const chem_mech *mech, int64_t n_cells, const 
                                   int64_t ldO, chem_precision precision, int64_t chunk_cells,
                                   void *workspace, size_t workspace_bytes, void *stream);
 
+/*
+ * Device-side status of a mechanism's tensor-core kernels.  Every wait inside them is
+ * bounded; a kernel that gives up records a nonzero code (1 tile loader, 2 MMA issuer,
+ * 3 epilogue) and its output is then invalid.  This call synchronises the current
+ * device, returns the code in *code (0: no failure since the last query) and clears it.
+ */
+chem_status chem_device_status(const chem_mech *mech, int32_t *code);
+
 /* Number of kernels this library has launched in the process so far. */
 uint64_t chem_kernel_launch_count(void);
 

@@ -63,8 +63,9 @@ def lib():
             L.chem_source_term_host_workspace.restype = C.c_size_t
             L.chem_source_term_host.argtypes = [P, I64, P, P, P, I64, P, I64, C.c_int, I64, P,
                                                 C.c_size_t, P]
+            L.chem_device_status.argtypes = [P, C.POINTER(I32)]
             for f in (L.chem_mechanism_load, L.chem_mechanism_free, L.chem_mechanism_info,
-                      L.chem_source_term, L.chem_source_term_host):
+                      L.chem_source_term, L.chem_source_term_host, L.chem_device_status):
                 f.restype = C.c_int
             _lib = L
     return _lib
@@ -124,6 +125,12 @@ class Mechanism:
         ns, nr, nb = C.c_int32(), C.c_int32(), C.c_size_t()
         _check(lib().chem_mechanism_info(self.handle, C.byref(ns), C.byref(nr), C.byref(nb)))
         return {"n_species": ns.value, "n_reactions": nr.value, "device_bytes": nb.value}
+
+    def device_status(self) -> int:
+        """Nonzero if a tensor-core kernel gave up on a bounded wait (clears it)."""
+        v = C.c_int32()
+        _check(lib().chem_device_status(self.handle, C.byref(v)))
+        return int(v.value)
 
     def close(self):
         if getattr(self, "_h", None) is not None:

@@ -4,6 +4,7 @@
 using namespace chem;
 
 namespace chem {
+int *bf16_status_word(const chem_mech *m);
 chem_status launch_source_bf16(const chem_mech *m, int64_t n, const float *T, const float *P,
                                const float *Y, int64_t ldY, float *om, int64_t ldO,
                                cudaStream_t s);
@@ -177,5 +178,24 @@ extern "C" chem_status chem_source_term_host(const chem_mech *m, int64_t n, cons
     }
     if (st != CHEM_OK) return st;
     if (e != cudaSuccess) return set_error(CHEM_ECUDA, "host pipeline: %s", cudaGetErrorString(e));
+    return CHEM_OK;
+}
+
+extern "C" chem_status chem_device_status(const chem_mech *m, int32_t *code)
+{
+    clear_error();
+    if (!m || !code) return set_error(CHEM_EINVAL, "NULL argument");
+    *code = 0;
+    chem_status st = check_device(m);
+    if (st != CHEM_OK) return st;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return set_error(CHEM_ECUDA, "synchronize: %s", cudaGetErrorString(e));
+    int *w = bf16_status_word(m);
+    if (!w) return CHEM_OK;
+    int v = 0;
+    e = cudaMemcpy(&v, w, sizeof v, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && v != 0) e = cudaMemset(w, 0, sizeof v);
+    if (e != cudaSuccess) return set_error(CHEM_ECUDA, "status word: %s", cudaGetErrorString(e));
+    *code = v;
     return CHEM_OK;
 }

@@ -92,6 +92,8 @@ struct chem_mech {
 namespace chem {
 
 chem_status set_error(chem_status st, const char *fmt, ...);
+// ln K_c of reaction j in temperature range r on [1, ln T, tau, tau^2, tau^3, tau^4, 1/T]
+void fold_kc(const chem_mech_desc *d, int j, int r, double out[7]);
 void clear_error();
 extern std::atomic<uint64_t> g_launches;
 

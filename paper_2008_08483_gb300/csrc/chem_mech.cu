@@ -144,7 +144,8 @@ static chem_status validate(const chem_mech_desc *d)
 // ln K_c coefficients of reaction j, temperature range r, on [1, ln T, tau, tau^2, tau^3,
 // tau^4, 1/T] (tau = T/1000).  With g/(RT) = a1 (1 - ln T) - a2 T/2 - a3 T^2/6 - a4 T^3/12
 // - a5 T^4/20 + a6/T - a7 and ln K_c = -sum_k nu_k g_k/(RT) + dnu (ln(p_ref/R) - ln T).
-static void fold_kc(const chem_mech_desc *d, int j, int r, double out[7])
+namespace chem {
+void fold_kc(const chem_mech_desc *d, int j, int r, double out[7])
 {
     const int ns = d->n_species;
     double c[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -166,6 +167,7 @@ static void fold_kc(const chem_mech_desc *d, int j, int r, double out[7])
     c[1] -= (double)dnu;
     for (int m = 0; m < 7; ++m) out[m] = c[m];
 }
+}  // namespace chem
 
 extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **out)
 {

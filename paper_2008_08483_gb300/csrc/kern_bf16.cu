@@ -1,15 +1,1008 @@
-// kern_bf16.cu -- split-BF16 tensor-core source term (tcgen05).  Not built yet.
+// kern_bf16.cu -- split-BF16 source term on tcgen05 tensor cores (sm_103a).
+//
+// Per tile of 128 cells (one cell per tensor-memory lane), for reaction chunks of RC:
+//   contraction 1 (Eqs. 4, 11): S = log2 X . [nu' | nu''] (M=128, N=2 RC, K=NSP), and the
+//       reverse half also accumulates G . nu, the Gibbs layer of Eq. 11 (G_k = g_k/(RT) log2 e
+//       - log2(p_ref/(RT)), per cell and species, three BF16 terms in tensor memory; nu is
+//       contraction 2's table read as an MN-major operand), so that S'' + log2 k_f =
+//       sum_k nu''_k log2 C_k + log2 k_r
+//       A = log2 X in tensor memory as three BF16 terms (hi + mid + lo); the extra
+//       column NSP_extra = log2 c_tot carries the reaction orders (and the third-body
+//       c_tot factor), so S = sum_k nu_k log2 C_k (+ log2 c_tot for third-body).
+//       B = the small-integer stoichiometric matrices, exact in BF16, in shared memory.
+//   epilogue (FP32, one thread per cell): log2 k_f (Eq. 6), log2 k_r = log2 k_f -
+//       log2 K_c from the Gibbs layer folded through nu in FP64 at load (Eqs. 9-11),
+//       third-body / falloff factors (Sec. 2.4), q = 2^(S + log2 k), q_net = q_f - q_r
+//       (Eq. 3), split into two BF16 terms written to tensor memory.
+//   contraction 2 (Eq. 2):  omega += q_net . nu^T          (M=128, N=NSP, K=RC)
+// omega accumulates in tensor memory across the chunks and is written once per tile.
+//
+// Warp roles (576 threads): warp 0 bulk-copies the T, P, Y tile into shared memory;
+// warp 1 owns tensor memory and issues every MMA from one thread; warps 2-17 form four
+// epilogue warpgroups: warpgroups 0-1 take the even chunks and 2-3 the odd ones, each
+// warpgroup of a pair handling half of the chunk's reactions (warp w reaches tensor-memory
+// lanes 32 (w % 4) .. 32 (w % 4) + 31).  Per-reaction coefficients live in shared memory;
+// third-body and falloff factors are computed out of line.
+// Every mbarrier wait is bounded: on timeout the kernel records an error code in the
+// mechanism's device status word and all roles wind down.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
 #include "chem_internal.h"
+#include "tc_ptx.h"
 
 namespace chem {
 
-chem_status bf16_build_tables(chem_mech *, const chem_mech_desc *) { return CHEM_EUNSUPPORTED; }
-void bf16_free_tables(void *) {}
+constexpr int RC = 32;                 // reactions per chunk
+constexpr int RH = RC / 2;             // reactions per warpgroup and chunk
+constexpr int kEpiWarp0 = 2;           // first epilogue warp
+constexpr int kEpiWarps = 16;
+constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);
+constexpr uint32_t kTmemCols = 512;
+constexpr float kLog2Floor = -1000.0f; // log2 X of an absent species: 2^x underflows to 0
+constexpr float kDead = -1.0e4f;       // log2 of a rate constant that is zero
+constexpr int kTbList = 8;             // third-body efficiency entries per reaction (padded)
 
-chem_status launch_source_bf16(const chem_mech *, int64_t, const float *, const float *,
-                               const float *, int64_t, float *, int64_t, cudaStream_t)
+// per-reaction coefficients, copied to shared memory with the stoichiometric tables
+struct alignas(16) CoefS {
+    float4 kf;         // Arrhenius layer (Eq. 6): log2 k_inf = x + y log2 T + z / T;
+                       // w = reaction kind (int bits)
+    int4 meta;         // third-body list begin, end; falloff record; unused
+};
+// per species: G_k = g_k/(RT) log2 e - log2(p_ref/(RT)) on [1, log2 T, tau, tau^2, tau^3,
+// tau^4, 1/T] (tau = T/1000), one set per temperature range (Eq. 10 with the standard
+// concentration folded into the bias as in Eq. 11)
+struct alignas(16) GibbsS {
+    float c[2][8];
+};
+struct alignas(16) FallBF {
+    float4 k0;         // log2 k0 = x + y log2 T + z / T
+    float4 troe;       // 1 - alpha, alpha, log2(e)/T***, log2(e)/T*
+    float4 t2;         // x = log2(e) T** (<= 0: absent)
+};
+
+struct Bf16Tables {
+    int nsp, nch, nfall, ntb, nfac;
+    size_t b1_bytes, b2_bytes, tab_bytes;        // tab = everything after B1 | B2
+    uint32_t o_coef, o_hmask, o_fall, o_tbe, o_tbsp, o_gib;   // offsets from the blob start
+    void *d_blob;
+    const uint16_t *btab;     // one contiguous block copied to shared memory
+    const float *invW;
+    int *status;
+};
+
+struct Bf16Params {
+    const float *T, *P, *Y;
+    float *om;
+    int64_t n, ldY, ldO;
+    int ns, nch, ntiles, nfac;
+    int stage_y;
+    const uint16_t *btab;
+    uint32_t blob_bytes;
+    const float *invW;
+    float t_mid, lg2R;
+    int *status;
+    // shared-memory layout (byte offsets from the 1024-aligned base); the copied block
+    // holds B1, B2, coefficients, third-body masks, falloff records and third-body lists
+    uint32_t o_b2, o_coef, o_hmask, o_fall, o_tbe, o_tbsp, o_gib, o_y, o_t, o_p, o_xw, o_iw, o_psum,
+        o_bar;
+    int bulk_out;              // omega rows contiguous (ldO == ns) and 16-byte aligned
+};
+
+enum {
+    BAR_BTAB, BAR_YFULL, BAR_YEMPTY, BAR_A1FULL, BAR_D1FULL0, BAR_D1FULL1, BAR_D1EMPTY0,
+    BAR_D1EMPTY1, BAR_A2FULL0, BAR_A2FULL1, BAR_A2EMPTY0, BAR_A2EMPTY1, BAR_D2FULL, BAR_D2EMPTY,
+    BAR_XREADY, BAR_WREADY, BAR_STDONE, BAR_DRAIN, BAR_FREADY, BAR_COUNT
+};
+
+struct SmemCtl {
+    uint32_t tmem_base;
+    volatile int abort;
+};
+
+// Bounded mbarrier wait: gives up after ~2^31 cycles (about a second), or as soon as
+// another role has given up, recording `code` in the device status word.
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, SmemCtl *ctl, int *status,
+                                         int code)
 {
-    return set_error(CHEM_EUNSUPPORTED, "split-BF16 path not built");
+    if (tc::mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (tc::mbar_try_wait_sleep(bar, parity, 20000)) return true;
+        if (ctl->abort) return false;
+        if (clock64() - t0 > (1ll << 31)) {
+            ctl->abort = 1;
+            atomicCAS(status, 0, code);
+            return false;
+        }
+    }
+}
+
+template <int NSP>
+struct Cols {                                     // tensor-memory column map
+    static constexpr uint32_t A1 = 0;             // log2 z: 3 splits x NSP/2 columns
+    static constexpr uint32_t AG = ((3 * NSP / 2 + 31) / 32) * 32;   // G: 3 splits x NSP/2
+    static constexpr uint32_t D1 = AG + ((3 * NSP / 2 + 31) / 32) * 32;   // 2 buffers x 2 RC
+    static constexpr uint32_t A2 = D1 + 4 * RC;   // 2 buffers x (2 splits x RC/2)
+    static constexpr uint32_t D2 = A2 + 2 * RC;   // NSP columns
+    static constexpr uint32_t FC = D2 + NSP;      // third-body / falloff multipliers
+    static constexpr int kMaxFactors = (int)(kTmemCols - FC);
+    static_assert(kMaxFactors >= 16, "tensor memory over budget");
+};
+
+// Per-cell features kept in registers by every epilogue thread.
+struct CellF {
+    float lg2T, invT, tau, tau2, lgct, inv_sum;
+    int rg;
+};
+
+// Shared-memory view of the per-reaction tables.
+struct SmemTabs {
+    const CoefS *coef;
+    const uint32_t *hmask;     // per half chunk: bit r set if reaction r needs a factor
+    const uint32_t *lmask;     // per half chunk: bit r set if slot r holds a reaction
+    const uint32_t *rmask;     // per half chunk: bit r set if reaction r is reversible
+    const int *fbase;          // per half chunk: multiplier column of its first flagged slot
+    const int *fslot;          // per multiplier, kind-sorted: reaction slot
+    const int *fcol;           // per multiplier, kind-sorted: tensor-memory column
+    const FallBF *fall;
+    const float *tbe;          // efficiency - 1 of the listed third-body species
+    const uint16_t *tbsp;
+};
+
+// Multipliers of q_net for four third-body (M / c_tot) or falloff (Pr / (1 + Pr) F)
+// reactions, Sec. 2.4, evaluated together so their dependency chains interleave.  The
+// c_tot part of a third-body factor is already in the contraction.  Third-body lists hold
+// kTbList (species, efficiency - 1) entries, padded with zero efficiencies.
+__device__ __forceinline__ void tb_factor4(const SmemTabs &tb, const int (&slot)[4], bool falloff,
+                                           const CellF &c, const float *Xs, int row, float (&out)[4])
+{
+    float s[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int t0 = tb.coef[slot[u]].meta.x;
+        float sz = 0.0f;                          // M / c_tot = 1 + sum_k (eff_k - 1) X_k,
+#pragma unroll
+        for (int t = 0; t < kTbList; ++t)         // X_k = z_k / sum_k z_k
+            sz = fmaf(tb.tbe[t0 + t], Xs[(int)tb.tbsp[t0 + t] * 128 + row], sz);
+        s[u] = fmaf(sz, c.inv_sum, 1.0f);
+        out[u] = s[u];
+    }
+    if (!falloff) return;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const CoefS &C = tb.coef[slot[u]];
+        if (__float_as_int(C.kf.w) < 2) continue;    // third-body entry: out[u] = M / c_tot
+        const FallBF &F = tb.fall[C.meta.z];
+        const float lkf = fmaf(C.kf.z, c.invT, fmaf(C.kf.y, c.lg2T, C.kf.x));
+        const float lk0 = fmaf(F.k0.z, c.invT, fmaf(F.k0.y, c.lg2T, F.k0.x));
+        const float lpr = lk0 - lkf + c.lgct + tc::lg2(s[u]);      // log2 Pr
+        float fac = -tc::lg2(1.0f + tc::ex2(-lpr));               // log2(Pr / (1 + Pr))
+        if (__float_as_int(C.kf.w) == 3) {
+            const float Tn = c.tau * 1000.0f;
+            float fc = F.troe.x * tc::ex2(-Tn * F.troe.z) + F.troe.y * tc::ex2(-Tn * F.troe.w);
+            if (F.t2.x > 0.0f) fc += tc::ex2(-F.t2.x * c.invT);
+            const float lfc = tc::lg2(fc);        // log2 F_cent
+            const float l10 = lfc * 0.30102999566398120f;
+            const float cc = -0.4f - 0.67f * l10, nn = 0.75f - 1.27f * l10;
+            const float x = lpr * 0.30102999566398120f + cc;
+            const float f1 = __fdividef(x, nn - 0.14f * x);
+            fac += __fdividef(lfc, 1.0f + f1 * f1);   // log2 F (Troe)
+        }
+        out[u] = tc::ex2(fac);
+    }
+}
+
+// q_net of one reaction for one cell before any third-body / falloff factor (Eqs. 3-7),
+// log2 domain: the contraction already holds sum nu' log2 C and sum nu'' log2 C - log2 K_c.
+__device__ __forceinline__ float rate_plain(const CoefS *C, float sf, float sr, bool rev,
+                                            const CellF &c)
+{
+    const float4 kf = C->kf;
+    const float lkf = fmaf(kf.z, c.invT, fmaf(kf.y, c.lg2T, kf.x));
+    const float qf = tc::ex2(sf + lkf);
+    return rev ? qf - tc::ex2(sr + lkf) : qf;
+}
+
+// two values -> three packed BF16x2 words (hi, mid, lo terms; value a in the low halves)
+__device__ __forceinline__ void split3x2(float a, float b, uint32_t &h, uint32_t &m, uint32_t &l)
+{
+    h = tc::pack_bf16x2(a, b);
+    const float a1 = a - __uint_as_float(h << 16), b1 = b - __uint_as_float(h & 0xFFFF0000u);
+    m = tc::pack_bf16x2(a1, b1);
+    const float a2 = a1 - __uint_as_float(m << 16), b2 = b1 - __uint_as_float(m & 0xFFFF0000u);
+    l = tc::pack_bf16x2(a2, b2);
+}
+
+__device__ __forceinline__ void split3(float x, uint16_t &h, uint16_t &m, uint16_t &l)
+{
+    // x = hi + mid + lo with each term the nearest BF16 of the remaining residual
+    const uint32_t ph = tc::pack_bf16x2(x, 0.0f) & 0xFFFFu;
+    const float r1 = x - __uint_as_float(ph << 16);
+    const uint32_t pm = tc::pack_bf16x2(r1, 0.0f) & 0xFFFFu;
+    const float r2 = r1 - __uint_as_float(pm << 16);
+    const uint32_t pl = tc::pack_bf16x2(r2, 0.0f) & 0xFFFFu;
+    h = (uint16_t)ph;
+    m = (uint16_t)pm;
+    l = (uint16_t)pl;
+}
+
+template <int NSP>
+__global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
+{
+    using CL = Cols<NSP>;
+    constexpr int SQ = NSP / 4;                   // species columns per warpgroup
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned base, offset on the shared array itself so that every access below
+    // stays a shared-memory access (an integer round trip would make them generic)
+    unsigned char *sm = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+    const uint32_t sbase = tc::smem_u32(sm);
+    SmemTabs tabs;
+    tabs.coef = (const CoefS *)(sm + p.o_coef);
+    tabs.hmask = (const uint32_t *)(sm + p.o_hmask);
+    tabs.lmask = tabs.hmask + 2 * p.nch;
+    tabs.rmask = tabs.hmask + 4 * p.nch;
+    tabs.fbase = (const int *)(tabs.hmask + 6 * p.nch);
+    tabs.fslot = tabs.fbase + 2 * p.nch;
+    tabs.fcol = tabs.fslot + p.nfac;
+    const GibbsS *gib = (const GibbsS *)(sm + p.o_gib);
+    tabs.fall = (const FallBF *)(sm + p.o_fall);
+    tabs.tbe = (const float *)(sm + p.o_tbe);
+    tabs.tbsp = (const uint16_t *)(sm + p.o_tbsp);
+    float *Ys = (float *)(sm + p.o_y);
+    float *Ts = (float *)(sm + p.o_t);
+    float *Ps = (float *)(sm + p.o_p);
+    float *Xs = (float *)(sm + p.o_xw);           // X [species][128] while the chunks run
+    float *Ws = (float *)(sm + p.o_xw);           // omega [128][ns] while the tile is stored
+    float *iW = (float *)(sm + p.o_iw);
+    float *Psum = (float *)(sm + p.o_psum);      // [4][128] partial sums of z_k per warpgroup
+    uint64_t *bars = (uint64_t *)(sm + p.o_bar);
+    SmemCtl *ctl = (SmemCtl *)(bars + BAR_COUNT);
+    auto BAR = [&](int i) { return tc::smem_u32(bars + i); };
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        const uint32_t cnt[BAR_COUNT] = {1, 1, 16, 16, 1, 1, 8, 8, 8, 8, 1, 1, 1, 16, 16, 16, 16, 1, 16};
+        for (int i = 0; i < BAR_COUNT; ++i) tc::mbar_init(BAR(i), cnt[i]);
+        tc::mbar_fence_init();
+        ctl->abort = 0;
+    }
+    for (int k = tid; k < p.ns; k += kThreads) iW[k] = p.invW[k];
+    if (warp == 1) {
+        tc::tmem_alloc(tc::smem_u32(&ctl->tmem_base), kTmemCols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = ctl->tmem_base;
+    const int64_t n = p.n;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------- tile loader
+        if (lane == 0) {
+            const uint32_t bt = p.blob_bytes;
+            tc::mbar_arrive_expect_tx(BAR(BAR_BTAB), bt);
+            for (uint32_t off = 0; off < bt; off += 16384)
+                tc::bulk_g2s(sbase + off, (const unsigned char *)p.btab + off,
+                             min(16384u, bt - off), BAR(BAR_BTAB));
+            int it = 0;
+            bool pending = false;
+            for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++it) {
+                if (!wait_bar(BAR(BAR_YEMPTY), (it & 1) ^ 1, ctl, p.status, 1)) break;
+                const int64_t i0 = (int64_t)t * 128;
+                if (p.stage_y && i0 + 128 <= n) {
+                    const uint32_t yb = (uint32_t)(128 * p.ldY * 4);
+                    tc::mbar_arrive_expect_tx(BAR(BAR_YFULL), yb + 1024);
+                    tc::bulk_g2s(sbase + p.o_y, p.Y + i0 * p.ldY, yb, BAR(BAR_YFULL));
+                    tc::bulk_g2s(sbase + p.o_t, p.T + i0, 512, BAR(BAR_YFULL));
+                    tc::bulk_g2s(sbase + p.o_p, p.P + i0, 512, BAR(BAR_YFULL));
+                    pending = true;
+                } else {
+                    tc::mbar_arrive(BAR(BAR_YFULL));
+                    pending = false;
+                }
+            }
+            // copies in flight are awaited before the CTA can exit
+            if (pending) wait_bar(BAR(BAR_YFULL), (it - 1) & 1, ctl, p.status, 1);
+            wait_bar(BAR(BAR_BTAB), 0, ctl, p.status, 1);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t id1 = tc::idesc_bf16_f32(128, 2 * RC);
+            constexpr uint32_t id2 = tc::idesc_bf16_f32(128, NSP);
+            const uint32_t b1 = sbase, b2 = sbase + p.o_b2;
+            uint32_t u_d1[2] = {0, 0}, u_a2[2] = {0, 0};
+            bool ok = wait_bar(BAR(BAR_BTAB), 0, ctl, p.status, 2);
+            constexpr uint32_t id1g = tc::idesc_bf16_f32(128, RC, true);
+            auto issue_mma1 = [&](int c) {
+                const int b = c & 1;
+                const uint32_t bc = b1 + (uint32_t)c * (2 * RC * NSP * 2);
+#pragma unroll
+                for (int s = 0; s < 3; ++s)
+#pragma unroll
+                    for (int kk = 0; kk < NSP / 16; ++kk)
+                        tc::mma_ts(tmem + CL::D1 + b * 2 * RC, tmem + CL::A1 + s * (NSP / 2) + kk * 8,
+                                   tc::sdesc_noswz(bc + kk * 256, 128, (NSP / 8) * 128), id1,
+                                   (s | kk) != 0);
+                // Gibbs layer into the reverse half: B = nu of contraction 2 ([species][reaction]
+                // core matrices) read MN-major: K step = 2 species core rows, lbo = K stride
+                const uint32_t bg = b2 + (uint32_t)c * (NSP * RC * 2);
+#pragma unroll
+                for (int s = 0; s < 3; ++s)
+#pragma unroll
+                    for (int kk = 0; kk < NSP / 16; ++kk)
+                        tc::mma_ts(tmem + CL::D1 + b * 2 * RC + RC,
+                                   tmem + CL::AG + s * (NSP / 2) + kk * 8,
+                                   tc::sdesc_noswz(bg + kk * 2 * (RC / 8) * 128, (RC / 8) * 128, 128),
+                                   id1g, 1);
+                tc::commit(BAR(BAR_D1FULL0 + b));
+                ++u_d1[b];
+            };
+            auto mma2 = [&](int c) {
+                const int b = c & 1;
+                const uint32_t bc = b2 + (uint32_t)c * (NSP * RC * 2);
+#pragma unroll
+                for (int s = 0; s < 2; ++s)
+#pragma unroll
+                    for (int kk = 0; kk < RC / 16; ++kk)
+                        tc::mma_ts(tmem + CL::D2, tmem + CL::A2 + b * RC + s * (RC / 2) + kk * 8,
+                                   tc::sdesc_noswz(bc + kk * 256, 128, (RC / 8) * 128), id2,
+                                   (c | s | kk) != 0);
+                tc::commit(BAR(BAR_A2EMPTY0 + b));
+                ++u_a2[b];
+                if (c == p.nch - 1) tc::commit(BAR(BAR_D2FULL));
+            };
+            int it = 0;
+            for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x, ++it) {
+                if (!(ok = wait_bar(BAR(BAR_A1FULL), it & 1, ctl, p.status, 2))) break;
+                tc::fence_after();
+                // Issue whatever is ready: contraction 1 into either tensor-memory buffer as
+                // soon as its epilogue pair has read it, contraction 2 strictly in chunk order
+                // (the omega accumulation order, hence the rounding, is fixed).
+                int c1[2] = {0, 1}, c2 = 0;
+                bool d2_free = false;
+                long long t0 = clock64();
+                while (c2 < p.nch) {
+                    bool prog = false;
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) {
+                        if (c1[b] < p.nch &&
+                            tc::mbar_test_wait(BAR(BAR_D1EMPTY0 + b), (u_d1[b] & 1) ^ 1)) {
+                            tc::fence_after();
+                            issue_mma1(c1[b]);
+                            c1[b] += 2;
+                            prog = true;
+                        }
+                    }
+                    if (!d2_free) d2_free = tc::mbar_test_wait(BAR(BAR_D2EMPTY), (it & 1) ^ 1);
+                    const int b2c = c2 & 1;
+                    if (d2_free && tc::mbar_test_wait(BAR(BAR_A2FULL0 + b2c), u_a2[b2c] & 1)) {
+                        tc::fence_after();
+                        mma2(c2);
+                        ++c2;
+                        prog = true;
+                    }
+                    if (prog) {
+                        t0 = clock64();
+                    } else if (clock64() - t0 < (1ll << 31) && !ctl->abort) {
+                        __nanosleep(100);               // back off: the epilogue warps share this SM
+                    } else if (ctl->abort || clock64() - t0 > (1ll << 31)) {
+                        ctl->abort = 1;
+                        atomicCAS(p.status, 0, 2);
+                        ok = false;
+                        break;
+                    }
+                }
+            }
+            // every MMA issued has completed before tensor memory is released
+            tc::commit(BAR(BAR_DRAIN));
+            wait_bar(BAR(BAR_DRAIN), 0, ctl, p.status, 2);
+        }
+    } else {
+        // ------------------------------------------------------------- epilogue
+        const int ew = warp - kEpiWarp0;             // 0..15
+        const int g = ew >> 2;                        // warpgroup 0..3
+        const int pr = g >> 1;                        // chunk parity of this warpgroup pair
+        const int hf = g & 1;                         // half of the chunk's reactions
+        const int q = warp & 3;                       // lane quarter of tensor memory
+        const int row = q * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        const int ns = p.ns;
+        int it = 0, u = 0;
+        bool ok = wait_bar(BAR(BAR_BTAB), 0, ctl, p.status, 3);   // coefficients in smem
+        for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x, ++it) {
+            const int64_t i0 = (int64_t)t * 128;
+            const int64_t ci = i0 + row;
+            const bool full = p.stage_y && i0 + 128 <= n;
+            if (!(ok = wait_bar(BAR(BAR_YFULL), it & 1, ctl, p.status, 3))) break;
+            // the previous tile's omega has left the shared buffer that X reuses
+            if (it > 0 && !(ok = wait_bar(BAR(BAR_STDONE), (it - 1) & 1, ctl, p.status, 3))) break;
+            // ---- prologue: features, X and split log2 X (Eq. 4 input layer)
+            float Tc = 1000.0f, Pc = 1.0e6f;
+            const float *yrow = nullptr;
+            if (full) {
+                Tc = Ts[row];
+                Pc = Ps[row];
+                yrow = Ys + (int64_t)row * p.ldY;
+            } else if (ci < n) {
+                Tc = __ldg(p.T + ci);
+                Pc = __ldg(p.P + ci);
+                yrow = p.Y + ci * p.ldY;
+            }
+            CellF cf;
+            cf.lg2T = log2f(Tc);
+            cf.invT = 1.0f / Tc;
+            cf.tau = Tc * 1e-3f;
+            cf.tau2 = cf.tau * cf.tau;
+            cf.rg = Tc >= p.t_mid ? 1 : 0;
+            cf.lgct = log2f(Pc) - p.lg2R - cf.lg2T;
+            // This warpgroup's quarter of the species columns: z_k = Y_k / W_k, whose log2
+            // goes to the contraction; X_k = z_k / sum_k z_k is completed by the column
+            // ns + 1 below (log2 c_tot - log2 sum, weighted by the reaction order).
+            float psum = 0.0f;
+            uint32_t wh[SQ / 2], wm[SQ / 2], wl[SQ / 2];   // log2 z, three BF16 terms
+            uint32_t gh[SQ / 2], gm[SQ / 2], gl[SQ / 2];   // G, three BF16 terms
+#pragma unroll
+            for (int e = 0; e < SQ / 2; ++e) {
+                float lx[2], gk[2];
+#pragma unroll
+                for (int hlf = 0; hlf < 2; ++hlf) {
+                    const int k = g * SQ + 2 * e + hlf;
+                    lx[hlf] = 0.0f;
+                    gk[hlf] = 0.0f;
+                    if (k < ns) {
+                        const float z = yrow ? fmaxf(yrow[k], 0.0f) * iW[k] : 0.0f;
+                        psum += z;
+                        Xs[k * 128 + row] = z;
+                        lx[hlf] = fmaxf(tc::lg2(z), kLog2Floor);
+                        // Gibbs layer (Eq. 10) for this species at this cell's temperature
+                        const float4 g0 = *(const float4 *)&gib[k].c[cf.rg][0];
+                        const float4 g1 = *(const float4 *)&gib[k].c[cf.rg][4];
+                        const float pt = fmaf(fmaf(fmaf(g1.y, cf.tau, g1.x), cf.tau, g0.w), cf.tau, g0.z);
+                        gk[hlf] = fmaf(pt, cf.tau, fmaf(g1.z, cf.invT, fmaf(g0.y, cf.lg2T, g0.x)));
+                    } else if (k == ns) {
+                        lx[hlf] = cf.lgct;            // third-body c_tot column
+                    }
+                }
+                split3x2(lx[0], lx[1], wh[e], wm[e], wl[e]);
+                split3x2(gk[0], gk[1], gh[e], gm[e], gl[e]);
+            }
+            const uint32_t a1 = tmem + lane_off + CL::A1 + g * (SQ / 2);
+            const uint32_t ag = tmem + lane_off + CL::AG + g * (SQ / 2);
+            if constexpr (SQ / 2 == 8) {
+                tc::tmem_st8(a1 + 0 * (NSP / 2), wh);
+                tc::tmem_st8(a1 + 1 * (NSP / 2), wm);
+                tc::tmem_st8(a1 + 2 * (NSP / 2), wl);
+                tc::tmem_st8(ag + 0 * (NSP / 2), gh);
+                tc::tmem_st8(ag + 1 * (NSP / 2), gm);
+                tc::tmem_st8(ag + 2 * (NSP / 2), gl);
+            } else {
+                static_assert(SQ / 2 == 4, "warpgroup species quarter of 8 or 16 columns");
+                tc::tmem_st4(a1 + 0 * (NSP / 2), wh);
+                tc::tmem_st4(a1 + 1 * (NSP / 2), wm);
+                tc::tmem_st4(a1 + 2 * (NSP / 2), wl);
+                tc::tmem_st4(ag + 0 * (NSP / 2), gh);
+                tc::tmem_st4(ag + 1 * (NSP / 2), gm);
+                tc::tmem_st4(ag + 2 * (NSP / 2), gl);
+            }
+            tc::tmem_wait_st();
+            Psum[g * 128 + row] = psum;
+            __syncwarp();
+            if (lane == 0) {
+                tc::mbar_arrive(BAR(BAR_YEMPTY));
+                tc::mbar_arrive(BAR(BAR_XREADY));
+            }
+            if (!(ok = wait_bar(BAR(BAR_XREADY), it & 1, ctl, p.status, 3))) break;
+            {
+                const float sum = Psum[row] + Psum[128 + row] + Psum[256 + row] + Psum[384 + row];
+                cf.inv_sum = sum > 0.0f ? 1.0f / sum : 0.0f;
+                const int kn = ns + 1;                    // normalisation column
+                if (kn / SQ == g) {
+                    // the packed word holding column kn; its other half is column kn - 1
+                    // (= ns, log2 c_tot) or kn + 1 (padding, zero)
+                    const float other = (kn & 1) ? cf.lgct : 0.0f;
+                    const float vn = sum > 0.0f ? cf.lgct - log2f(sum) : 0.0f;
+                    uint16_t ho, mo, lo_, hn, mn, ln;
+                    split3(other, ho, mo, lo_);
+                    split3(vn, hn, mn, ln);
+                    auto pk = [&](uint16_t o, uint16_t nn) {
+                        return (kn & 1) ? ((uint32_t)o | ((uint32_t)nn << 16))
+                                        : ((uint32_t)nn | ((uint32_t)o << 16));
+                    };
+                    const uint32_t col = tmem + lane_off + CL::A1 + kn / 2;
+                    tc::tmem_st1(col + 0 * (NSP / 2), pk(ho, hn));
+                    tc::tmem_st1(col + 1 * (NSP / 2), pk(mo, mn));
+                    tc::tmem_st1(col + 2 * (NSP / 2), pk(lo_, ln));
+                }
+                tc::tmem_wait_st();
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(BAR(BAR_A1FULL));
+                // Third-body / falloff multipliers of this tile, a quarter per warpgroup, while
+                // the first contractions run.  They are read after this warp's own wait for
+                // contraction 1, which orders them after every warp's A1FULL arrival below.
+                // warpgroup g takes entries g, g + 4, g + 8, ... of the kind-sorted list
+                const int n_g = (p.nfac - g + 3) / 4;
+                for (int i0 = 0; i0 < n_g; i0 += 4) {
+                    int sl[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) sl[u] = tabs.fslot[g + 4 * min(i0 + u, n_g - 1)];
+                    bool fall = false;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        fall |= __float_as_int(tabs.coef[sl[u]].kf.w) >= 2;
+                    float v[4];
+                    tb_factor4(tabs, sl, fall, cf, Xs, row, v);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (i0 + u < n_g)
+                            tc::tmem_st1(tmem + lane_off + CL::FC + tabs.fcol[g + 4 * (i0 + u)],
+                                         __float_as_uint(v[u]));
+                }
+                tc::tmem_wait_st();
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(BAR(BAR_FREADY));
+            }
+            if (!(ok = wait_bar(BAR(BAR_FREADY), it & 1, ctl, p.status, 3))) break;
+            tc::fence_after();
+            // ---- this pair's chunks, this warpgroup's half of each
+            for (int c = pr; c < p.nch; c += 2, ++u) {
+                if (!(ok = wait_bar(BAR(BAR_D1FULL0 + pr), u & 1, ctl, p.status, 3))) break;
+                tc::fence_after();
+                uint32_t sf[RH], sr[RH];
+                const uint32_t d1 = tmem + lane_off + CL::D1 + pr * 2 * RC + hf * RH;
+                tc::tmem_ld16(d1, sf);
+                tc::tmem_ld16(d1 + RC, sr);
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(BAR(BAR_D1EMPTY0 + pr));
+                const int j0 = c * RC + hf * RH;
+                const uint32_t lm = tabs.lmask[c * 2 + hf], rm = tabs.rmask[c * 2 + hf];
+                float q[RH];
+#pragma unroll
+                for (int r = 0; r < RH; ++r)
+                    q[r] = ((lm >> r) & 1u) ? rate_plain(tabs.coef + j0 + r, __uint_as_float(sf[r]),
+                                                        __uint_as_float(sr[r]), (rm >> r) & 1u, cf)
+                                            : 0.0f;
+                const uint32_t hm = tabs.hmask[c * 2 + hf];
+                if (hm) {
+                    // the (at most 4) multipliers of this half chunk are consecutive columns
+                    const int fb = tabs.fbase[c * 2 + hf];
+                    const int lb = min(fb, CL::kMaxFactors - 8);
+                    uint32_t fv[8];
+                    tc::tmem_ld8(tmem + lane_off + CL::FC + lb, fv);
+#pragma unroll
+                    for (int r = 0; r < RH; ++r) {
+                        if ((hm >> r) & 1u) {
+                            const int pos = __popc(hm & ((1u << r) - 1u)) + fb - lb;
+                            uint32_t w = fv[0];
+#pragma unroll
+                            for (int e = 1; e < 8; ++e) w = pos == e ? fv[e] : w;
+                            q[r] *= __uint_as_float(w);
+                        }
+                    }
+                }
+                uint32_t hw[RH / 2], lw[RH / 2];
+#pragma unroll
+                for (int r = 0; r < RH; r += 2) {
+                    const uint32_t h = tc::pack_bf16x2(q[r], q[r + 1]);
+                    const float r0 = q[r] - __uint_as_float(h << 16);
+                    const float r1 = q[r + 1] - __uint_as_float(h & 0xFFFF0000u);
+                    hw[r / 2] = h;
+                    lw[r / 2] = tc::pack_bf16x2(r0, r1);
+                }
+                if (!(ok = wait_bar(BAR(BAR_A2EMPTY0 + pr), (u & 1) ^ 1, ctl, p.status, 3))) break;
+                tc::fence_after();
+                const uint32_t a2 = tmem + lane_off + CL::A2 + pr * RC + hf * (RH / 2);
+                tc::tmem_st8(a2, hw);
+                tc::tmem_st8(a2 + RC / 2, lw);
+                tc::tmem_wait_st();
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(BAR(BAR_A2FULL0 + pr));
+            }
+            if (!ok) break;
+            // ---- omega of the tile: tensor memory -> shared -> global (coalesced)
+            if (!(ok = wait_bar(BAR(BAR_D2FULL), it & 1, ctl, p.status, 3))) break;
+            tc::fence_after();
+            {
+                uint32_t w[SQ];
+                const uint32_t d2 = tmem + lane_off + CL::D2 + g * SQ;
+                if constexpr (SQ == 16) tc::tmem_ld16(d2, w);
+                else tc::tmem_ld8(d2, w);
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(BAR(BAR_D2EMPTY));
+#pragma unroll
+                for (int e = 0; e < SQ; ++e) {
+                    const int k = g * SQ + e;
+                    if (k < ns) Ws[row * ns + k] = __uint_as_float(w[e]);
+                }
+            }
+            tc::fence_proxy_async_smem();            // visible to the bulk store
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(BAR(BAR_WREADY));
+            if (!(ok = wait_bar(BAR(BAR_WREADY), it & 1, ctl, p.status, 3))) break;
+            if (p.bulk_out && i0 + 128 <= n) {
+                // one bulk store of the tile; the shared buffer is reused after it is read
+                if (ew == 0 && lane == 0) {
+                    tc::bulk_s2g(p.om + i0 * p.ldO, sbase + p.o_xw, (uint32_t)(128 * ns * 4));
+                    tc::bulk_commit();
+                    tc::bulk_wait_read0();
+                }
+            } else {
+                for (int r = ew; r < 128; r += kEpiWarps) {
+                    const int64_t i = i0 + r;
+                    if (i >= n) break;
+                    float *orow = p.om + i * p.ldO;
+                    for (int k = lane; k < ns; k += 32) orow[k] = Ws[r * ns + k];
+                }
+            }
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(BAR(BAR_STDONE));
+        }
+    }
+    if (warp == kEpiWarp0 && lane == 0) tc::bulk_wait0();   // omega stores have landed
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// host side: tables, launch
+// ---------------------------------------------------------------------------------------
+
+static uint16_t bf16_of_int(int v)
+{
+    float f = (float)v;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return (uint16_t)(u >> 16);              // exact for |v| <= 256
+}
+
+chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
+{
+    const int ns = d->n_species, nr = d->n_reactions;
+    // columns: species 0..ns-1, then log2 c_tot (third-body factor) and the
+    // normalisation column log2 c_tot - log2 sum_k z_k (weighted by the reaction order)
+    int nsp = ((ns + 2 + 15) / 16) * 16;
+    if (nsp <= 32) nsp = 32;
+    else if (nsp <= 64) nsp = 64;
+    else return set_error(CHEM_EUNSUPPORTED, "split-BF16 path supports up to 62 species");
+    // an even number of chunks keeps both epilogue warpgroup pairs equally busy
+    int nch = (nr + RC - 1) / RC;
+    if (nch > 1 && (nch & 1)) ++nch;
+    const int nrp = nch * RC;
+    // Reactions that need a third-body or falloff factor are spread evenly over the
+    // reaction sequence, and the sequence evenly over the slots (padding in between).
+    std::vector<int> plain, special;
+    for (int j = 0; j < nr; ++j) (d->kind[j] == 0 ? plain : special).push_back(j);
+    std::vector<int> seq(nr, -1);
+    for (size_t i = 0; i < special.size(); ++i)
+        seq[(size_t)(((double)i + 0.5) * nr / special.size())] = special[i];
+    {
+        size_t pi = 0;
+        for (int jj = 0; jj < nr; ++jj)
+            if (seq[jj] < 0) seq[jj] = plain[pi++];
+    }
+    std::vector<int> order(nrp, -1);        // slot -> reaction (-1: padding)
+    for (int i = 0; i < nr; ++i) order[(size_t)((int64_t)i * nrp / nr)] = seq[i];
+    std::vector<uint16_t> b1((size_t)nch * 2 * RC * nsp, 0), b2((size_t)nch * nsp * RC, 0);
+    std::vector<CoefS> cf(nrp);
+    // per half chunk: third-body, live and reversible masks, then the multiplier base index;
+    // then the slot of every multiplier
+    std::vector<uint32_t> hmask((size_t)nch * 8, 0);
+    std::vector<uint32_t> fslot;
+    std::vector<FallBF> fl;
+    std::vector<uint16_t> tbsp;
+    std::vector<float> tbe;
+    auto b1_at = [&](int c, int r, int k) -> uint16_t & {
+        return b1[(size_t)c * 2 * RC * nsp + ((r / 8) * (nsp / 8) + k / 8) * 64 + (r % 8) * 8 + k % 8];
+    };
+    auto b2_at = [&](int c, int nrow, int r) -> uint16_t & {
+        return b2[(size_t)c * nsp * RC + ((nrow / 8) * (RC / 8) + r / 8) * 64 + (nrow % 8) * 8 + r % 8];
+    };
+    auto fbits = [](int v) {
+        float f;
+        memcpy(&f, &v, sizeof f);
+        return f;
+    };
+    for (int jj = 0; jj < nrp; ++jj) {
+        CoefS &C = cf[jj];
+        memset(&C, 0, sizeof C);
+        const int c = jj / RC, r = jj % RC;
+        const size_t mslot = (size_t)c * 2 + r / RH;
+        if (order[jj] < 0) {                    // padding slot: skipped by the epilogue
+            C.kf = make_float4(kDead, 0, 0, 0);
+            continue;
+        }
+        const int j = order[jj];
+        hmask[(size_t)nch * 2 + mslot] |= 1u << (r % RH);
+        if (d->reversible[j]) hmask[(size_t)nch * 4 + mslot] |= 1u << (r % RH);
+        const int kind = d->kind[j];
+        const double *ar = d->arrh + (size_t)j * 3;
+        int ordf = 0, ordr = 0;
+        for (int k = 0; k < ns; ++k) {
+            const int f = d->nu_f[(size_t)j * ns + k], pr = d->nu_r[(size_t)j * ns + k];
+            ordf += f;
+            ordr += pr;
+            b1_at(c, r, k) = bf16_of_int(f);
+            b1_at(c, RC + r, k) = bf16_of_int(pr);
+            b2_at(c, k, r) = bf16_of_int(pr - f);
+        }
+        const int tbx = kind == CHEM_RXN_THIRD_BODY ? 1 : 0;   // log2 M = log2 c_tot + log2(M/c_tot)
+        b1_at(c, r, ns) = bf16_of_int(tbx);
+        b1_at(c, RC + r, ns) = bf16_of_int(tbx);
+        b1_at(c, r, ns + 1) = bf16_of_int(ordf);
+        b1_at(c, RC + r, ns + 1) = bf16_of_int(ordr);
+        C.kf = make_float4((float)(ar[0] * kLog2e), (float)ar[1], (float)(-ar[2] * kLog2e),
+                           fbits(kind));
+        if (kind >= 1) {
+            if (!hmask[mslot]) hmask[(size_t)nch * 6 + mslot] = (uint32_t)fslot.size();
+            hmask[mslot] |= 1u << (r % RH);
+            fslot.push_back((uint32_t)jj);
+            C.meta.x = (int)tbsp.size();
+            int cnt = 0;
+            for (int k = 0; k < ns; ++k) {
+                const double e = d->eff ? d->eff[(size_t)j * ns + k] : 1.0;
+                if (e != 1.0) {
+                    tbsp.push_back((uint16_t)k);
+                    tbe.push_back((float)(e - 1.0));
+                    ++cnt;
+                }
+            }
+            if (cnt > kTbList)
+                return set_error(CHEM_EUNSUPPORTED,
+                                 "split-BF16 path: reaction %d lists more than %d efficiencies", j,
+                                 kTbList);
+            for (; cnt < kTbList; ++cnt) {
+                tbsp.push_back(0);
+                tbe.push_back(0.0f);
+            }
+            C.meta.y = (int)tbsp.size();
+        }
+        if (kind >= 2) {
+            FallBF F;
+            memset(&F, 0, sizeof F);
+            const double *al = d->arrh_low + (size_t)j * 3;
+            F.k0 = make_float4((float)(al[0] * kLog2e), (float)al[1], (float)(-al[2] * kLog2e), 0.f);
+            if (kind == 3) {
+                const double *tp = d->troe + (size_t)j * 4;
+                F.troe = make_float4((float)(1.0 - tp[0]), (float)tp[0], (float)(kLog2e / tp[1]),
+                                     (float)(kLog2e / tp[2]));
+                F.t2 = make_float4(tp[3] > 0.0 ? (float)(tp[3] * kLog2e) : -1.0f, 0, 0, 0);
+            }
+            C.meta.z = (int)fl.size();
+            fl.push_back(F);
+        }
+    }
+    // Gibbs layer per species (log2 units, the standard concentration folded into the bias):
+    // G = (a1 - a7) log2e - log2(p_ref/R) + (1 - a1) log2 T - a2/2 T log2e - a3/6 T^2 log2e
+    //     - a4/12 T^3 log2e - a5/20 T^4 log2e + a6 log2e / T
+    std::vector<GibbsS> gb(ns);
+    const double lg2_pref_R = log2(d->p_ref / kR);
+    for (int k = 0; k < ns; ++k) {
+        memset(&gb[k], 0, sizeof gb[k]);
+        for (int rg = 0; rg < 2; ++rg) {
+            const double *a = d->nasa7 + (size_t)k * 14 + (size_t)rg * 7;
+            const double cc[7] = {(a[0] - a[6]) * kLog2e - lg2_pref_R, 1.0 - a[0],
+                                  -a[1] / 2.0 * 1e3 * kLog2e, -a[2] / 6.0 * 1e6 * kLog2e,
+                                  -a[3] / 12.0 * 1e9 * kLog2e, -a[4] / 20.0 * 1e12 * kLog2e,
+                                  a[5] * kLog2e};
+            for (int q = 0; q < 7; ++q) gb[k].c[rg][q] = (float)cc[q];
+        }
+    }
+    {
+        const int max_fac = nsp == 32 ? Cols<32>::kMaxFactors : Cols<64>::kMaxFactors;
+        if ((int)fslot.size() > max_fac)
+            return set_error(CHEM_EUNSUPPORTED,
+                             "split-BF16 path holds at most %d third-body/falloff reactions", max_fac);
+        for (size_t h2 = 0; h2 < (size_t)nch * 2; ++h2)
+            if (__builtin_popcount(hmask[h2]) > 4)
+                return set_error(CHEM_EUNSUPPORTED, "more than 4 third-body reactions in a chunk half");
+        // evaluation order: third-body multipliers first, then falloff (their columns stay
+        // in slot order, so each half chunk reads consecutive columns)
+        std::vector<uint32_t> ord_slot, ord_col;
+        for (int pass = 0; pass < 2; ++pass)
+            for (size_t f = 0; f < fslot.size(); ++f) {
+                const int kd = d->kind[order[fslot[f]]];
+                if ((pass == 0) == (kd == CHEM_RXN_THIRD_BODY)) {
+                    ord_slot.push_back(fslot[f]);
+                    ord_col.push_back((uint32_t)f);
+                }
+            }
+        hmask.insert(hmask.end(), ord_slot.begin(), ord_slot.end());
+        hmask.insert(hmask.end(), ord_col.begin(), ord_col.end());
+    }
+    const int nfac = (int)fslot.size();
+    if (tbsp.empty()) {
+        tbsp.push_back(0);
+        tbe.push_back(0.f);
+    }
+    if (fl.empty()) fl.push_back(FallBF{});
+    std::vector<float> invW(ns);
+    for (int k = 0; k < ns; ++k) invW[k] = (float)(1.0 / d->mol_weight[k]);
+
+    // B1 | B2 | coefficients | masks | falloff | third-body lists: contiguous, copied to
+    // shared memory by one bulk transfer (16-byte granules)
+    auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    auto a256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t ob1 = 0, ob2 = b1.size() * 2, ocf = ob2 + b2.size() * 2;
+    const size_t ohm = a16(ocf + cf.size() * sizeof(CoefS));
+    const size_t ofl = a16(ohm + hmask.size() * 4);
+    const size_t otbe = a16(ofl + fl.size() * sizeof(FallBF));
+    const size_t otbs = a16(otbe + tbe.size() * 4);
+    const size_t ogb = a16(otbs + tbsp.size() * 2);
+    const size_t blob = a16(ogb + gb.size() * sizeof(GibbsS));
+    const size_t oiw = a256(blob), ost = a256(oiw + invW.size() * 4), total = a256(ost + 16);
+    std::vector<unsigned char> h(total, 0);
+    memcpy(h.data() + ob1, b1.data(), b1.size() * 2);
+    memcpy(h.data() + ob2, b2.data(), b2.size() * 2);
+    memcpy(h.data() + ocf, cf.data(), cf.size() * sizeof(CoefS));
+    memcpy(h.data() + ohm, hmask.data(), hmask.size() * 4);
+    memcpy(h.data() + ofl, fl.data(), fl.size() * sizeof(FallBF));
+    memcpy(h.data() + otbe, tbe.data(), tbe.size() * 4);
+    memcpy(h.data() + otbs, tbsp.data(), tbsp.size() * 2);
+    memcpy(h.data() + ogb, gb.data(), gb.size() * sizeof(GibbsS));
+    memcpy(h.data() + oiw, invW.data(), invW.size() * 4);
+    Bf16Tables *t = new (std::nothrow) Bf16Tables();
+    if (!t) return set_error(CHEM_ENOMEM, "host allocation failed");
+    cudaError_t e = cudaMalloc(&t->d_blob, total);
+    if (e != cudaSuccess) {
+        delete t;
+        return set_error(CHEM_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+    }
+    e = cudaMemcpy(t->d_blob, h.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(t->d_blob);
+        delete t;
+        return set_error(CHEM_ECUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
+    }
+    unsigned char *base = (unsigned char *)t->d_blob;
+    t->nsp = nsp;
+    t->nch = nch;
+    t->nfall = (int)fl.size();
+    t->ntb = (int)tbsp.size();
+    t->b1_bytes = b1.size() * 2;
+    t->b2_bytes = b2.size() * 2;
+    t->tab_bytes = blob - ocf;
+    t->o_coef = (uint32_t)ocf;
+    t->o_hmask = (uint32_t)ohm;
+    t->o_fall = (uint32_t)ofl;
+    t->o_tbe = (uint32_t)otbe;
+    t->o_tbsp = (uint32_t)otbs;
+    t->o_gib = (uint32_t)ogb;
+    t->nfac = nfac;
+    t->btab = (const uint16_t *)(base + ob1);
+    t->invW = (const float *)(base + oiw);
+    t->status = (int *)(base + ost);
+    m->bf16 = t;
+    m->have_bf16 = true;
+    m->device_bytes += total;
+    return CHEM_OK;
+}
+
+void bf16_free_tables(void *p)
+{
+    Bf16Tables *t = (Bf16Tables *)p;
+    if (!t) return;
+    cudaFree(t->d_blob);
+    delete t;
+}
+
+int *bf16_status_word(const chem_mech *m)
+{
+    return m->have_bf16 ? ((Bf16Tables *)m->bf16)->status : nullptr;
+}
+
+static int sm_count(int dev)
+{
+    static int cache[64] = {0};
+    if (dev < 0 || dev >= 64) return 148;
+    if (!cache[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = v > 0 ? v : 148;
+    }
+    return cache[dev];
+}
+
+template <int NSP>
+static chem_status launch_nsp(const Bf16Params &prm, size_t smem, cudaStream_t s, int dev)
+{
+    static std::atomic<uint32_t> done{0};
+    const uint32_t bit = 1u << (dev & 31);
+    if (!(done.load() & bit)) {
+        cudaError_t e = cudaFuncSetAttribute(k_source_bf16<NSP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             227 * 1024);
+        if (e != cudaSuccess)
+            return set_error(CHEM_ECUDA, "split-BF16 attribute: %s", cudaGetErrorString(e));
+        done.fetch_or(bit);
+    }
+    const int grid = std::min(prm.ntiles, sm_count(dev));
+    k_source_bf16<NSP><<<grid, kThreads, smem, s>>>(prm);
+    g_launches.fetch_add(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(CHEM_ECUDA, "split-BF16 launch: %s", cudaGetErrorString(e));
+    return CHEM_OK;
+}
+
+chem_status launch_source_bf16(const chem_mech *m, int64_t n, const float *T, const float *P,
+                               const float *Y, int64_t ldY, float *om, int64_t ldO,
+                               cudaStream_t s)
+{
+    if (!m->have_bf16)
+        return set_error(CHEM_EUNSUPPORTED, "split-BF16 path not available for this mechanism");
+    const Bf16Tables *t = (const Bf16Tables *)m->bf16;
+    Bf16Params prm;
+    memset(&prm, 0, sizeof prm);
+    prm.T = T;
+    prm.P = P;
+    prm.Y = Y;
+    prm.om = om;
+    prm.n = n;
+    prm.ldY = ldY;
+    prm.ldO = ldO;
+    prm.ns = m->ns;
+    prm.nch = t->nch;
+    prm.nfac = t->nfac;
+    prm.ntiles = (int)((n + 127) / 128);
+    prm.btab = t->btab;
+    prm.blob_bytes = (uint32_t)(t->b1_bytes + t->b2_bytes + t->tab_bytes);
+    prm.invW = t->invW;
+    prm.t_mid = (float)m->t_mid;
+    prm.lg2R = (float)log2(kR);
+    prm.status = t->status;
+    if ((int64_t)((n + 127) / 128) > 0x7fffffff) return set_error(CHEM_EINVAL, "n_cells too large");
+    // shared memory layout
+    auto al = [](size_t x, size_t a) { return (x + a - 1) & ~(a - 1); };
+    prm.o_b2 = (uint32_t)t->b1_bytes;
+    prm.o_coef = t->o_coef;
+    prm.o_hmask = t->o_hmask;
+    prm.o_fall = t->o_fall;
+    prm.o_tbe = t->o_tbe;
+    prm.o_tbsp = t->o_tbsp;
+    prm.o_gib = t->o_gib;
+    size_t off = al(prm.blob_bytes, 128);
+    const size_t ybytes = (size_t)128 * ldY * 4;
+    const size_t xw = (size_t)128 * m->ns * 4;
+    const size_t fixed = 2 * 512 + xw + al(m->ns * 4, 128) + 2048 + BAR_COUNT * 8 + 64 + 1024;
+    const bool aligned = ((uintptr_t)Y % 16 == 0) && ((uintptr_t)T % 16 == 0) && ((uintptr_t)P % 16 == 0);
+    prm.stage_y = aligned && (off + ybytes + fixed <= 227 * 1024) ? 1 : 0;
+    prm.bulk_out = (ldO == m->ns && (uintptr_t)om % 16 == 0) ? 1 : 0;
+    prm.o_y = (uint32_t)off;
+    if (prm.stage_y) off = al(off + ybytes, 128);
+    prm.o_t = (uint32_t)off;
+    off += 512;
+    prm.o_p = (uint32_t)off;
+    off += 512;
+    prm.o_xw = (uint32_t)off;
+    off = al(off + xw, 128);
+    prm.o_iw = (uint32_t)off;
+    off = al(off + m->ns * 4, 128);
+    prm.o_psum = (uint32_t)off;
+    off += 4 * 128 * 4;
+    prm.o_bar = (uint32_t)off;
+    off += BAR_COUNT * 8 + 64;
+    const size_t smem = off + 1024;          // room to align the base to 1024 bytes
+    if (smem > 227 * 1024)
+        return set_error(CHEM_EUNSUPPORTED, "split-BF16 tables need %zu bytes of shared memory",
+                         smem);
+    switch (t->nsp) {
+    case 32: return launch_nsp<32>(prm, smem, s, m->device);
+    default: return launch_nsp<64>(prm, smem, s, m->device);
+    }
 }
 
 }  // namespace chem
