@@ -37,12 +37,33 @@ WORKLOAD = ("53 species / 325 reactions synthetic GRI-size mechanism (30 third-b
 
 
 def peaks():
+    """(HBM GB/s, BF16 TFLOP/s burst, source) from MEASURED_PEAKS.json, else the fallback."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)
-        return float(p["hbm_gbs"]), "measured"
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
     except Exception:
-        return 6800.0, "fallback"
+        return 6800.0, 1900.0, "fallback"
+
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one 2^20-cell launch of the
+# split-BF16 kernel from the ncu capture summarised in
+# profiles/k_source_bf16_gri53_325_2p20cells.md; valid only for the kernel source it was
+# taken on (compared by hash, else reported as null).
+NCU_TRAFFIC = {"source": "paper_2008_08483_gb300/csrc/kern_bf16.cu",
+               "sha256": "6df4bac07f1ea0d1dcf4420f193692e573695a657a4589753b3ae32fb7b875d8",
+               "bytes_per_launch": 408_609_792, "cells": 1 << 20}
+
+
+def recorded_traffic():
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, NCU_TRAFFIC["source"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != NCU_TRAFFIC["sha256"]:
+                return None
+    except OSError:
+        return None
+    return NCU_TRAFFIC["bytes_per_launch"]
 
 
 class ClockSampler:
@@ -286,19 +307,26 @@ def main():
     # roofline of the dominant (only) kernel: algorithmic bytes / launch duration
     elt = 8 if prec == chem.FP64 else 4
     bytes_per_cell = elt * (2 + 2 * ns)
-    hbm, src = peaks()
+    hbm, bf16, src = peaks()
     achieved = bytes_per_cell * N_CELLS / (ms * 1e-3) / 1e9
+    traffic = recorded_traffic() if prec == chem.SPLIT_BF16 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None,
+            "frac": achieved / hbm, "traffic": traffic,
             "peak_source": f"{src} hbm_gbs", "bytes_per_cell": bytes_per_cell,
             "kernel": f"source term ({prec_name})"}
+    # the paper's dense matrix form: 6 N_S N_R flops per cell (S', S'' and omega products)
+    flops_cell = 6 * ns * mech.n_reactions
+    tflops = flops_cell * N_CELLS / (ms * 1e-3) / 1e12
+    tensor = {"achieved": tflops, "peak": bf16, "unit": "TFLOP/s", "frac": tflops / bf16,
+              "flops_per_cell": flops_cell, "peak_source": f"{src} bf16_tflops (burst)"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"split_bf16": "bf16", "fp32": "f32", "fp64": "f64"}[prec_name],
             "data": "synthetic", "config": config(prec_name, N_CELLS, ws),
-            "roofline": roof, "clocks": clk, "gpu_launches": int(launches)}
+            "roofline": roof, "tensor_algorithmic": tensor, "clocks": clk,
+            "gpu_launches": int(launches)}
 
     # end to end through the C ABI with pinned host buffers
     if args.no_e2e:

@@ -166,6 +166,34 @@ chem_status chem_source_term_host(const chem_mech *mech, int64_t n_cells, const 
                                   void *workspace, size_t workspace_bytes, void *stream);
 
 /*
+ * Derivatives of omega with respect to the state (T, ln C), where C are the molar
+ * concentrations (mol/cm^3, C = exp(ln C)); M = sum_k eff_k C_k for third-body and
+ * falloff reactions, so the state fixes omega without P.  Chain rule of Eqs. 2-8 and
+ * Sec. 2.4 (Arrhenius, equilibrium constant, third-body and Lindemann/Troe factors).
+ * Arrays are device pointers of the precision's element type (CHEM_FP64: double,
+ * CHEM_FP32: float; CHEM_SPLIT_BF16 returns CHEM_EUNSUPPORTED).  T[n], lnC[n][ldC].
+ * Asynchronous on `stream`; argument errors are synchronous (CHEM_EINVAL).
+ *
+ * chem_source_term_jvp: domega[n][ldO] = d omega/dT * dT + d omega/d ln C * dlnC for a
+ *   tangent dT[n], dlnC[n][ldC]; also omega[n][ldO] when omega is not NULL.
+ * chem_source_term_vjp: g_T[n] = sum_k g_omega_k d omega_k/dT and
+ *   g_lnC[n][ldC] = sum_k g_omega_k d omega_k/d ln C for a cotangent g_omega[n][ldG].
+ * chem_source_term_jacobian: the dense Jacobian, cell index fastest:
+ *   J[(k (n_species + 1) + m) ldJ + i] = d omega_k / d ln C_m of cell i for m < n_species,
+ *   and d omega_k / dT for m = n_species; ldJ >= n_cells.
+ */
+chem_status chem_source_term_jvp(const chem_mech *mech, int64_t n_cells, const void *T,
+                                 const void *lnC, int64_t ldC, const void *dT, const void *dlnC,
+                                 void *omega, void *domega, int64_t ldO, chem_precision precision,
+                                 void *stream);
+chem_status chem_source_term_vjp(const chem_mech *mech, int64_t n_cells, const void *T,
+                                 const void *lnC, int64_t ldC, const void *g_omega, int64_t ldG,
+                                 void *g_T, void *g_lnC, chem_precision precision, void *stream);
+chem_status chem_source_term_jacobian(const chem_mech *mech, int64_t n_cells, const void *T,
+                                      const void *lnC, int64_t ldC, void *J, int64_t ldJ,
+                                      chem_precision precision, void *stream);
+
+/*
  * Device-side status of a mechanism's tensor-core kernels.  Every wait inside them is
  * bounded; a kernel that gives up records a nonzero code (1 tile loader, 2 MMA issuer,
  * 3 epilogue) and its output is then invalid.  This call synchronises the current

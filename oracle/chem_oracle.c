@@ -254,3 +254,121 @@ int orc_source_term_tc(const orc_mech *m, int64_t n, const double *T, const doub
 {
     return orc_run(m, n, T, NULL, C, ldC, omega, ldO, nthreads);
 }
+
+/* ---- analytic Jacobian of omega with respect to (ln C, T) --------------------------------
+ *
+ * For each reaction, with q_f = k_f prod C^nu' and q_r = k_f / K_c prod C^nu'':
+ *   d ln q_f / d ln C_m = nu'_m + d ln k_f / d ln C_m,   d ln q_r / d ln C_m = nu''_m + same
+ *   d ln q_f / dT = d ln k_f / dT,                       d ln q_r / dT = d ln k_f / dT - d ln K_c / dT
+ * with d ln k_inf / dT = b/T + (E/R)/T^2 (Eq. 5), d ln K_c / dT = sum_k nu_k h_k/(R T^2) - dnu/T
+ * (Eq. 8, since d(g/RT)/dT = -h/(R T^2)), d ln M / d ln C_m = eff_m C_m / M for third-body
+ * reactions, and for falloff reactions the chain rule through Pr = k0 M / k_inf and the
+ * Troe function.  Then d omega_k = sum_j nu_kj (d q_f - d q_r) (Eq. 2).
+ * dw_dlnC is [ns][ns] (row: species of omega, column: ln C_m), dw_dT is [ns].
+ */
+
+/* d log10 F / d log10 Pr and d log10 F / dT (at fixed Pr) of the Troe function */
+static void orc_troe_dF(const double *tp, double T, double Pr, double *dlF_dlPr, double *dlF_dT)
+{
+    double alpha = tp[0], T3 = tp[1], T1 = tp[2], T2 = tp[3];
+    double e3 = exp(-T / T3), e1 = exp(-T / T1);
+    double Fc = (1.0 - alpha) * e3 + alpha * e1;
+    double dFc = -(1.0 - alpha) / T3 * e3 - alpha / T1 * e1;
+    if (T2 > 0.0) {
+        double e2 = exp(-T2 / T);
+        Fc += e2;
+        dFc += T2 / (T * T) * e2;
+    }
+    double L = log10(Fc);
+    double dL_dT = dFc / (Fc * log(10.0));
+    double c = -0.4 - 0.67 * L, n = 0.75 - 1.27 * L;
+    double x = log10(Pr) + c;
+    double D = n - 0.14 * x;
+    double f1 = x / D;
+    double g = 1.0 + f1 * f1;
+    /* df1/dx at fixed L: (D + 0.14 x) / D^2 = n / D^2 */
+    double df1_dx = n / (D * D);
+    *dlF_dlPr = -L * 2.0 * f1 / (g * g) * df1_dx;
+    /* through L: dx/dL = -0.67, dD/dL = -1.27 + 0.14 * 0.67 */
+    double dD_dL = -1.27 + 0.14 * 0.67;
+    double df1_dL = (-0.67 * D - x * dD_dL) / (D * D);
+    double dlF_dL = 1.0 / g - L * 2.0 * f1 / (g * g) * df1_dL;
+    *dlF_dT = dlF_dL * dL_dT;
+}
+
+void orc_jacobian_tc(const orc_mech *m, double T, const double *C, double *h_RT,
+                     double *g_RT, double *dw_dlnC, double *dw_dT)
+{
+    const int ns = m->ns;
+    orc_thermo(m, T, NULL, h_RT, NULL, g_RT);
+    double ln_pref_RT = log(m->p_ref / (ORC_R * T));
+    for (int i = 0; i < ns * ns; ++i) dw_dlnC[i] = 0.0;
+    for (int k = 0; k < ns; ++k) dw_dT[k] = 0.0;
+    double *dmod = (double *)malloc(sizeof(double) * (size_t)ns);   /* d ln(modifier)/d ln C */
+    if (!dmod) return;
+    for (int j = 0; j < m->nr; ++j) {
+        const int32_t *nf = m->nu_f + (size_t)j * ns;
+        const int32_t *nr = m->nu_r + (size_t)j * ns;
+        const double *ar = m->arrh + (size_t)j * 3;
+        double kinf = exp(ar[0]) * pow(T, ar[1]) * exp(-ar[2] / T);
+        double dlkinf_dT = ar[1] / T + ar[2] / (T * T);
+        double kf = kinf, dlkf_dT = dlkinf_dT;
+        int kind = m->kind[j];
+        for (int k = 0; k < ns; ++k) dmod[k] = 0.0;
+        if (kind != 0) {
+            double M = 0.0;
+            for (int k = 0; k < ns; ++k) M += m->eff[(size_t)j * ns + k] * C[k];
+            if (kind == 1) {
+                kf = kinf * M;
+                for (int k = 0; k < ns; ++k)
+                    dmod[k] = M > 0.0 ? m->eff[(size_t)j * ns + k] * C[k] / M : 0.0;
+            } else {
+                const double *al = m->arrh_low + (size_t)j * 3;
+                double k0 = exp(al[0]) * pow(T, al[1]) * exp(-al[2] / T);
+                double Pr = k0 * M / kinf;
+                if (!(Pr > 0.0)) continue;              /* k_f = 0: no contribution */
+                double F = 1.0, dlF_dlPr = 0.0, dlF_dT = 0.0;   /* log10 F derivatives */
+                if (kind == 3) {
+                    F = orc_troe_F(m->troe + (size_t)j * 4, T, Pr);
+                    orc_troe_dF(m->troe + (size_t)j * 4, T, Pr, &dlF_dlPr, &dlF_dT);
+                }
+                kf = kinf * (Pr / (1.0 + Pr)) * F;
+                double dmod_dlPr = 1.0 / (1.0 + Pr) + dlF_dlPr;
+                double dlPr_dT = (al[1] - ar[1]) / T + (al[2] - ar[2]) / (T * T);
+                dlkf_dT = dlkinf_dT + dmod_dlPr * dlPr_dT + dlF_dT * log(10.0);
+                for (int k = 0; k < ns; ++k)
+                    dmod[k] = dmod_dlPr * m->eff[(size_t)j * ns + k] * C[k] / M;
+            }
+        }
+        double lnKc = 0.0, dlKc_dT = 0.0;
+        int dnu = 0;
+        for (int k = 0; k < ns; ++k) {
+            int nu = nr[k] - nf[k];
+            if (nu) {
+                lnKc -= nu * g_RT[k];
+                dlKc_dT += nu * h_RT[k] / T;
+                dnu += nu;
+            }
+        }
+        lnKc += dnu * ln_pref_RT;
+        dlKc_dT -= dnu / T;
+        double kr = m->rev[j] ? kf / exp(lnKc) : 0.0;
+        double qf = kf, qr = kr;
+        for (int k = 0; k < ns; ++k) {
+            if (nf[k]) qf *= pow(C[k], (double)nf[k]);
+            if (nr[k]) qr *= pow(C[k], (double)nr[k]);
+        }
+        double dqnet_dT = qf * dlkf_dT - qr * (dlkf_dT - dlKc_dT);
+        for (int k = 0; k < ns; ++k) {
+            int nu = nr[k] - nf[k];
+            if (!nu) continue;
+            dw_dT[k] += nu * dqnet_dT;
+            double *row = dw_dlnC + (size_t)k * ns;
+            for (int mm = 0; mm < ns; ++mm) {
+                double d = qf * (nf[mm] + dmod[mm]) - qr * (nr[mm] + dmod[mm]);
+                row[mm] += nu * d;
+            }
+        }
+    }
+    free(dmod);
+}

@@ -55,6 +55,7 @@ def _load():
             lib.orc_troe_F.argtypes = [P, C.c_double, C.c_double]
             lib.orc_troe_F.restype = C.c_double
             lib.orc_cell_detail.argtypes = [P, C.c_double, P, P, P, P, P, P, P, P, P, P]
+            lib.orc_jacobian_tc.argtypes = [P, C.c_double, P, P, P, P, P]
             for f in (lib.orc_source_term_tpy, lib.orc_source_term_tc):
                 f.restype = C.c_int
             lib.orc_source_term_tpy.argtypes = [P, C.c_int64, P, P, P, C.c_int64, P, C.c_int64,
@@ -166,3 +167,15 @@ def source_term_tc(mech, T, Cc, nthreads: int | None = None) -> np.ndarray:
     if rc != 0:
         raise RuntimeError("oracle source term failed")
     return out
+
+
+def jacobian_tc(mech, T: float, C_):
+    """Analytic d omega / d ln C [ns, ns] and d omega / dT [ns] at (T, C)."""
+    om = _om(mech)
+    Cc = np.ascontiguousarray(C_, np.float64)
+    J = np.zeros((om.ns, om.ns))
+    dT = np.zeros(om.ns)
+    h = np.zeros(om.ns)
+    g = np.zeros(om.ns)
+    _load().orc_jacobian_tc(om.ref, float(T), _ptr(Cc), _ptr(h), _ptr(g), _ptr(J), _ptr(dT))
+    return J, dT

@@ -64,6 +64,12 @@ def lib():
             L.chem_source_term_host.argtypes = [P, I64, P, P, P, I64, P, I64, C.c_int, I64, P,
                                                 C.c_size_t, P]
             L.chem_device_status.argtypes = [P, C.POINTER(I32)]
+            L.chem_source_term_jvp.argtypes = [P, I64, P, P, I64, P, P, P, P, I64, C.c_int, P]
+            L.chem_source_term_vjp.argtypes = [P, I64, P, P, I64, P, I64, P, P, C.c_int, P]
+            L.chem_source_term_jacobian.argtypes = [P, I64, P, P, I64, P, I64, C.c_int, P]
+            for f in (L.chem_source_term_jvp, L.chem_source_term_vjp,
+                      L.chem_source_term_jacobian):
+                f.restype = C.c_int
             for f in (L.chem_mechanism_load, L.chem_mechanism_free, L.chem_mechanism_info,
                       L.chem_source_term, L.chem_source_term_host, L.chem_device_status):
                 f.restype = C.c_int
@@ -189,3 +195,97 @@ def source_term_host(mech: Mechanism, T, P, Y, out, precision: int, workspace, c
                                        workspace.numel() * workspace.element_size(),
                                        _stream_ptr(stream)))
     return out
+
+
+def _dptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _check_state(T, lnC, precision):
+    dt = _dtype(precision)
+    if precision not in (FP64, FP32):
+        raise ChemError(4, "derivatives are built for FP64 and FP32")
+    for name, t in (("T", T), ("lnC", lnC)):
+        if not t.is_cuda or t.dtype != dt:
+            raise ChemError(1, f"{name} must be a CUDA {dt} tensor")
+    if T.stride(0) != 1 or lnC.dim() != 2 or lnC.stride(1) != 1:
+        raise ChemError(1, "T contiguous and lnC row-major with unit column stride")
+
+
+def source_term_jvp(mech: Mechanism, T, lnC, dT, dlnC, precision: int = FP64, with_omega=True,
+                    stream=None):
+    """(omega or None, d omega) for the tangent (dT, dlnC) at the state (T, ln C)."""
+    import torch
+    _check_state(T, lnC, precision)
+    n = T.shape[0]
+    dT = dT.contiguous()
+    dlnC = dlnC if dlnC.stride(1) == 1 and dlnC.stride(0) == lnC.stride(0) else \
+        _like_rows(dlnC, lnC)
+    dom = torch.empty((n, mech.n_species), dtype=T.dtype, device=T.device)
+    om = torch.empty_like(dom) if with_omega else None
+    _check(lib().chem_source_term_jvp(mech.handle, n, T.data_ptr(), lnC.data_ptr(), lnC.stride(0),
+                                      dT.data_ptr(), dlnC.data_ptr(), _dptr(om), dom.data_ptr(),
+                                      dom.stride(0), int(precision), _stream_ptr(stream)))
+    return om, dom
+
+
+def _like_rows(x, ref):
+    import torch
+    out = torch.zeros((ref.shape[0], ref.stride(0)), dtype=ref.dtype, device=ref.device)
+    out[:, :x.shape[1]] = x
+    return out[:, :ref.shape[1]]
+
+
+def source_term_vjp(mech: Mechanism, T, lnC, g_omega, precision: int = FP64, stream=None):
+    """(g_T, g_lnC) = (d omega / d(T, ln C))^T g_omega."""
+    import torch
+    _check_state(T, lnC, precision)
+    n = T.shape[0]
+    g_omega = g_omega.contiguous()
+    gT = torch.empty((n,), dtype=T.dtype, device=T.device)
+    glnC = torch.empty((n, lnC.stride(0)), dtype=T.dtype, device=T.device)[:, :lnC.shape[1]]
+    _check(lib().chem_source_term_vjp(mech.handle, n, T.data_ptr(), lnC.data_ptr(), lnC.stride(0),
+                                      g_omega.data_ptr(), g_omega.stride(0), gT.data_ptr(),
+                                      glnC.data_ptr(), int(precision), _stream_ptr(stream)))
+    return gT, glnC
+
+
+def source_term_jacobian(mech: Mechanism, T, lnC, precision: int = FP64, stream=None):
+    """Dense Jacobian as a tensor [n, ns, ns + 1]: d omega_k / d ln C_m (m < ns), d / dT."""
+    import torch
+    _check_state(T, lnC, precision)
+    n, ns = T.shape[0], mech.n_species
+    J = torch.empty((ns, ns + 1, n), dtype=T.dtype, device=T.device)
+    _check(lib().chem_source_term_jacobian(mech.handle, n, T.data_ptr(), lnC.data_ptr(),
+                                           lnC.stride(0), J.data_ptr(), n, int(precision),
+                                           _stream_ptr(stream)))
+    return J.permute(2, 0, 1)
+
+
+def _omega_fn():
+    import torch
+
+    class OmegaFn(torch.autograd.Function):
+        """omega(T, ln C) with the hand-written vjp kernel as its backward pass."""
+
+        @staticmethod
+        def forward(ctx, mech, T, lnC, precision):
+            Tc, lc = T.detach().contiguous(), lnC.detach().contiguous()
+            om, _ = source_term_jvp(mech, Tc, lc, torch.zeros_like(Tc), torch.zeros_like(lc),
+                                    precision)
+            ctx.mech, ctx.precision = mech, precision
+            ctx.save_for_backward(Tc, lc)
+            return om
+
+        @staticmethod
+        def backward(ctx, g):
+            Tc, lc = ctx.saved_tensors
+            gT, glnC = source_term_vjp(ctx.mech, Tc, lc, g.contiguous(), ctx.precision)
+            return None, gT, glnC, None
+
+    return OmegaFn
+
+
+def omega(mech: Mechanism, T, lnC, precision: int = FP64):
+    """Differentiable omega(T, ln C) (torch.autograd), backward by chem_source_term_vjp."""
+    return _omega_fn().apply(mech, T, lnC, precision)

@@ -1,0 +1,373 @@
+// kern_tangent.cu -- derivatives of omega with respect to (ln C, T): jvp, vjp and the dense
+// Jacobian, one thread per cell (SIMT, double or float).
+//
+// With q_f = k_f prod C^nu' and q_r = k_f / K_c prod C^nu'' (Eqs. 3, 7), per reaction
+//   d ln q_f = sum_m nu'_m d ln C_m + d ln k_f
+//   d ln q_r = sum_m nu''_m d ln C_m + d ln k_f - d ln K_c
+//   d ln k_f = (b/T + (E/R)/T^2) dT + d ln(modifier)                             (Eq. 5)
+//   d ln K_c / dT from the folded Gibbs polynomial (Eqs. 9-11)
+//   modifier: third body M = sum_m eff_m C_m, d ln M = sum_m eff_m C_m d ln C_m / M;
+//             falloff Pr / (1 + Pr) F(T, Pr), Pr = k0 M / k_inf, through the chain rule
+//   d omega_k = sum_j nu_kj (q_f d ln q_f - q_r d ln q_r)                        (Eq. 2)
+// sum_m eff_m C_m x_m is evaluated as sum_m C_m x_m + sum_{listed m} (eff_m - 1) C_m x_m.
+#include <math.h>
+#include <string.h>
+
+#include "chem_internal.h"
+
+namespace chem {
+
+enum TangentMode { kJvp = 0, kVjp = 1, kJac = 2 };
+
+template <typename R>
+struct TanArgs {
+    int64_t n;
+    const R *T, *lnC;
+    int64_t ldC;
+    const R *dT, *dlnC;      // jvp tangent (dlnC row stride ldC)
+    R *om;                   // jvp: omega (may be NULL)
+    R *dom;                  // jvp: d omega
+    int64_t ldO;
+    const R *gw;             // vjp: cotangent of omega (row stride ldO)
+    R *gT, *glnC;            // vjp outputs (glnC row stride ldC)
+    R *J;                    // jac: [(k (ns + 1) + m) ldJ + i], m = ns is T
+    int64_t ldJ;
+};
+
+__device__ __forceinline__ double dexp(double x) { return exp(x); }
+__device__ __forceinline__ float dexp(float x) { return expf(x); }
+__device__ __forceinline__ double dlog(double x) { return log(x); }
+__device__ __forceinline__ float dlog(float x) { return logf(x); }
+__device__ __forceinline__ double dlog10(double x) { return log10(x); }
+__device__ __forceinline__ float dlog10(float x) { return log10f(x); }
+
+template <typename R, int MODE, int BLK>
+__global__ void __launch_bounds__(BLK) k_tangent(MechViewF64 mv, TanArgs<R> a)
+{
+    extern __shared__ unsigned char smem_tan[];
+    R *sm = (R *)smem_tan;
+    const int ns = mv.ns, tid = threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * BLK + tid;
+    if (i >= a.n) return;
+    R *sC = sm + tid;                           // C_m
+    R *sL = sm + ns * BLK + tid;                // ln C_m
+    R *sA = sm + 2 * ns * BLK + tid;            // jvp: d ln C_m; vjp: cotangent of omega_k
+    R *sB = sm + 3 * ns * BLK + tid;            // jvp: d omega_k; vjp: g ln C_m; jac: V_k
+    R *sW = sm + 4 * ns * BLK + tid;            // jvp: omega_k
+    const R Ti = a.T[i];
+    R ctot = 0, sdl = 0;
+    for (int m = 0; m < ns; ++m) {
+        const R l = a.lnC[i * a.ldC + m];
+        const R c = dexp(l);
+        sL[m * BLK] = l;
+        sC[m * BLK] = c;
+        ctot += c;
+        if (MODE == kJvp) {
+            const R d = a.dlnC[i * a.ldC + m];
+            sA[m * BLK] = d;
+            sdl += c * d;
+            sB[m * BLK] = 0;
+            sW[m * BLK] = 0;
+        } else if (MODE == kVjp) {
+            sA[m * BLK] = a.gw[i * a.ldO + m];
+            sB[m * BLK] = 0;
+        } else {
+            sB[m * BLK] = 0;
+            for (int mm = 0; mm <= ns; ++mm) a.J[((int64_t)m * (ns + 1) + mm) * a.ldJ + i] = 0;
+        }
+    }
+    const R dT = MODE == kJvp ? a.dT[i] : R(0);
+    const R lnT = dlog(Ti), invT = R(1) / Ti, tau = Ti * R(1e-3);
+    const int rg = (double)Ti >= mv.t_mid ? 1 : 0;
+    R gT = 0, Wtb = 0;      // vjp: cotangent of T; weight of the c_tot part of M
+    for (int j = 0; j < mv.nr; ++j) {
+        const RxnF64 *X = mv.rxn + j;
+        const R lkinf = R(X->lnA) + R(X->b) * lnT - R(X->EoR) * invT;
+        const R dlkinf = R(X->b) * invT + R(X->EoR) * invT * invT;
+        R lmod = 0, dmod_dlM = 0, dmod_dT = 0, M = 1;
+        bool dead = false;
+        const int kind = X->kind;
+        if (kind != 0) {
+            M = ctot;
+            for (int t = X->tb_begin; t < X->tb_end; ++t) M += R(mv.tb_e[t]) * sC[mv.tb_sp[t] * BLK];
+            if (!(M > R(0))) {
+                dead = true;
+            } else if (kind == 1) {
+                lmod = dlog(M);
+                dmod_dlM = 1;
+            } else {
+                const R lk0 = R(X->low[0]) + R(X->low[1]) * lnT - R(X->low[2]) * invT;
+                const R Pr = dexp(lk0 - lkinf) * M;
+                if (!(Pr > R(0))) {
+                    dead = true;
+                } else {
+                    lmod = dlog(Pr / (R(1) + Pr));
+                    R dlF_dlPr = 0, dlF_dT = 0;
+                    if (kind == 3) {
+                        const R e3 = dexp(-Ti * R(X->troe[2])), e1 = dexp(-Ti * R(X->troe[3]));
+                        R Fc = R(X->troe[0]) * e3 + R(X->troe[1]) * e1;
+                        R dFc = -R(X->troe[0]) * R(X->troe[2]) * e3 - R(X->troe[1]) * R(X->troe[3]) * e1;
+                        if (X->troe[4] > 0.0) {
+                            const R e2 = dexp(-R(X->troe[4]) * invT);
+                            Fc += e2;
+                            dFc += R(X->troe[4]) * invT * invT * e2;
+                        }
+                        const R L = dlog10(Fc);
+                        const R dL_dT = dFc / (Fc * R(2.302585092994045684));
+                        const R c = R(-0.4) - R(0.67) * L, nn = R(0.75) - R(1.27) * L;
+                        const R x = dlog10(Pr) + c;
+                        const R D = nn - R(0.14) * x;
+                        const R f1 = x / D, g = R(1) + f1 * f1;
+                        lmod += L / g * R(2.302585092994045684);
+                        dlF_dlPr = -L * R(2) * f1 / (g * g) * (nn / (D * D));
+                        const R dD_dL = R(-1.27) + R(0.14) * R(0.67);
+                        const R df1_dL = (R(-0.67) * D - x * dD_dL) / (D * D);
+                        dlF_dT = (R(1) / g - L * R(2) * f1 / (g * g) * df1_dL) * dL_dT;
+                    }
+                    dmod_dlM = R(1) / (R(1) + Pr) + dlF_dlPr;
+                    const R dlPr_dT = (R(X->low[1]) - R(X->b)) * invT +
+                                      (R(X->low[2]) - R(X->EoR)) * invT * invT;
+                    dmod_dT = dmod_dlM * dlPr_dT + dlF_dT * R(2.302585092994045684);
+                }
+            }
+        }
+        if (dead) continue;
+        const double *kc = X->kc[rg];
+        const R lKc = R(kc[0]) + R(kc[1]) * lnT +
+                      tau * (R(kc[2]) + tau * (R(kc[3]) + tau * (R(kc[4]) + tau * R(kc[5])))) +
+                      R(kc[6]) * invT;
+        const R dlKc = R(kc[1]) * invT +
+                       (R(kc[2]) + tau * (R(2) * R(kc[3]) + tau * (R(3) * R(kc[4]) + tau * R(4) * R(kc[5])))) * R(1e-3) -
+                       R(kc[6]) * invT * invT;
+        R sf = lkinf + lmod, sr = lkinf + lmod - lKc;
+        for (int t = 0; t < X->nf; ++t) sf += R(X->nuf[t]) * sL[X->spf[t] * BLK];
+        for (int t = 0; t < X->nr; ++t) sr += R(X->nur[t]) * sL[X->spr[t] * BLK];
+        const R qf = dexp(sf);
+        const R qr = X->rev ? dexp(sr) : R(0);
+        const R dlkf_dT = dlkinf + dmod_dT;            // d ln k_f / dT
+        if (MODE == kJvp) {
+            R dlM = 0;
+            if (kind != 0) {
+                R s = sdl;
+                for (int t = X->tb_begin; t < X->tb_end; ++t) {
+                    const int m = mv.tb_sp[t];
+                    s += R(mv.tb_e[t]) * sC[m * BLK] * sA[m * BLK];
+                }
+                dlM = s / M;
+            }
+            R tf = dlkf_dT * dT + dmod_dlM * dlM, tr = (dlkf_dT - dlKc) * dT + dmod_dlM * dlM;
+            for (int t = 0; t < X->nf; ++t) tf += R(X->nuf[t]) * sA[X->spf[t] * BLK];
+            for (int t = 0; t < X->nr; ++t) tr += R(X->nur[t]) * sA[X->spr[t] * BLK];
+            const R qn = qf - qr, dqn = qf * tf - qr * tr;
+            for (int t = 0; t < X->nf; ++t) {
+                sB[X->spf[t] * BLK] -= R(X->nuf[t]) * dqn;
+                sW[X->spf[t] * BLK] -= R(X->nuf[t]) * qn;
+            }
+            for (int t = 0; t < X->nr; ++t) {
+                sB[X->spr[t] * BLK] += R(X->nur[t]) * dqn;
+                sW[X->spr[t] * BLK] += R(X->nur[t]) * qn;
+            }
+        } else if (MODE == kVjp) {
+            R aa = 0;                                  // sum_k nu_kj g omega_k
+            for (int t = 0; t < X->nf; ++t) aa -= R(X->nuf[t]) * sA[X->spf[t] * BLK];
+            for (int t = 0; t < X->nr; ++t) aa += R(X->nur[t]) * sA[X->spr[t] * BLK];
+            const R uf = aa * qf, ur = aa * qr;
+            for (int t = 0; t < X->nf; ++t) sB[X->spf[t] * BLK] += uf * R(X->nuf[t]);
+            for (int t = 0; t < X->nr; ++t) sB[X->spr[t] * BLK] -= ur * R(X->nur[t]);
+            gT += uf * dlkf_dT - ur * (dlkf_dT - dlKc);
+            if (kind != 0) {
+                const R w = (uf - ur) * dmod_dlM / M;  // times eff_m C_m for every m
+                Wtb += w;
+                for (int t = X->tb_begin; t < X->tb_end; ++t) {
+                    const int m = mv.tb_sp[t];
+                    sB[m * BLK] += w * R(mv.tb_e[t]) * sC[m * BLK];
+                }
+            }
+        } else {
+            // d omega_k / d ln C_m and d omega_k / dT for the species of this reaction
+            const R dqT = qf * dlkf_dT - qr * (dlkf_dT - dlKc);
+            const R w = kind != 0 ? (qf - qr) * dmod_dlM / M : R(0);
+            auto row = [&](int k, R nu) {
+                R *Jk = a.J + (int64_t)k * (ns + 1) * a.ldJ + i;
+                Jk[(int64_t)ns * a.ldJ] += nu * dqT;
+                for (int t = 0; t < X->nf; ++t)
+                    Jk[(int64_t)X->spf[t] * a.ldJ] += nu * qf * R(X->nuf[t]);
+                for (int t = 0; t < X->nr; ++t)
+                    Jk[(int64_t)X->spr[t] * a.ldJ] -= nu * qr * R(X->nur[t]);
+                if (kind != 0) {
+                    sB[k * BLK] += nu * w;                // c_tot part: C_m V_k at the end
+                    for (int t = X->tb_begin; t < X->tb_end; ++t) {
+                        const int m = mv.tb_sp[t];
+                        Jk[(int64_t)m * a.ldJ] += nu * w * R(mv.tb_e[t]) * sC[m * BLK];
+                    }
+                }
+            };
+            for (int t = 0; t < X->nf; ++t) row(X->spf[t], -R(X->nuf[t]));
+            for (int t = 0; t < X->nr; ++t) row(X->spr[t], R(X->nur[t]));
+        }
+    }
+    if (MODE == kJvp) {
+        for (int k = 0; k < ns; ++k) {
+            a.dom[i * a.ldO + k] = sB[k * BLK];
+            if (a.om) a.om[i * a.ldO + k] = sW[k * BLK];
+        }
+    } else if (MODE == kVjp) {
+        a.gT[i] = gT;
+        for (int m = 0; m < ns; ++m) a.glnC[i * a.ldC + m] = sB[m * BLK] + Wtb * sC[m * BLK];
+    } else {
+        for (int k = 0; k < ns; ++k) {
+            const R v = sB[k * BLK];
+            if (v == R(0)) continue;
+            R *Jk = a.J + (int64_t)k * (ns + 1) * a.ldJ + i;
+            for (int m = 0; m < ns; ++m) Jk[(int64_t)m * a.ldJ] += v * sC[m * BLK];
+        }
+    }
+}
+
+template <typename R, int MODE>
+static chem_status launch_tan(const chem_mech *m, const TanArgs<R> &a, cudaStream_t s,
+                              const char *name)
+{
+    static std::atomic<uint32_t> done64{0}, done32{0};
+    const size_t per = 5 * sizeof(R) * (size_t)m->ns;
+    auto go = [&](auto kern, int blk, std::atomic<uint32_t> &done) -> chem_status {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (!(done.load() & (1u << (dev & 31)))) {
+            cudaError_t e =
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+            if (e != cudaSuccess) return set_error(CHEM_ECUDA, "%s: %s", name, cudaGetErrorString(e));
+            done.fetch_or(1u << (dev & 31));
+        }
+        kern<<<(unsigned)((a.n + blk - 1) / blk), blk, per * blk, s>>>(m->v64, a);
+        g_launches.fetch_add(1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return set_error(CHEM_ECUDA, "%s launch: %s", name, cudaGetErrorString(e));
+        return CHEM_OK;
+    };
+    if (per * 64 <= 200 * 1024) return go(k_tangent<R, MODE, 64>, 64, done64);
+    if (per * 32 <= 227 * 1024) return go(k_tangent<R, MODE, 32>, 32, done32);
+    return set_error(CHEM_EUNSUPPORTED, "%s: %d species exceed the SIMT kernel", name, m->ns);
+}
+
+template <typename R>
+chem_status tangent_dispatch(const chem_mech *m, int mode, const TanArgs<R> &a, cudaStream_t s)
+{
+    switch (mode) {
+    case kJvp: return launch_tan<R, kJvp>(m, a, s, "jvp");
+    case kVjp: return launch_tan<R, kVjp>(m, a, s, "vjp");
+    default: return launch_tan<R, kJac>(m, a, s, "jacobian");
+    }
+}
+
+}  // namespace chem
+
+using namespace chem;
+
+static chem_status tan_common(const chem_mech *m, int64_t n, const void *T, const void *lnC,
+                              int64_t ldC, chem_precision prec)
+{
+    if (!m) return set_error(CHEM_EINVAL, "mechanism is NULL");
+    if (n < 0) return set_error(CHEM_EINVAL, "n_cells < 0");
+    if (ldC < m->ns) return set_error(CHEM_EINVAL, "ldC below n_species=%d", m->ns);
+    if (prec != CHEM_FP64 && prec != CHEM_FP32)
+        return set_error(CHEM_EUNSUPPORTED, "derivatives are built for CHEM_FP64 and CHEM_FP32");
+    if (n > 0 && (!T || !lnC)) return set_error(CHEM_EINVAL, "NULL T or lnC with n_cells > 0");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != m->device) return set_error(CHEM_EINVAL, "mechanism lives on device %d", m->device);
+    return CHEM_OK;
+}
+
+template <typename R>
+static TanArgs<R> targs(int64_t n, const void *T, const void *lnC, int64_t ldC)
+{
+    TanArgs<R> a;
+    memset(&a, 0, sizeof a);
+    a.n = n;
+    a.T = (const R *)T;
+    a.lnC = (const R *)lnC;
+    a.ldC = ldC;
+    return a;
+}
+
+extern "C" chem_status chem_source_term_jvp(const chem_mech *m, int64_t n, const void *T,
+                                            const void *lnC, int64_t ldC, const void *dT,
+                                            const void *dlnC, void *omega, void *domega,
+                                            int64_t ldO, chem_precision prec, void *stream)
+{
+    clear_error();
+    chem_status st = tan_common(m, n, T, lnC, ldC, prec);
+    if (st != CHEM_OK) return st;
+    if (ldO < m->ns) return set_error(CHEM_EINVAL, "ldO below n_species=%d", m->ns);
+    if (n == 0) return CHEM_OK;
+    if (!dT || !dlnC || !domega) return set_error(CHEM_EINVAL, "NULL tangent or output");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (prec == CHEM_FP64) {
+        TanArgs<double> a = targs<double>(n, T, lnC, ldC);
+        a.dT = (const double *)dT;
+        a.dlnC = (const double *)dlnC;
+        a.om = (double *)omega;
+        a.dom = (double *)domega;
+        a.ldO = ldO;
+        return tangent_dispatch<double>(m, kJvp, a, s);
+    }
+    TanArgs<float> a = targs<float>(n, T, lnC, ldC);
+    a.dT = (const float *)dT;
+    a.dlnC = (const float *)dlnC;
+    a.om = (float *)omega;
+    a.dom = (float *)domega;
+    a.ldO = ldO;
+    return tangent_dispatch<float>(m, kJvp, a, s);
+}
+
+extern "C" chem_status chem_source_term_vjp(const chem_mech *m, int64_t n, const void *T,
+                                            const void *lnC, int64_t ldC, const void *g_omega,
+                                            int64_t ldG, void *g_T, void *g_lnC,
+                                            chem_precision prec, void *stream)
+{
+    clear_error();
+    chem_status st = tan_common(m, n, T, lnC, ldC, prec);
+    if (st != CHEM_OK) return st;
+    if (ldG < m->ns) return set_error(CHEM_EINVAL, "ldG below n_species=%d", m->ns);
+    if (n == 0) return CHEM_OK;
+    if (!g_omega || !g_T || !g_lnC) return set_error(CHEM_EINVAL, "NULL cotangent or output");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (prec == CHEM_FP64) {
+        TanArgs<double> a = targs<double>(n, T, lnC, ldC);
+        a.gw = (const double *)g_omega;
+        a.ldO = ldG;
+        a.gT = (double *)g_T;
+        a.glnC = (double *)g_lnC;
+        return tangent_dispatch<double>(m, kVjp, a, s);
+    }
+    TanArgs<float> a = targs<float>(n, T, lnC, ldC);
+    a.gw = (const float *)g_omega;
+    a.ldO = ldG;
+    a.gT = (float *)g_T;
+    a.glnC = (float *)g_lnC;
+    return tangent_dispatch<float>(m, kVjp, a, s);
+}
+
+extern "C" chem_status chem_source_term_jacobian(const chem_mech *m, int64_t n, const void *T,
+                                                 const void *lnC, int64_t ldC, void *J,
+                                                 int64_t ldJ, chem_precision prec, void *stream)
+{
+    clear_error();
+    chem_status st = tan_common(m, n, T, lnC, ldC, prec);
+    if (st != CHEM_OK) return st;
+    if (ldJ < n) return set_error(CHEM_EINVAL, "ldJ below n_cells");
+    if (n == 0) return CHEM_OK;
+    if (!J) return set_error(CHEM_EINVAL, "NULL Jacobian");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (prec == CHEM_FP64) {
+        TanArgs<double> a = targs<double>(n, T, lnC, ldC);
+        a.J = (double *)J;
+        a.ldJ = ldJ;
+        return tangent_dispatch<double>(m, kJac, a, s);
+    }
+    TanArgs<float> a = targs<float>(n, T, lnC, ldC);
+    a.J = (float *)J;
+    a.ldJ = ldJ;
+    return tangent_dispatch<float>(m, kJac, a, s);
+}

@@ -321,3 +321,54 @@ def test_log_rates_stay_in_fp32_range(size, kind, Tr, Pr):
             small = np.maximum(small, nu_abs.T @ tiny)
         assert np.all(small <= 1e-12 * np.abs(d["omega"]).max())
     assert worst < 80.0
+
+
+# ---------------------------------------------------------------------------
+# analytic Jacobian (d omega / d(ln C, T))
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("size,kw", [("h2air_9_21", dict(n_lindemann=2, n_irreversible=3)),
+                                     ("gri_53_325", dict(n_lindemann=4, n_irreversible=10))])
+def test_jacobian_matches_central_differences(size, kw):
+    """The oracle's analytic Jacobian against central differences of its own omega
+    (step 1e-6 relative), including third-body, Lindemann, Troe and irreversible reactions,
+    at states on both sides of T_mid."""
+    m = synth.make_mechanism(size, seed=2, **kw)
+    om = O.OracleMechanism(m)
+    T, P, Y = synth.make_states(m, 6, seed=21, T_range=(700.0, 2600.0),
+                                kind="dirichlet" if size == "h2air_9_21" else "mixture")
+    for i in range(len(T)):
+        C = O.concentrations(om, T[i], P[i], Y[i])
+        J, dT = O.jacobian_tc(om, T[i], C)
+        lnC = np.log(C)
+
+        def w(T_, l_):
+            return O.source_term_tc(om, [T_], np.exp(l_)[None])[0]
+        Jfd = np.zeros_like(J)
+        for mm in range(len(C)):
+            e = np.zeros_like(lnC)
+            e[mm] = 1e-6
+            Jfd[:, mm] = (w(T[i], lnC + e) - w(T[i], lnC - e)) / 2e-6
+        hT = 1e-6 * T[i]
+        dTfd = (w(T[i] + hT, lnC) - w(T[i] - hT, lnC)) / (2 * hT)
+        assert np.abs(J - Jfd).max() <= 1e-6 * np.abs(J).max()
+        assert np.abs(dT - dTfd).max() <= 1e-6 * np.abs(dT).max()
+
+
+def test_jacobian_detailed_balance_structure():
+    """At an equilibrium composition q_f = q_r for every reaction, so d omega / d ln C
+    reduces to sum_j nu_kj q_j (nu'_m - nu''_m) = -sum_j nu_kj q_j nu_mj, whose rows are
+    orthogonal to the element vectors (element conservation of the linearised system)."""
+    m = synth.make_mechanism("gri_53_325", seed=4)
+    om = O.OracleMechanism(m)
+    T = 1800.0
+    g = O.thermo(om, T)[3]
+    lam = np.random.default_rng(3).uniform(-2, 2, m.n_elements)
+    C = m.p_ref / (O.R_CGS * T) * np.exp(-g + m.elem_comp @ lam)
+    J, _ = O.jacobian_tc(om, T, C)
+    q = O.cell_detail(om, T, C)["qf"]
+    nu = (m.nu_r - m.nu_f).astype(float)              # [nr, ns]
+    expect = -(nu.T * q) @ nu
+    assert np.abs(J - expect).max() <= 1e-10 * np.abs(expect).max()
+    E = m.elem_comp.astype(float)
+    assert np.abs(E.T @ J).max() <= 1e-10 * np.abs(J).max()
