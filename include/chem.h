@@ -194,6 +194,79 @@ chem_status chem_source_term_jacobian(const chem_mech *mech, int64_t n_cells, co
                                       chem_precision precision, void *stream);
 
 /*
+ * Constant-pressure adiabatic 0-D reactor: the stiff time integration the paper names as
+ * future work for the source term (Conclusion; its own test integrates the same reactor
+ * explicitly, Sec. 3.1.2).  Per cell the state is y = (T, Y_1 .. Y_ns) at fixed P and
+ *   dY_k/dt = W_k omega_k / rho,        dT/dt = -sum_k H_k omega_k / (rho c_p)
+ * with rho = P / (R T sum_k Y_k/W_k), C_k = rho Y_k / W_k, molar enthalpies
+ * H_k = R T (h/RT)_k and c_p = sum_k Y_k R (cp/R)_k / W_k from the NASA-7 polynomials
+ * (Eq. 10).  omega is Eqs. 2-11 and Sec. 2.4 with the mass-action products taken as
+ * polynomials in C: negative mass fractions are NOT clipped here, so that the right-hand
+ * side is smooth for an implicit integrator.  All arrays are FP64 DEVICE arrays;
+ * T[n], P[n], Y[n][ldY].  Each cell is handled by one warp; results do not depend on the
+ * other cells of the batch.
+ *
+ * chem_ode_rhs: f[i * ldF + 0] = dT/dt, f[i * ldF + 1 + k] = dY_k/dt; ldF >= n_species + 1.
+ * chem_ode_jacobian: the analytic Jacobian, cell-major and row-major per cell:
+ *   J[(i (n_species + 1) + r) (n_species + 1) + c] = d f_r / d y_c (index 0 is T).
+ * Both are asynchronous on `stream`.  Errors: CHEM_EINVAL (NULL pointers with n > 0, n < 0,
+ * ldY < n_species, ldF < n_species + 1, other device), CHEM_EUNSUPPORTED (a reaction with
+ * more than 16 distinct species, or a mechanism whose per-warp vectors exceed shared
+ * memory), CHEM_ENOMEM, CHEM_ECUDA.
+ */
+chem_status chem_ode_rhs(const chem_mech *mech, int64_t n_cells, const double *T,
+                         const double *P, const double *Y, int64_t ldY, double *f,
+                         int64_t ldF, void *stream);
+chem_status chem_ode_jacobian(const chem_mech *mech, int64_t n_cells, const double *T,
+                              const double *P, const double *Y, int64_t ldY, double *J,
+                              void *stream);
+
+/* Per-cell outcome of chem_integrate_cells. */
+enum { CHEM_CELL_OK = 0, CHEM_CELL_STEP_UNDERFLOW = 1, CHEM_CELL_MAX_STEPS = 2 };
+
+/* Options of chem_integrate_cells; a NULL pointer means all defaults. */
+typedef struct {
+    double h_init;          /* first step (s); <= 0: min(1e-10 s, t_end) */
+    double h_min;           /* a cell fails when its step falls below this (s); <= 0: 1e-20 */
+    double h_max;           /* largest step (s); <= 0: t_end */
+    int64_t max_steps;      /* attempted steps per cell before it fails; <= 0: 100000 */
+    double ign_dT;          /* ignition event: first time T reaches T0 + ign_dT; <= 0: 400 K */
+    double *t_ign;          /* [n] device or NULL: ignition time (s), linear in T within the
+                               accepted step that crosses; -1 when not reached */
+    int32_t *n_accepted;    /* [n] device or NULL: accepted steps per cell */
+    int32_t *n_rejected;    /* [n] device or NULL: rejected steps per cell */
+} chem_integrate_opts;
+
+/*
+ * Integrate every cell's reactor from t = 0 to t_end in place: on return T[n] and
+ * Y[n][ldY] hold the state at t_end (P[n] is constant).  Rosenbrock method Rodas3
+ * (Sandu et al. 1997: four stages, order 3 with an embedded order-2 solution, stiffly
+ * accurate and L-stable) with the analytic Jacobian of chem_ode_jacobian, an FP64 LU with
+ * partial pivoting per step, and per-cell step-size control on the RMS norm of the
+ * embedded error with weights atol + rtol max(|y_old|, |y_new|); each cell takes its own
+ * steps, so its result does not depend on the rest of the batch.  cell_status[n] (device,
+ * may be NULL) receives CHEM_CELL_*; a failed cell keeps its last accepted state.
+ * The call allocates a small device workspace on `stream` (stream-ordered) and
+ * SYNCHRONISES `stream` before returning, to report failures: CHEM_ENONCONV when at
+ * least one cell failed (the others are valid).  Errors: as chem_ode_rhs, plus
+ * CHEM_EINVAL for t_end < 0, rtol <= 0 or atol < 0.
+ */
+chem_status chem_integrate_cells(const chem_mech *mech, int64_t n_cells, double *T,
+                                 const double *P, double *Y, int64_t ldY, double t_end,
+                                 double rtol, double atol, const chem_integrate_opts *opts,
+                                 int32_t *cell_status, void *stream);
+
+/*
+ * The classical coefficients of the integrator's Rosenbrock method (host call, no GPU
+ * needed): *stages = s, gamma_ii = *gamma, alpha[s][s] and gamma[s][s] strictly lower
+ * (row-major, 4 x 4 buffers), b[s] and the embedded bhat[s], in the form
+ *   (I - h gamma_ii J) k_i = h f(y + sum_j alpha_ij k_j) + h J sum_j gamma_ij k_j,
+ *   y_new = y + sum_i b_i k_i.
+ */
+chem_status chem_rosenbrock_tableau(int32_t *stages, double *gamma_ii, double *alpha,
+                                    double *gamma, double *b, double *bhat);
+
+/*
  * Device-side status of a mechanism's tensor-core kernels.  Every wait inside them is
  * bounded; a kernel that gives up records a nonzero code (1 tile loader, 2 MMA issuer,
  * 3 epilogue) and its output is then invalid.  This call synchronises the current

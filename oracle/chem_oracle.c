@@ -372,3 +372,206 @@ void orc_jacobian_tc(const orc_mech *m, double T, const double *C, double *h_RT,
     }
     free(dmod);
 }
+
+/* ---- constant-pressure adiabatic 0-D reactor ---------------------------------------------
+ *
+ * State y = (T, Y_1 .. Y_ns) at fixed pressure P.  With S = sum_k Y_k / W_k,
+ * rho = P / (R T S) and C_k = rho Y_k / W_k:
+ *   dY_k / dt = W_k omega_k / rho
+ *   dT / dt   = -sum_k H_k omega_k / (rho c_p)
+ * with the molar enthalpies H_k = R T (h/RT)_k and the mass heat capacity
+ * c_p = sum_k Y_k R (cp/R)_k / W_k.  These keep the mixture enthalpy sum_k Y_k H_k / W_k
+ * constant (adiabatic, constant pressure) and sum_k Y_k constant.  The mass-action products
+ * take C as it comes, without clipping: the right-hand side is then a polynomial in C and a
+ * smooth function of y, as an implicit integrator that may step through small negative mass
+ * fractions needs.
+ */
+
+/* d/dC_m of prod_k C_k^nu_k, i.e. nu_m C_m^(nu_m - 1) prod_{k != m} C_k^nu_k */
+static double orc_dprod(const int32_t *nu, const double *C, int ns, int mcol)
+{
+    if (!nu[mcol]) return 0.0;
+    double p = nu[mcol] * pow(C[mcol], (double)(nu[mcol] - 1));
+    for (int k = 0; k < ns; ++k)
+        if (k != mcol && nu[k]) p *= pow(C[k], (double)nu[k]);
+    return p;
+}
+
+/*
+ * d omega / dC [ns][ns] and d omega / dT at fixed C [ns], with the mass-action products
+ * differentiated directly (no division by C, so C_m = 0 is fine):
+ *   d q_f / dC_m = k_f d(prod C^nu')/dC_m + eff_m (d k_f / dM) prod C^nu'
+ *   d q_r / dC_m = k_r d(prod C^nu'')/dC_m + eff_m (d k_f / dM) / K_c prod C^nu''
+ * with d k_f / dM = k_inf for third-body reactions and k_f (1/(1+Pr) + d log F / d log Pr) / M
+ * for falloff reactions; the temperature derivatives are those of orc_jacobian_tc.
+ */
+void orc_dwdC(const orc_mech *m, double T, const double *C, double *dwdC, double *dwdT)
+{
+    const int ns = m->ns;
+    double *h_RT = (double *)malloc(sizeof(double) * (size_t)ns * 2);
+    if (!h_RT) return;
+    double *g_RT = h_RT + ns;
+    orc_thermo(m, T, NULL, h_RT, NULL, g_RT);
+    double ln_pref_RT = log(m->p_ref / (ORC_R * T));
+    for (int i = 0; i < ns * ns; ++i) dwdC[i] = 0.0;
+    for (int k = 0; k < ns; ++k) dwdT[k] = 0.0;
+    for (int j = 0; j < m->nr; ++j) {
+        const int32_t *nf = m->nu_f + (size_t)j * ns;
+        const int32_t *nr = m->nu_r + (size_t)j * ns;
+        const double *ar = m->arrh + (size_t)j * 3;
+        const double *eff = m->eff + (size_t)j * ns;
+        double kinf = exp(ar[0]) * pow(T, ar[1]) * exp(-ar[2] / T);
+        double dlkf_dT = ar[1] / T + ar[2] / (T * T);
+        double kf = kinf, dkf_dM = 0.0;
+        int kind = m->kind[j];
+        if (kind != 0) {
+            double M = 0.0;
+            for (int k = 0; k < ns; ++k) M += eff[k] * C[k];
+            if (kind == 1) {
+                kf = kinf * M;
+                dkf_dM = kinf;
+            } else {
+                const double *al = m->arrh_low + (size_t)j * 3;
+                double k0 = exp(al[0]) * pow(T, al[1]) * exp(-al[2] / T);
+                double Pr = k0 * M / kinf;
+                if (!(Pr > 0.0)) continue;
+                double F = 1.0, dlF_dlPr = 0.0, dlF_dT = 0.0;
+                if (kind == 3) {
+                    F = orc_troe_F(m->troe + (size_t)j * 4, T, Pr);
+                    orc_troe_dF(m->troe + (size_t)j * 4, T, Pr, &dlF_dlPr, &dlF_dT);
+                }
+                kf = kinf * (Pr / (1.0 + Pr)) * F;
+                double dmod_dlPr = 1.0 / (1.0 + Pr) + dlF_dlPr;
+                dkf_dM = kf * dmod_dlPr / M;
+                double dlPr_dT = (al[1] - ar[1]) / T + (al[2] - ar[2]) / (T * T);
+                dlkf_dT += dmod_dlPr * dlPr_dT + dlF_dT * log(10.0);
+            }
+        }
+        double lnKc = 0.0, dlKc_dT = 0.0;
+        int dnu = 0;
+        for (int k = 0; k < ns; ++k) {
+            int nu = nr[k] - nf[k];
+            if (nu) {
+                lnKc -= nu * g_RT[k];
+                dlKc_dT += nu * h_RT[k] / T;
+                dnu += nu;
+            }
+        }
+        lnKc += dnu * ln_pref_RT;
+        dlKc_dT -= dnu / T;
+        double Kc = exp(lnKc);
+        int rev = m->rev[j];
+        double kr = rev ? kf / Kc : 0.0;
+        double pf = 1.0, pr = 1.0;
+        for (int k = 0; k < ns; ++k) {
+            if (nf[k]) pf *= pow(C[k], (double)nf[k]);
+            if (nr[k]) pr *= pow(C[k], (double)nr[k]);
+        }
+        double qf = kf * pf, qr = kr * pr;
+        double dqnet_dT = qf * dlkf_dT - qr * (dlkf_dT - dlKc_dT);
+        double dqnet_dM = dkf_dM * (pf - (rev ? pr / Kc : 0.0));
+        for (int k = 0; k < ns; ++k) {
+            int nu = nr[k] - nf[k];
+            if (!nu) continue;
+            dwdT[k] += nu * dqnet_dT;
+            double *row = dwdC + (size_t)k * ns;
+            for (int mm = 0; mm < ns; ++mm) {
+                double d = kf * orc_dprod(nf, C, ns, mm) - kr * orc_dprod(nr, C, ns, mm);
+                if (kind != 0) d += eff[mm] * dqnet_dM;
+                row[mm] += nu * d;
+            }
+        }
+    }
+    free(h_RT);
+}
+
+/* Right-hand side f [ns + 1] of the reactor at state y [ns + 1] and pressure P. */
+void orc_ode_rhs(const orc_mech *m, double P, const double *y, double *f)
+{
+    const int ns = m->ns;
+    double *buf = (double *)malloc(sizeof(double) * (size_t)ns * 5);
+    if (!buf) return;
+    double *C = buf, *g = buf + ns, *h_RT = buf + 2 * ns, *cp_R = buf + 3 * ns, *w = buf + 4 * ns;
+    const double T = y[0];
+    const double *Y = y + 1;
+    double S = 0.0;
+    for (int k = 0; k < ns; ++k) S += Y[k] / m->W[k];
+    double rho = P / (ORC_R * T * S);
+    for (int k = 0; k < ns; ++k) C[k] = rho * Y[k] / m->W[k];
+    orc_cell_detail(m, T, C, g, NULL, NULL, NULL, NULL, NULL, NULL, NULL, w);
+    orc_thermo(m, T, cp_R, h_RT, NULL, NULL);
+    double cp = 0.0, Q = 0.0;
+    for (int k = 0; k < ns; ++k) {
+        cp += Y[k] * ORC_R * cp_R[k] / m->W[k];
+        Q += ORC_R * T * h_RT[k] * w[k];
+    }
+    f[0] = -Q / (rho * cp);
+    for (int k = 0; k < ns; ++k) f[1 + k] = m->W[k] * w[k] / rho;
+    free(buf);
+}
+
+/*
+ * Jacobian J [(ns + 1)][(ns + 1)] (row: component of f, column: component of y) of
+ * orc_ode_rhs, by the chain rule through C(T, Y) = rho Y / W:
+ *   dC_m/dT = -C_m / T,   dC_m/dY_n = rho delta_mn / W_m - C_m / (S W_n)
+ *   d(1/rho)/dT = 1/(rho T),   d(1/rho)/dY_n = 1/(rho S W_n)
+ *   dH_k/dT = R (cp/R)_k,   d(cp/R)_k/dT = a2 + 2 a3 T + 3 a4 T^2 + 4 a5 T^3
+ */
+void orc_ode_jac(const orc_mech *m, double P, const double *y, double *J)
+{
+    const int ns = m->ns, n = ns + 1;
+    double *buf = (double *)malloc(sizeof(double) * ((size_t)ns * 10 + (size_t)ns * ns));
+    if (!buf) return;
+    double *C = buf, *g = buf + ns, *h_RT = buf + 2 * ns, *cp_R = buf + 3 * ns, *w = buf + 4 * ns;
+    double *dwdT = buf + 5 * ns, *wT = buf + 6 * ns, *dcp = buf + 7 * ns, *wC = buf + 8 * ns;
+    double *dwdC = buf + 10 * ns;
+    const double T = y[0];
+    const double *Y = y + 1;
+    double S = 0.0;
+    for (int k = 0; k < ns; ++k) S += Y[k] / m->W[k];
+    double rho = P / (ORC_R * T * S);
+    for (int k = 0; k < ns; ++k) C[k] = rho * Y[k] / m->W[k];
+    orc_cell_detail(m, T, C, g, NULL, NULL, NULL, NULL, NULL, NULL, NULL, w);
+    orc_thermo(m, T, cp_R, h_RT, NULL, NULL);
+    orc_dwdC(m, T, C, dwdC, dwdT);
+    for (int k = 0; k < ns; ++k) {
+        const double *a = m->nasa + (size_t)k * 14 + (T < m->t_mid ? 0 : 7);
+        dcp[k] = ORC_R * (a[1] + 2.0 * a[2] * T + 3.0 * a[3] * T * T + 4.0 * a[4] * T * T * T);
+    }
+    /* total derivatives of omega: wT[k] = d omega_k/dT, wC[k] = sum_m dwdC[k][m] C_m */
+    for (int k = 0; k < ns; ++k) {
+        double s = 0.0;
+        for (int mm = 0; mm < ns; ++mm) s += dwdC[(size_t)k * ns + mm] * C[mm];
+        wC[k] = s;
+        wT[k] = dwdT[k] - s / T;
+    }
+    double cp = 0.0, Q = 0.0, dcpT = 0.0;
+    for (int k = 0; k < ns; ++k) {
+        cp += Y[k] * ORC_R * cp_R[k] / m->W[k];
+        Q += ORC_R * T * h_RT[k] * w[k];
+        dcpT += Y[k] * dcp[k] / m->W[k];
+    }
+    double rc = rho * cp;
+    /* column T */
+    {
+        double dQ = 0.0;
+        for (int k = 0; k < ns; ++k) dQ += ORC_R * cp_R[k] * w[k] + ORC_R * T * h_RT[k] * wT[k];
+        double drc = -rc / T + rho * dcpT;
+        J[0] = -dQ / rc + Q * drc / (rc * rc);
+        for (int k = 0; k < ns; ++k)
+            J[(size_t)(1 + k) * n] = m->W[k] * wT[k] / rho + m->W[k] * w[k] / (rho * T);
+    }
+    /* columns Y_n */
+    for (int nn = 0; nn < ns; ++nn) {
+        double dQ = 0.0;
+        for (int k = 0; k < ns; ++k) {
+            double dw = dwdC[(size_t)k * ns + nn] * rho / m->W[nn] - wC[k] / (S * m->W[nn]);
+            dQ += ORC_R * T * h_RT[k] * dw;
+            J[(size_t)(1 + k) * n + 1 + nn] =
+                m->W[k] * dw / rho + m->W[k] * w[k] / (rho * S * m->W[nn]);
+        }
+        double drc = -rc / (S * m->W[nn]) + rho * ORC_R * cp_R[nn] / m->W[nn];
+        J[1 + nn] = -dQ / rc + Q * drc / (rc * rc);
+    }
+    free(buf);
+}

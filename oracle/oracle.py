@@ -3,7 +3,10 @@
 TEST INFRASTRUCTURE: imported only by the tests, by the package smoke check and
 by the benchmark's CPU-baseline / reference leg.  The CUDA library never
 imports, links or calls it.  It computes the plain per-cell, per-reaction
-definition of the net production rates (Eqs. 1-3, 5, 7, 8, 10 and Sec. 2.4).
+definition of the net production rates (Eqs. 1-3, 5, 7, 8, 10 and Sec. 2.4),
+and the constant-pressure adiabatic reactor built on them, integrated by
+scipy's Radau (an implicit Runge-Kutta method of order 5, a library routine
+independent of the Rosenbrock integrator of the CUDA library).
 
 Mechanisms are any object with the array attributes of
 ``paper_2008_08483_gb300.synth.Mechanism``; only the data is shared.
@@ -56,6 +59,9 @@ def _load():
             lib.orc_troe_F.restype = C.c_double
             lib.orc_cell_detail.argtypes = [P, C.c_double, P, P, P, P, P, P, P, P, P, P]
             lib.orc_jacobian_tc.argtypes = [P, C.c_double, P, P, P, P, P]
+            lib.orc_dwdC.argtypes = [P, C.c_double, P, P, P]
+            lib.orc_ode_rhs.argtypes = [P, C.c_double, P, P]
+            lib.orc_ode_jac.argtypes = [P, C.c_double, P, P]
             for f in (lib.orc_source_term_tpy, lib.orc_source_term_tc):
                 f.restype = C.c_int
             lib.orc_source_term_tpy.argtypes = [P, C.c_int64, P, P, P, C.c_int64, P, C.c_int64,
@@ -179,3 +185,55 @@ def jacobian_tc(mech, T: float, C_):
     g = np.zeros(om.ns)
     _load().orc_jacobian_tc(om.ref, float(T), _ptr(Cc), _ptr(h), _ptr(g), _ptr(J), _ptr(dT))
     return J, dT
+
+
+def dwdC(mech, T: float, C_):
+    """d omega / dC [ns, ns] and d omega / dT at fixed C [ns] (direct mass-action form)."""
+    om = _om(mech)
+    Cc = np.ascontiguousarray(C_, np.float64)
+    J = np.zeros((om.ns, om.ns))
+    dT = np.zeros(om.ns)
+    _load().orc_dwdC(om.ref, float(T), _ptr(Cc), _ptr(J), _ptr(dT))
+    return J, dT
+
+
+def ode_rhs(mech, P: float, y):
+    """Right-hand side of the constant-pressure adiabatic reactor, y = (T, Y_1..Y_ns)."""
+    om = _om(mech)
+    y = np.ascontiguousarray(y, np.float64)
+    f = np.zeros(om.ns + 1)
+    _load().orc_ode_rhs(om.ref, float(P), _ptr(y), _ptr(f))
+    return f
+
+
+def ode_jac(mech, P: float, y):
+    """Analytic Jacobian [ns+1, ns+1] of ode_rhs (row: component of f, column: of y)."""
+    om = _om(mech)
+    y = np.ascontiguousarray(y, np.float64)
+    J = np.zeros((om.ns + 1, om.ns + 1))
+    _load().orc_ode_jac(om.ref, float(P), _ptr(y), _ptr(J))
+    return J
+
+
+def integrate_reactor(mech, T0: float, P: float, Y0, t_end: float, rtol: float = 1e-10,
+                      atol: float = 1e-20, ign_dT: float = 400.0, t_eval=None):
+    """Constant-pressure adiabatic reactor from (T0, Y0) to t_end with scipy Radau on the
+    oracle's right-hand side and analytic Jacobian.  The ignition delay is the first time at
+    which T reaches T0 + ign_dT (an event located on Radau's dense output); NaN if never."""
+    from scipy.integrate import solve_ivp
+
+    om = _om(mech)
+    y0 = np.concatenate([[float(T0)], np.asarray(Y0, np.float64)])
+    target = float(T0) + ign_dT
+
+    def ev(t, y):
+        return y[0] - target
+    ev.direction = 1.0
+    sol = solve_ivp(lambda t, y: ode_rhs(om, P, y), (0.0, float(t_end)), y0, method="Radau",
+                    jac=lambda t, y: ode_jac(om, P, y), rtol=rtol, atol=atol, events=ev,
+                    t_eval=t_eval)
+    if sol.status != 0:
+        raise RuntimeError("oracle reactor integration failed: " + str(sol.message))
+    t_ign = float(sol.t_events[0][0]) if len(sol.t_events[0]) else float("nan")
+    return dict(y_end=sol.y[:, -1].copy(), t_ign=t_ign, nfev=int(sol.nfev),
+                njev=int(sol.njev), nsteps=int(len(sol.t) - 1) if t_eval is None else -1, sol=sol)

@@ -41,6 +41,15 @@ class _Desc(C.Structure):
                 ("p_ref", C.c_double)]
 
 
+class _IntegOpts(C.Structure):
+    _fields_ = [("h_init", C.c_double), ("h_min", C.c_double), ("h_max", C.c_double),
+                ("max_steps", C.c_int64), ("ign_dT", C.c_double), ("t_ign", C.c_void_p),
+                ("n_accepted", C.c_void_p), ("n_rejected", C.c_void_p)]
+
+
+CELL_OK, CELL_STEP_UNDERFLOW, CELL_MAX_STEPS = 0, 1, 2
+
+
 def lib():
     """The loaded CUDA library (raises ChemError if it is missing)."""
     global _lib
@@ -69,6 +78,14 @@ def lib():
             L.chem_source_term_jacobian.argtypes = [P, I64, P, P, I64, P, I64, C.c_int, P]
             for f in (L.chem_source_term_jvp, L.chem_source_term_vjp,
                       L.chem_source_term_jacobian):
+                f.restype = C.c_int
+            L.chem_ode_rhs.argtypes = [P, I64, P, P, P, I64, P, I64, P]
+            L.chem_ode_jacobian.argtypes = [P, I64, P, P, P, I64, P, P]
+            L.chem_integrate_cells.argtypes = [P, I64, P, P, P, I64, C.c_double, C.c_double,
+                                               C.c_double, C.POINTER(_IntegOpts), P, P]
+            L.chem_rosenbrock_tableau.argtypes = [C.POINTER(I32), P, P, P, P, P]
+            for f in (L.chem_ode_rhs, L.chem_ode_jacobian, L.chem_integrate_cells,
+                      L.chem_rosenbrock_tableau):
                 f.restype = C.c_int
             for f in (L.chem_mechanism_load, L.chem_mechanism_free, L.chem_mechanism_info,
                       L.chem_source_term, L.chem_source_term_host, L.chem_device_status):
@@ -289,3 +306,82 @@ def _omega_fn():
 def omega(mech: Mechanism, T, lnC, precision: int = FP64):
     """Differentiable omega(T, ln C) (torch.autograd), backward by chem_source_term_vjp."""
     return _omega_fn().apply(mech, T, lnC, precision)
+
+
+# ---------------------------------------------------------------------------------------
+# constant-pressure adiabatic reactor (chem_ode_rhs, chem_ode_jacobian, chem_integrate_cells)
+# ---------------------------------------------------------------------------------------
+
+def _check_reactor(T, P, Y):
+    import torch
+    for name, t in (("T", T), ("P", P), ("Y", Y)):
+        if not t.is_cuda or t.dtype != torch.float64:
+            raise ChemError(1, f"{name} must be a CUDA float64 tensor")
+    if T.stride(0) != 1 or P.stride(0) != 1 or Y.dim() != 2 or Y.stride(1) != 1:
+        raise ChemError(1, "T, P contiguous and Y row-major with unit column stride")
+
+
+def ode_rhs(mech: Mechanism, T, P, Y, stream=None):
+    """f [n, ns + 1] = (dT/dt, dY/dt) of the constant-pressure reactor at (T, P, Y)."""
+    import torch
+    _check_reactor(T, P, Y)
+    n = T.shape[0]
+    f = torch.empty((n, mech.n_species + 1), dtype=torch.float64, device=T.device)
+    _check(lib().chem_ode_rhs(mech.handle, n, T.data_ptr(), P.data_ptr(), Y.data_ptr(),
+                              Y.stride(0), f.data_ptr(), f.stride(0), _stream_ptr(stream)))
+    return f
+
+
+def ode_jacobian(mech: Mechanism, T, P, Y, stream=None):
+    """J [n, ns + 1, ns + 1] = d f / d (T, Y) of the constant-pressure reactor."""
+    import torch
+    _check_reactor(T, P, Y)
+    n, m = T.shape[0], mech.n_species + 1
+    J = torch.empty((n, m, m), dtype=torch.float64, device=T.device)
+    _check(lib().chem_ode_jacobian(mech.handle, n, T.data_ptr(), P.data_ptr(), Y.data_ptr(),
+                                   Y.stride(0), J.data_ptr(), _stream_ptr(stream)))
+    return J
+
+
+def integrate(mech: Mechanism, T, P, Y, t_end: float, rtol: float = 1e-6, atol: float = 1e-12,
+              h_init: float = 0.0, h_min: float = 0.0, h_max: float = 0.0, max_steps: int = 0,
+              ign_dT: float = 0.0, stats: bool = True, raise_on_failure: bool = False,
+              stream=None):
+    """Integrate the reactors in place (T and Y are overwritten with the state at t_end).
+    Returns a dict with per-cell 'status', 't_ign', 'n_accepted', 'n_rejected' (CUDA tensors)
+    and 'failed' (bool).  CHEM_ENONCONV raises only when raise_on_failure is set."""
+    import torch
+    _check_reactor(T, P, Y)
+    n = T.shape[0]
+    dev = T.device
+    status = torch.empty((n,), dtype=torch.int32, device=dev)
+    out = {"status": status}
+    opts = _IntegOpts(float(h_init), float(h_min), float(h_max), int(max_steps), float(ign_dT),
+                      None, None, None)
+    if stats:
+        out["t_ign"] = torch.empty((n,), dtype=torch.float64, device=dev)
+        out["n_accepted"] = torch.empty((n,), dtype=torch.int32, device=dev)
+        out["n_rejected"] = torch.empty((n,), dtype=torch.int32, device=dev)
+        opts.t_ign = out["t_ign"].data_ptr()
+        opts.n_accepted = out["n_accepted"].data_ptr()
+        opts.n_rejected = out["n_rejected"].data_ptr()
+    rc = lib().chem_integrate_cells(mech.handle, n, T.data_ptr(), P.data_ptr(), Y.data_ptr(),
+                                    Y.stride(0), float(t_end), float(rtol), float(atol),
+                                    C.byref(opts), status.data_ptr(), _stream_ptr(stream))
+    out["failed"] = rc == 8
+    if rc != 0 and (rc != 8 or raise_on_failure):
+        _check(rc)
+    return out
+
+
+def rosenbrock_tableau():
+    """Classical coefficients of the integrator's Rosenbrock method (host call)."""
+    s = C.c_int32()
+    g = C.c_double()
+    alpha, gamma = np.zeros((4, 4)), np.zeros((4, 4))
+    b, bh = np.zeros(4), np.zeros(4)
+    _check(lib().chem_rosenbrock_tableau(C.byref(s), C.byref(g), _ptr(alpha), _ptr(gamma),
+                                         _ptr(b), _ptr(bh)))
+    k = s.value
+    return dict(stages=k, gamma_ii=g.value, alpha=alpha[:k, :k], gamma=gamma[:k, :k], b=b[:k],
+                bhat=bh[:k])

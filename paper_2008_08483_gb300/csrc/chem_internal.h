@@ -56,6 +56,26 @@ struct alignas(16) SpecF32 {
     float pad[3];
 };
 
+// One reaction for the reactor integrator: the distinct species of the reaction as Jacobian
+// rows (net coefficient nu''_k - nu'_k != 0) and columns (any species on either side, with
+// its nu' and nu''), so that the per-reaction updates of omega and of d omega / dC touch
+// distinct entries.
+constexpr int kIntMax = 16;
+struct alignas(16) RxnInt {
+    int32_t nrow, ncol;
+    uint16_t row_sp[kIntMax];
+    uint16_t col_sp[kIntMax];
+    int8_t row_nu[kIntMax];
+    uint8_t col_nuf[kIntMax], col_nur[kIntMax];
+};
+
+struct IntView {
+    const RxnInt *rxn;
+    const double *nasa;          // [ns][2][7] NASA-7 sets (T < t_mid, T >= t_mid)
+    const double *W;             // [ns] molecular weights
+    bool ok;                     // every reaction fits kIntMax
+};
+
 struct MechViewF64 {
     int ns, nr;
     const RxnF64 *rxn;
@@ -85,6 +105,7 @@ struct chem_mech {
     void *d_blob;
     chem::MechViewF64 v64;
     chem::MechViewF32 v32;
+    chem::IntView vint;
     bool have_bf16;
     void *bf16;                  // split-BF16 tables (tensor-core path), see kern_bf16.cu
 };

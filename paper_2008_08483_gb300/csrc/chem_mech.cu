@@ -186,6 +186,8 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
     std::vector<float> tb_e32;
     std::vector<double> invW(ns);
     for (int k = 0; k < ns; ++k) invW[k] = 1.0 / d->mol_weight[k];
+    std::vector<RxnInt> rint(nr);
+    bool int_ok = true;
 
     for (int j = 0; j < nr; ++j) {
         RxnF64 &a = r64[j];
@@ -220,6 +222,27 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
         }
         a.nf = b.nf = nf;
         a.nr = b.nr = nrr;
+        {
+            RxnInt &c = rint[j];
+            memset(&c, 0, sizeof c);
+            for (int k = 0; k < ns && int_ok; ++k) {
+                int f = d->nu_f[(size_t)j * ns + k], p = d->nu_r[(size_t)j * ns + k];
+                if (!f && !p) continue;
+                if (c.ncol >= kIntMax) {
+                    int_ok = false;
+                    break;
+                }
+                c.col_sp[c.ncol] = (uint16_t)k;
+                c.col_nuf[c.ncol] = (uint8_t)f;
+                c.col_nur[c.ncol] = (uint8_t)p;
+                ++c.ncol;
+                if (p != f) {
+                    c.row_sp[c.nrow] = (uint16_t)k;
+                    c.row_nu[c.nrow] = (int8_t)(p - f);
+                    ++c.nrow;
+                }
+            }
+        }
         b.ordf = ordf;
         b.ordr = ordr;
         b.dnu = ordr - ordf;
@@ -276,7 +299,10 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
     size_t o_tbe64 = align(o_tbsp + sizeof(uint16_t) * ntb);
     size_t o_tbe32 = align(o_tbe64 + sizeof(double) * ntb);
     size_t o_invw = align(o_tbe32 + sizeof(float) * ntb);
-    size_t total = align(o_invw + sizeof(double) * ns);
+    size_t o_rint = align(o_invw + sizeof(double) * ns);
+    size_t o_nasa = align(o_rint + sizeof(RxnInt) * nr);
+    size_t o_w = align(o_nasa + sizeof(double) * 14 * ns);
+    size_t total = align(o_w + sizeof(double) * ns);
     std::vector<unsigned char> h(total, 0);
     memcpy(h.data() + o_r64, r64.data(), sizeof(RxnF64) * nr);
     memcpy(h.data() + o_r32, r32.data(), sizeof(RxnF32) * nr);
@@ -287,6 +313,9 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
         memcpy(h.data() + o_tbe32, tb_e32.data(), sizeof(float) * tb_e32.size());
     }
     memcpy(h.data() + o_invw, invW.data(), sizeof(double) * ns);
+    memcpy(h.data() + o_rint, rint.data(), sizeof(RxnInt) * nr);
+    memcpy(h.data() + o_nasa, d->nasa7, sizeof(double) * 14 * ns);
+    memcpy(h.data() + o_w, d->mol_weight, sizeof(double) * ns);
 
     chem_mech *m = new (std::nothrow) chem_mech();
     if (!m) return set_error(CHEM_ENOMEM, "host allocation failed");
@@ -328,6 +357,10 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
     m->v32.tb_e = (const float *)(base + o_tbe32);
     m->v32.t_mid = (float)d->t_mid;
     m->v32.lg2_pref_R = dsplit(log2(d->p_ref / kR));
+    m->vint.rxn = (const RxnInt *)(base + o_rint);
+    m->vint.nasa = (const double *)(base + o_nasa);
+    m->vint.W = (const double *)(base + o_w);
+    m->vint.ok = int_ok;
 
     st = bf16_build_tables(m, d);
     if (st != CHEM_OK && st != CHEM_EUNSUPPORTED) {

@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include "chem_internal.h"
+#include "rxn_terms.cuh"
 
 namespace chem {
 
@@ -34,12 +35,6 @@ struct TanArgs {
     int64_t ldJ;
 };
 
-__device__ __forceinline__ double dexp(double x) { return exp(x); }
-__device__ __forceinline__ float dexp(float x) { return expf(x); }
-__device__ __forceinline__ double dlog(double x) { return log(x); }
-__device__ __forceinline__ float dlog(float x) { return logf(x); }
-__device__ __forceinline__ double dlog10(double x) { return log10(x); }
-__device__ __forceinline__ float dlog10(float x) { return log10f(x); }
 
 template <typename R, int MODE, int BLK>
 __global__ void __launch_bounds__(BLK) k_tangent(MechViewF64 mv, TanArgs<R> a)
@@ -58,7 +53,7 @@ __global__ void __launch_bounds__(BLK) k_tangent(MechViewF64 mv, TanArgs<R> a)
     R ctot = 0, sdl = 0;
     for (int m = 0; m < ns; ++m) {
         const R l = a.lnC[i * a.ldC + m];
-        const R c = dexp(l);
+        const R c = rt_exp(l);
         sL[m * BLK] = l;
         sC[m * BLK] = c;
         ctot += c;
@@ -77,73 +72,25 @@ __global__ void __launch_bounds__(BLK) k_tangent(MechViewF64 mv, TanArgs<R> a)
         }
     }
     const R dT = MODE == kJvp ? a.dT[i] : R(0);
-    const R lnT = dlog(Ti), invT = R(1) / Ti, tau = Ti * R(1e-3);
-    const int rg = (double)Ti >= mv.t_mid ? 1 : 0;
+    const TFeat<R> tfe = t_features<R>(Ti, mv.t_mid);
     R gT = 0, Wtb = 0;      // vjp: cotangent of T; weight of the c_tot part of M
     for (int j = 0; j < mv.nr; ++j) {
         const RxnF64 *X = mv.rxn + j;
-        const R lkinf = R(X->lnA) + R(X->b) * lnT - R(X->EoR) * invT;
-        const R dlkinf = R(X->b) * invT + R(X->EoR) * invT * invT;
-        R lmod = 0, dmod_dlM = 0, dmod_dT = 0, M = 1;
-        bool dead = false;
         const int kind = X->kind;
+        R M = 1;
         if (kind != 0) {
             M = ctot;
             for (int t = X->tb_begin; t < X->tb_end; ++t) M += R(mv.tb_e[t]) * sC[mv.tb_sp[t] * BLK];
-            if (!(M > R(0))) {
-                dead = true;
-            } else if (kind == 1) {
-                lmod = dlog(M);
-                dmod_dlM = 1;
-            } else {
-                const R lk0 = R(X->low[0]) + R(X->low[1]) * lnT - R(X->low[2]) * invT;
-                const R Pr = dexp(lk0 - lkinf) * M;
-                if (!(Pr > R(0))) {
-                    dead = true;
-                } else {
-                    lmod = dlog(Pr / (R(1) + Pr));
-                    R dlF_dlPr = 0, dlF_dT = 0;
-                    if (kind == 3) {
-                        const R e3 = dexp(-Ti * R(X->troe[2])), e1 = dexp(-Ti * R(X->troe[3]));
-                        R Fc = R(X->troe[0]) * e3 + R(X->troe[1]) * e1;
-                        R dFc = -R(X->troe[0]) * R(X->troe[2]) * e3 - R(X->troe[1]) * R(X->troe[3]) * e1;
-                        if (X->troe[4] > 0.0) {
-                            const R e2 = dexp(-R(X->troe[4]) * invT);
-                            Fc += e2;
-                            dFc += R(X->troe[4]) * invT * invT * e2;
-                        }
-                        const R L = dlog10(Fc);
-                        const R dL_dT = dFc / (Fc * R(2.302585092994045684));
-                        const R c = R(-0.4) - R(0.67) * L, nn = R(0.75) - R(1.27) * L;
-                        const R x = dlog10(Pr) + c;
-                        const R D = nn - R(0.14) * x;
-                        const R f1 = x / D, g = R(1) + f1 * f1;
-                        lmod += L / g * R(2.302585092994045684);
-                        dlF_dlPr = -L * R(2) * f1 / (g * g) * (nn / (D * D));
-                        const R dD_dL = R(-1.27) + R(0.14) * R(0.67);
-                        const R df1_dL = (R(-0.67) * D - x * dD_dL) / (D * D);
-                        dlF_dT = (R(1) / g - L * R(2) * f1 / (g * g) * df1_dL) * dL_dT;
-                    }
-                    dmod_dlM = R(1) / (R(1) + Pr) + dlF_dlPr;
-                    const R dlPr_dT = (R(X->low[1]) - R(X->b)) * invT +
-                                      (R(X->low[2]) - R(X->EoR)) * invT * invT;
-                    dmod_dT = dmod_dlM * dlPr_dT + dlF_dT * R(2.302585092994045684);
-                }
-            }
         }
-        if (dead) continue;
-        const double *kc = X->kc[rg];
-        const R lKc = R(kc[0]) + R(kc[1]) * lnT +
-                      tau * (R(kc[2]) + tau * (R(kc[3]) + tau * (R(kc[4]) + tau * R(kc[5])))) +
-                      R(kc[6]) * invT;
-        const R dlKc = R(kc[1]) * invT +
-                       (R(kc[2]) + tau * (R(2) * R(kc[3]) + tau * (R(3) * R(kc[4]) + tau * R(4) * R(kc[5])))) * R(1e-3) -
-                       R(kc[6]) * invT * invT;
+        const RxnTerms<R> rt = rxn_terms<R>(X, tfe, M);
+        if (rt.dead) continue;
+        const R lkinf = rt.lkinf, lmod = rt.lmod, dmod_dlM = rt.dmod_dlM, dmod_dT = rt.dmod_dT;
+        const R lKc = rt.lKc, dlKc = rt.dlKc, dlkinf = rt.dlkinf;
         R sf = lkinf + lmod, sr = lkinf + lmod - lKc;
         for (int t = 0; t < X->nf; ++t) sf += R(X->nuf[t]) * sL[X->spf[t] * BLK];
         for (int t = 0; t < X->nr; ++t) sr += R(X->nur[t]) * sL[X->spr[t] * BLK];
-        const R qf = dexp(sf);
-        const R qr = X->rev ? dexp(sr) : R(0);
+        const R qf = rt_exp(sf);
+        const R qr = X->rev ? rt_exp(sr) : R(0);
         const R dlkf_dT = dlkinf + dmod_dT;            // d ln k_f / dT
         if (MODE == kJvp) {
             R dlM = 0;
