@@ -336,6 +336,8 @@ def main():
 
     if rank == 0 and not args.no_extras:
         extras(line, h, mech, T, P, Y, dev, dev32, out32, ns, prec_name, stream, args)
+        extras_integrator(line, mech, dev, stream)
+        extras_heavy(line, dev, stream)
     if rank == 0:
         print(json.dumps(line), flush=True)
     h.close()
@@ -413,6 +415,100 @@ def extras(line, h, mech, T, P, Y, dev, dev32, out32, ns, prec_name, stream, arg
     if "fp64" in paths and "cells_per_s" in paths.get(prec_name, {}):
         paths["speedup_vs_fp64"] = paths[prec_name]["cells_per_s"] / paths["fp64"]["cells_per_s"]
     line["paths"] = paths
+
+
+def extras_integrator(line, mech, dev, stream, n=4096, t_end=1e-2, rtol=1e-6, atol=1e-12):
+    """Batched constant-pressure autoignition: 4096 reactors of the 53/325 mechanism,
+    T0 ~ U[900,1400] K, P0 ~ U[1,20] atm, phi ~ U[0.5,2], integrated to 10 ms (Rodas3, FP64
+    LU and error control); the ignition delay of two reactors against the oracle's Radau."""
+    import torch
+    from paper_2008_08483_gb300 import chem, synth
+    h = chem.Mechanism(mech)
+    T, P, Y, _ = synth.make_ignition_states(mech, n, seed=STATE_SEED)
+    Tt, Pt, Yt = (torch.as_tensor(a, dtype=torch.float64, device=dev) for a in (T, P, Y))
+    # warm-up on a copy of a few reactors (kernel attributes, allocator)
+    chem.integrate(h, Tt[:64].clone(), Pt[:64].clone(), Yt[:64].clone(), 1e-6)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = chem.kernel_launch_count()
+    t0 = time.perf_counter()
+    e0.record(stream)
+    out = chem.integrate(h, Tt, Pt, Yt, t_end, rtol=rtol, atol=atol, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = e0.elapsed_time(e1)
+    nacc = out["n_accepted"].cpu().numpy()
+    nrej = out["n_rejected"].cpu().numpy()
+    t_ign = out["t_ign"].cpu().numpy()
+    res = {"workload": f"{n} reactors, 53/325, to {t_end} s, rtol {rtol}, atol {atol}",
+           "ms": ms, "wall_s": wall, "reactors_per_s": n / (ms * 1e-3),
+           "reactor_steps_per_s": float(nacc.sum() + nrej.sum()) / (ms * 1e-3),
+           "steps_mean": float(nacc.mean()), "steps_max": int(nacc.max()),
+           "rejected_mean": float(nrej.mean()), "failed": int(out["failed"]),
+           "ignited": int((t_ign > 0).sum()), "t_ign_median_s": float(np.median(t_ign)),
+           "launches": int(chem.kernel_launch_count() - n0)}
+    # cpu_baseline leg of this workload: the oracle's reactor under scipy Radau on two
+    # reactors at the same tolerances (timed), and the ignition delay of reactor 0 against a
+    # tight Radau run
+    from oracle import oracle as O
+    om = O.OracleMechanism(mech)
+    tc = time.perf_counter()
+    for i in (0, 1):
+        O.integrate_reactor(om, T[i], P[i], Y[i], t_end, rtol=rtol, atol=atol)
+    tc = time.perf_counter() - tc
+    res["cpu_baseline"] = {"value": 2.0 / tc, "unit": "reactors/s", "cores": 1, "kind": "oracle",
+                           "sample": "reactors 0 and 1, scipy Radau on the oracle right-hand "
+                                     f"side and Jacobian at rtol {rtol}, atol {atol}"}
+    ref = O.integrate_reactor(om, T[0], P[0], Y[0], t_end, rtol=1e-9, atol=1e-20)
+    res["t_ign_rel_err_vs_radau"] = {"cell": 0, "err": float(abs(t_ign[0] / ref["t_ign"] - 1.0)),
+                                     "radau_rtol": 1e-9}
+    h.close()
+    line["integrator"] = res
+
+
+def extras_heavy(line, dev, stream, n=1 << 18):
+    """160 species / 1000 reactions, 2^18 cells: source term per precision and the
+    derivative kernels (jvp, vjp, dense Jacobian) alongside."""
+    import torch
+    from paper_2008_08483_gb300 import chem, synth
+    mech = synth.make_mechanism("heavy_160_1000", seed=MECH_SEED)
+    h = chem.Mechanism(mech)
+    T, P, Y = synth.make_states(mech, n, seed=STATE_SEED, T_range=(700.0, 2600.0),
+                                P_atm=(1.0, 100.0))
+    res = {"workload": f"160/1000, {n} cells, T~U[700,2600] K, P~logU[1,100] atm"}
+    for name in ("fp64", "fp32", "split_bf16"):
+        p = chem.PRECISIONS[name]
+        dt = torch.float64 if p == chem.FP64 else torch.float32
+        din = [torch.as_tensor(a, dtype=dt, device=dev) for a in (T, P, Y)]
+        o = torch.empty((n, mech.n_species), dtype=dt, device=dev)
+        try:
+            ms = time_device(lambda: chem.source_term(h, *din, p, out=o, stream=stream),
+                             5, 2, stream, 1, dev)
+            res[name] = {"cells_per_s": n / (ms * 1e-3), "ms_per_call": ms}
+        except chem.ChemError as e:
+            res[name] = {"status": str(e)}
+    # (T, ln C) states of the first 256 cells: C_k = rho Y_k / W_k, rho = P / (R T sum Y/W)
+    Wk = mech.mol_weight
+    rho = P[:256] / (synth.R_CGS * T[:256] * (Y[:256] / Wk).sum(1))
+    lnC = np.log(np.maximum(rho[:, None] * Y[:256] / Wk, 1e-300))
+    lnC = np.tile(lnC, (n // 256, 1))
+    Tn = np.tile(T[:256], n // 256)
+    for name in ("fp64", "fp32"):
+        p = chem.PRECISIONS[name]
+        dt = torch.float64 if p == chem.FP64 else torch.float32
+        Tt = torch.as_tensor(Tn, dtype=dt, device=dev)
+        lt = torch.as_tensor(lnC, dtype=dt, device=dev)
+        g = torch.ones((n, mech.n_species), dtype=dt, device=dev)
+        dT = torch.ones((n,), dtype=dt, device=dev)
+        ms_j = time_device(lambda: chem.source_term_jvp(h, Tt, lt, dT, lt, p, stream=stream),
+                           3, 1, stream, 1, dev)
+        ms_v = time_device(lambda: chem.source_term_vjp(h, Tt, lt, g, p, stream=stream),
+                           3, 1, stream, 1, dev)
+        res[f"jvp_{name}"] = {"cells_per_s": n / (ms_j * 1e-3), "ms_per_call": ms_j}
+        res[f"vjp_{name}"] = {"cells_per_s": n / (ms_v * 1e-3), "ms_per_call": ms_v}
+    h.close()
+    line["heavy_160_1000"] = res
 
 
 if __name__ == "__main__":

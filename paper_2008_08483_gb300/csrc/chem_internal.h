@@ -65,12 +65,20 @@ struct alignas(16) RxnInt {
     int32_t nrow, ncol;
     uint16_t row_sp[kIntMax];
     uint16_t col_sp[kIntMax];
-    int8_t row_nu[kIntMax];
     uint8_t col_nuf[kIntMax], col_nur[kIntMax];
+    double row_nu[kIntMax];      // nu''_k - nu'_k
 };
 
 struct IntView {
     const RxnInt *rxn;
+    const int32_t *order;        // [n_slots] reaction processing order, -1 = empty slot;
+                                 // grouped by kind in blocks of 32 (warp-uniform kind)
+    int32_t n_slots;
+    // per group of 32 slots, the reactions of the group that change species k:
+    // entries gptr[g (ns + 1) + k] .. gptr[g (ns + 1) + k + 1] of (slot, nu''_k - nu'_k)
+    const int32_t *gptr;
+    const int32_t *gent_slot;
+    const double *gent_nu;
     const double *nasa;          // [ns][2][7] NASA-7 sets (T < t_mid, T >= t_mid)
     const double *W;             // [ns] molecular weights
     bool ok;                     // every reaction fits kIntMax

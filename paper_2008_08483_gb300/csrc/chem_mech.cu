@@ -188,6 +188,14 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
     for (int k = 0; k < ns; ++k) invW[k] = 1.0 / d->mol_weight[k];
     std::vector<RxnInt> rint(nr);
     bool int_ok = true;
+    // integrator processing order: reactions grouped by kind, each kind padded to a multiple
+    // of 32 slots so that a warp's 32 reactions share one kind
+    std::vector<int32_t> order;
+    for (int kd = 0; kd <= 3; ++kd) {
+        for (int j = 0; j < nr; ++j)
+            if (d->kind[j] == kd) order.push_back(j);
+        while (order.size() % 32) order.push_back(-1);
+    }
 
     for (int j = 0; j < nr; ++j) {
         RxnF64 &a = r64[j];
@@ -238,7 +246,7 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
                 ++c.ncol;
                 if (p != f) {
                     c.row_sp[c.nrow] = (uint16_t)k;
-                    c.row_nu[c.nrow] = (int8_t)(p - f);
+                    c.row_nu[c.nrow] = (double)(p - f);
                     ++c.nrow;
                 }
             }
@@ -302,7 +310,31 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
     size_t o_rint = align(o_invw + sizeof(double) * ns);
     size_t o_nasa = align(o_rint + sizeof(RxnInt) * nr);
     size_t o_w = align(o_nasa + sizeof(double) * 14 * ns);
-    size_t total = align(o_w + sizeof(double) * ns);
+    // per group of 32 slots: species -> (slot, net coefficient) lists
+    const size_t n_groups = order.size() / 32;
+    std::vector<int32_t> gptr(n_groups * (ns + 1) + 1, 0), gslot;
+    std::vector<double> gnu;
+    for (size_t g = 0; g < n_groups; ++g) {
+        for (int k = 0; k < ns; ++k) {
+            gptr[g * (ns + 1) + k] = (int32_t)gslot.size();
+            for (int r = 0; r < 32; ++r) {
+                int j = order[g * 32 + r];
+                if (j < 0) continue;
+                int nu = d->nu_r[(size_t)j * ns + k] - d->nu_f[(size_t)j * ns + k];
+                if (nu) {
+                    gslot.push_back(r);
+                    gnu.push_back((double)nu);
+                }
+            }
+        }
+        gptr[g * (ns + 1) + ns] = (int32_t)gslot.size();
+    }
+    const size_t nge = gslot.size() ? gslot.size() : 1;
+    size_t o_ord = align(o_w + sizeof(double) * ns);
+    size_t o_gptr = align(o_ord + sizeof(int32_t) * order.size());
+    size_t o_gslot = align(o_gptr + sizeof(int32_t) * gptr.size());
+    size_t o_gnu = align(o_gslot + sizeof(int32_t) * nge);
+    size_t total = align(o_gnu + sizeof(double) * nge);
     std::vector<unsigned char> h(total, 0);
     memcpy(h.data() + o_r64, r64.data(), sizeof(RxnF64) * nr);
     memcpy(h.data() + o_r32, r32.data(), sizeof(RxnF32) * nr);
@@ -316,6 +348,12 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
     memcpy(h.data() + o_rint, rint.data(), sizeof(RxnInt) * nr);
     memcpy(h.data() + o_nasa, d->nasa7, sizeof(double) * 14 * ns);
     memcpy(h.data() + o_w, d->mol_weight, sizeof(double) * ns);
+    memcpy(h.data() + o_ord, order.data(), sizeof(int32_t) * order.size());
+    memcpy(h.data() + o_gptr, gptr.data(), sizeof(int32_t) * gptr.size());
+    if (!gslot.empty()) {
+        memcpy(h.data() + o_gslot, gslot.data(), sizeof(int32_t) * gslot.size());
+        memcpy(h.data() + o_gnu, gnu.data(), sizeof(double) * gnu.size());
+    }
 
     chem_mech *m = new (std::nothrow) chem_mech();
     if (!m) return set_error(CHEM_ENOMEM, "host allocation failed");
@@ -361,6 +399,11 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
     m->vint.nasa = (const double *)(base + o_nasa);
     m->vint.W = (const double *)(base + o_w);
     m->vint.ok = int_ok;
+    m->vint.order = (const int32_t *)(base + o_ord);
+    m->vint.n_slots = (int32_t)order.size();
+    m->vint.gptr = (const int32_t *)(base + o_gptr);
+    m->vint.gent_slot = (const int32_t *)(base + o_gslot);
+    m->vint.gent_nu = (const double *)(base + o_gnu);
 
     st = bf16_build_tables(m, d);
     if (st != CHEM_OK && st != CHEM_EUNSUPPORTED) {

@@ -48,6 +48,7 @@ namespace chem {
 // ---------------------------------------------------------------------------------------
 
 constexpr int kStages = 4;
+constexpr int kDStride = kIntMax + 1;
 
 // classical Rodas3 table
 static const double kGammaII = 0.5;
@@ -108,6 +109,8 @@ struct WarpLayout {
     int nv, nsp;         // padded vector lengths
     int oY, oYs, oR, oU, oYn, oInvd, oPiv;    // vectors; U holds kStages vectors
     int oC, oH, oCp, oDcp, oWo, oJT, oVM, oWC, oAK;   // per-species arrays
+    int oD;              // [32][kDStride] per-column derivatives of one group of reactions
+    int oQ;              // [3][32] q_net, d q_net/dT, d q_net/dM of one group
     int oMat;            // matrix offset when it lives in shared memory, else -1
     int per_warp;        // doubles of shared memory per warp
 };
@@ -136,6 +139,8 @@ static WarpLayout make_layout(int ns, bool mat_in_smem)
     L.oVM = o; o += L.nsp;
     L.oWC = o; o += L.nsp;
     L.oAK = o; o += L.nsp;
+    L.oD = o; o += 32 * kDStride;
+    L.oQ = o; o += 96;
     if (mat_in_smem) {
         L.oMat = o;
         o += L.n * L.ldw;
@@ -182,7 +187,7 @@ __device__ __forceinline__ double ipow(double c, int e)
 struct Ctx {
     double *y, *ys, *r, *U, *yn, *invd;
     int *piv, *pv;
-    double *C, *H, *Cp, *Dcp, *Wo, *JT, *VM, *WC, *AK;
+    double *C, *H, *Cp, *Dcp, *Wo, *JT, *VM, *WC, *AK, *D, *Q;
     double *A;                // matrix, row-major with leading dimension ldw
 };
 
@@ -206,6 +211,8 @@ __device__ __forceinline__ Ctx make_ctx(double *base, double *mat, const WarpLay
     c.VM = base + L.oVM;
     c.WC = base + L.oWC;
     c.AK = base + L.oAK;
+    c.D = base + L.oD;
+    c.Q = base + L.oQ;
     c.A = mat;
     return c;
 }
@@ -245,10 +252,11 @@ __device__ void reactor_eval(const MechViewF64 &mv, const IntView &iv, const War
     }
     __syncwarp();
     const double ctot = P / (kR * T);     // sum_k C_k
-    for (int g = 0; g < mv.nr; g += 32) {
-        const int j = g + lane;
-        double kf = 0.0, kr = 0.0, qn = 0.0, dqT = 0.0, dqM = 0.0;
-        if (j < mv.nr) {
+    for (int g = 0; g < iv.n_slots; g += 32) {
+        // phase A: one reaction per lane (all lanes of a group share the reaction kind)
+        const int j = iv.order[g + lane];
+        double qn = 0.0, dqT = 0.0, dqM = 0.0;
+        if (j >= 0) {
             const RxnF64 *X = mv.rxn + j;
             double M = 1.0;
             if (X->kind != 0) {
@@ -256,6 +264,7 @@ __device__ void reactor_eval(const MechViewF64 &mv, const IntView &iv, const War
                 for (int t = X->tb_begin; t < X->tb_end; ++t) M += mv.tb_e[t] * c.C[mv.tb_sp[t]];
             }
             const RxnTerms<double> rt = rxn_terms<double>(X, tf, M);
+            double kf = 0.0, kr = 0.0;
             if (!rt.dead) {
                 kf = exp(rt.lkinf + rt.lmod);
                 kr = X->rev ? exp(rt.lkinf + rt.lmod - rt.lKc) : 0.0;
@@ -270,66 +279,71 @@ __device__ void reactor_eval(const MechViewF64 &mv, const IntView &iv, const War
                     if (X->kind != 0) dqM = qn * rt.dmod_dlM / M;
                 }
             }
-        }
-        const int cnt = min(32, mv.nr - g);
-        for (int r = 0; r < cnt; ++r) {
-            const double bq = __shfl_sync(0xffffffffu, qn, r);
-            const RxnInt *I = iv.rxn + g + r;
-            const int nrow = I->nrow;
-            double bkf = 0.0, bkr = 0.0, bdT = 0.0, bdM = 0.0;
             if (JAC) {
-                bkf = __shfl_sync(0xffffffffu, kf, r);
-                bkr = __shfl_sync(0xffffffffu, kr, r);
-                bdT = __shfl_sync(0xffffffffu, dqT, r);
-                bdM = __shfl_sync(0xffffffffu, dqM, r);
-            }
-            if (lane < nrow) {
-                const int k = I->row_sp[lane];
-                const double nu = (double)I->row_nu[lane];
-                c.Wo[k] += nu * bq;
-                if (JAC) {
-                    c.JT[k] += nu * bdT;
-                    c.VM[k] += nu * bdM;
-                }
-            }
-            if (JAC) {
-                // mass-action part of d q_net / dC_m for the columns of this reaction
-                const int ncol = I->ncol, np = nrow * ncol;
-                for (int p = lane; p < np; p += 32) {
-                    const int t = p / ncol, cc = p - t * ncol;
-                    const int k = I->row_sp[t], m = I->col_sp[cc];
-                    double df = 0.0, dr = 0.0;
+                // mass-action part of d q_net / dC_m for each column m of the reaction:
+                // k_f nu'_m C_m^(nu'_m - 1) prod_{u != m} C_u^nu'_u - (same for the reverse)
+                const RxnInt *I = iv.rxn + j;
+                const int ncol = I->ncol;
+                for (int cc = 0; cc < ncol; ++cc) {
                     const int ef = I->col_nuf[cc], er = I->col_nur[cc];
-                    if (ef) {
-                        df = bkf * (double)ef * ipow(c.C[m], ef - 1);
-                        for (int u = 0; u < ncol; ++u)
-                            if (u != cc && I->col_nuf[u]) df *= ipow(c.C[I->col_sp[u]], I->col_nuf[u]);
+                    const double cm = c.C[I->col_sp[cc]];
+                    double df = 0.0, dr = 0.0;
+                    if (ef) df = kf * (double)ef * ipow(cm, ef - 1);
+                    if (er && kr != 0.0) dr = kr * (double)er * ipow(cm, er - 1);
+                    for (int u = 0; u < ncol; ++u) {
+                        if (u == cc) continue;
+                        const double cu = c.C[I->col_sp[u]];
+                        if (I->col_nuf[u]) df *= ipow(cu, I->col_nuf[u]);
+                        if (I->col_nur[u]) dr *= ipow(cu, I->col_nur[u]);
                     }
-                    if (er && bkr != 0.0) {
-                        dr = bkr * (double)er * ipow(c.C[m], er - 1);
-                        for (int u = 0; u < ncol; ++u)
-                            if (u != cc && I->col_nur[u]) dr *= ipow(c.C[I->col_sp[u]], I->col_nur[u]);
-                    }
-                    c.A[(1 + k) * ldw + 1 + m] += (double)I->row_nu[t] * (df - dr);
+                    c.D[lane * kDStride + cc] = df - dr;
                 }
-                // listed third-body efficiencies: (eff_m - 1) part of d q_net / dC_m
-                if (bdM != 0.0) {
-                    const RxnF64 *X = mv.rxn + g + r;
-                    const int nt = X->tb_end - X->tb_begin;
-                    if (nt > 0) {
-                        __syncwarp();
-                        const int npt = nrow * nt;
-                        for (int p = lane; p < npt; p += 32) {
-                            const int t = p / nt, cc = p - t * nt;
-                            const int k = I->row_sp[t], m = mv.tb_sp[X->tb_begin + cc];
-                            c.A[(1 + k) * ldw + 1 + m] +=
-                                (double)I->row_nu[t] * bdM * mv.tb_e[X->tb_begin + cc];
-                        }
+            }
+        }
+        c.Q[lane] = qn;
+        if (JAC) {
+            c.Q[32 + lane] = dqT;
+            c.Q[64 + lane] = dqM;
+        }
+        __syncwarp();
+        // phase B: each lane gathers the group's contributions to its own species rows
+        // (fixed order: slot order within the group), so no two lanes touch one entry
+        const int *gp = iv.gptr + (g >> 5) * (ns + 1);
+        for (int k = lane; k < ns; k += 32) {
+            const int e0 = gp[k], e1 = gp[k + 1];
+            double w = 0.0, jt = 0.0, vm = 0.0;
+            for (int e = e0; e < e1; ++e) {
+                const int r = iv.gent_slot[e];
+                const double nu = iv.gent_nu[e];
+                w += nu * c.Q[r];
+                if (JAC) {
+                    jt += nu * c.Q[32 + r];
+                    vm += nu * c.Q[64 + r];
+                }
+            }
+            c.Wo[k] += w;
+            if (JAC) {
+                c.JT[k] += jt;
+                c.VM[k] += vm;
+                double *Ak = c.A + (1 + k) * ldw + 1;
+                for (int e = e0; e < e1; ++e) {
+                    const int r = iv.gent_slot[e];
+                    const double nu = iv.gent_nu[e];
+                    const int jr = iv.order[g + r];
+                    const RxnInt *I = iv.rxn + jr;
+                    const int ncol = I->ncol;
+                    for (int cc = 0; cc < ncol; ++cc) Ak[I->col_sp[cc]] += nu * c.D[r * kDStride + cc];
+                    // listed third-body efficiencies: (eff_m - 1) part of d q_net / dC_m
+                    const double dm = c.Q[64 + r];
+                    if (dm != 0.0) {
+                        const RxnF64 *X = mv.rxn + jr;
+                        const double s = nu * dm;
+                        for (int t = X->tb_begin; t < X->tb_end; ++t) Ak[mv.tb_sp[t]] += s * mv.tb_e[t];
                     }
                 }
             }
-            __syncwarp();
         }
+        __syncwarp();
     }
     __syncwarp();
     // right-hand side
@@ -442,7 +456,18 @@ __device__ bool lu_factor(const Ctx &c, int n, int ldw, int lane)
         __syncwarp();
         for (int jc = k + 1 + lane; jc < n; jc += 32) {
             const double u = A[k * ldw + jc];
-            for (int i = k + 1; i < n; ++i) A[i * ldw + jc] -= A[i * ldw + k] * u;
+            int i = k + 1;
+            for (; i + 7 < n; i += 8) {            // 8 rows per batch: loads issue together
+                double a[8], b[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    a[q] = A[(i + q) * ldw + k];
+                    b[q] = A[(i + q) * ldw + jc];
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) A[(i + q) * ldw + jc] = b[q] - a[q] * u;
+            }
+            for (; i < n; ++i) A[i * ldw + jc] -= A[i * ldw + k] * u;
         }
         __syncwarp();
     }
@@ -460,9 +485,32 @@ __device__ bool lu_factor(const Ctx &c, int n, int ldw, int lane)
 }
 
 // x = A^-1 b for the factors of lu_factor; b is read from rhs, x written to x (distinct).
+// Systems of up to 64 unknowns keep x in registers (two per lane) and broadcast each solved
+// component with a shuffle; larger ones work in shared memory.
 __device__ void lu_solve(const Ctx &c, int n, int ldw, const double *rhs, double *x, int lane)
 {
     const double *A = c.A;
+    if (n <= 64) {
+        const int i0 = lane, i1 = lane + 32;
+        double x0 = i0 < n ? rhs[c.pv[i0]] : 0.0;
+        double x1 = i1 < n ? rhs[c.pv[i1]] : 0.0;
+        for (int j = 0; j < n - 1; ++j) {
+            const double xj = __shfl_sync(0xffffffffu, j < 32 ? x0 : x1, j & 31);
+            if (i0 > j && i0 < n) x0 -= A[i0 * ldw + j] * xj;
+            if (i1 > j && i1 < n) x1 -= A[i1 * ldw + j] * xj;
+        }
+        for (int j = n - 1; j >= 0; --j) {
+            const double xj = __shfl_sync(0xffffffffu, j < 32 ? x0 : x1, j & 31) * c.invd[j];
+            if (i0 < j) x0 -= A[i0 * ldw + j] * xj;
+            else if (i0 == j) x0 = xj;
+            if (i1 < j) x1 -= A[i1 * ldw + j] * xj;
+            else if (i1 == j) x1 = xj;
+        }
+        if (i0 < n) x[i0] = x0;
+        if (i1 < n) x[i1] = x1;
+        __syncwarp();
+        return;
+    }
     for (int i = lane; i < n; i += 32) x[i] = rhs[c.pv[i]];
     __syncwarp();
     for (int j = 0; j < n - 1; ++j) {
