@@ -226,8 +226,10 @@ enum { CHEM_CELL_OK = 0, CHEM_CELL_STEP_UNDERFLOW = 1, CHEM_CELL_MAX_STEPS = 2 }
 
 /* Options of chem_integrate_cells; a NULL pointer means all defaults. */
 typedef struct {
-    double h_init;          /* first step (s); <= 0: min(1e-10 s, t_end) */
-    double h_min;           /* a cell fails when its step falls below this (s); <= 0: 1e-20 */
+    double h_init;          /* first step (s); <= 0: automatic, 0.01 |y| / |f(y0)| in the
+                               error norm's weighted RMS, at most t_end */
+    double h_min;           /* a cell fails when its step falls below this (s); <= 0: only
+                               when a step no longer advances t in double precision */
     double h_max;           /* largest step (s); <= 0: t_end */
     int64_t max_steps;      /* attempted steps per cell before it fails; <= 0: 100000 */
     double ign_dT;          /* ignition event: first time T reaches T0 + ign_dT; <= 0: 400 K */
@@ -265,6 +267,86 @@ chem_status chem_integrate_cells(const chem_mech *mech, int64_t n_cells, double 
  */
 chem_status chem_rosenbrock_tableau(int32_t *stages, double *gamma_ii, double *alpha,
                                     double *gamma, double *b, double *bhat);
+
+/*
+ * Serving: a persistent request loop for many producers (the paper's offload pattern, in
+ * which every CFD rank hands its cells to the GPU for the source term, Secs. 1 and 3.2).
+ * A server owns one host worker thread, a fixed set of device slots (each a stream with
+ * device buffers and page-locked host staging, sized from the HBM budget at creation) and
+ * the CUDA graphs it has captured.  submit() only queues; the worker packs queued requests
+ * that share (mechanism, kind, precision, dt, tolerances) into one batch for a free slot,
+ * copies the batch to the device, replays the slot's graph for the batch's power-of-two
+ * size bucket (capturing it on first use) and copies the results back, while other slots'
+ * batches run: requests that arrive while the GPU is busy join the next free slot.  Cells
+ * are independent, so a request's result does not depend on the batch it ran in.
+ * The mechanisms must outlive the server.  All calls are thread-safe.
+ */
+enum { CHEM_REQ_SOURCE = 0, CHEM_REQ_INTEGRATE = 1 };
+
+typedef struct {
+    int32_t mech_index;         /* index into the server's mechanism list */
+    int32_t kind;               /* CHEM_REQ_SOURCE or CHEM_REQ_INTEGRATE */
+    chem_precision precision;   /* SOURCE: element type of T, P, Y, omega (CHEM_FP64: double,
+                                   otherwise float); INTEGRATE: must be CHEM_FP64 */
+    int32_t reserved;
+    int64_t n_cells;            /* >= 1 */
+    const void *T, *P, *Y;      /* HOST arrays [n], [n], [n][n_species] (dense rows) */
+    void *omega;                /* SOURCE: HOST output [n][n_species] */
+    double *T_out, *Y_out;      /* INTEGRATE: HOST outputs [n], [n][n_species]; may alias T, Y */
+    int32_t *cell_status;       /* INTEGRATE: HOST output [n] (CHEM_CELL_*), or NULL */
+    double dt, rtol, atol;      /* INTEGRATE: time to advance (s) and tolerances */
+} chem_request;
+
+typedef struct {
+    chem_status status;         /* of the request's batch; CHEM_ENONCONV: some cell failed */
+    int32_t batch_requests;     /* requests in the batch it ran in */
+    int64_t n_cells;
+    int64_t batch_cells;        /* cells of that batch */
+    int32_t n_failed;           /* INTEGRATE: cells with a nonzero status */
+    int32_t slot;
+    double queue_us;            /* submit -> batch launch */
+    double latency_us;          /* submit -> results in the caller's host arrays */
+} chem_result;
+
+typedef struct {
+    int32_t n_slots;
+    int64_t slot_cells;         /* capacity of one slot (largest request) */
+    size_t device_bytes;        /* device memory the server holds */
+    uint64_t submitted, completed, batches, graphs_captured, graph_launches;
+    int32_t max_batch_requests; /* most requests seen in one batch */
+} chem_serve_info;
+
+/*
+ * Create a server for n_mechs loaded mechanisms (same device) within hbm_budget bytes of
+ * device memory, split into 4 slots.  Errors: CHEM_EINVAL, CHEM_ENOMEM (budget below one
+ * slot of 64 cells of the largest mechanism, or an allocation failed), CHEM_ECUDA.
+ */
+chem_status chem_serve_create(const chem_mech *const *mechs, int32_t n_mechs, size_t hbm_budget,
+                              void **server);
+
+/*
+ * Queue a request without blocking; *ticket identifies it.  The host arrays must stay valid
+ * until chem_serve_poll reports the request complete.  Errors, synchronous: CHEM_EINVAL
+ * (malformed request), CHEM_ENOMEM (n_cells above the slot capacity: over budget),
+ * CHEM_EUNSUPPORTED (a path this mechanism does not support), CHEM_EBUSY (server stopping).
+ */
+chem_status chem_serve_submit(void *server, const chem_request *req, uint64_t *ticket);
+
+/*
+ * Wait up to timeout_us (0: do not wait; < 0: wait without limit) for a ticket.  On
+ * completion fills *result, releases the ticket and returns CHEM_OK (the request's own
+ * outcome is result->status).  CHEM_ENOTREADY: timeout_us == 0 and not done;
+ * CHEM_ETIMEOUT: the wait ran out; CHEM_EINVAL: unknown or already released ticket.
+ */
+chem_status chem_serve_poll(void *server, uint64_t ticket, chem_result *result,
+                            int64_t timeout_us);
+
+/* Counters of a server. */
+chem_status chem_serve_info_get(void *server, chem_serve_info *info);
+
+/* Stop the worker after the batches on the GPU finish, release everything.  Requests still
+ * queued are dropped; their tickets become invalid. */
+chem_status chem_serve_destroy(void *server);
 
 /*
  * Device-side status of a mechanism's tensor-core kernels.  Every wait inside them is

@@ -48,6 +48,28 @@ class _IntegOpts(C.Structure):
 
 
 CELL_OK, CELL_STEP_UNDERFLOW, CELL_MAX_STEPS = 0, 1, 2
+REQ_SOURCE, REQ_INTEGRATE = 0, 1
+
+
+class _Request(C.Structure):
+    _fields_ = [("mech_index", C.c_int32), ("kind", C.c_int32), ("precision", C.c_int),
+                ("reserved", C.c_int32), ("n_cells", C.c_int64), ("T", C.c_void_p),
+                ("P", C.c_void_p), ("Y", C.c_void_p), ("omega", C.c_void_p),
+                ("T_out", C.c_void_p), ("Y_out", C.c_void_p), ("cell_status", C.c_void_p),
+                ("dt", C.c_double), ("rtol", C.c_double), ("atol", C.c_double)]
+
+
+class _Result(C.Structure):
+    _fields_ = [("status", C.c_int), ("batch_requests", C.c_int32), ("n_cells", C.c_int64),
+                ("batch_cells", C.c_int64), ("n_failed", C.c_int32), ("slot", C.c_int32),
+                ("queue_us", C.c_double), ("latency_us", C.c_double)]
+
+
+class _ServeInfo(C.Structure):
+    _fields_ = [("n_slots", C.c_int32), ("slot_cells", C.c_int64), ("device_bytes", C.c_size_t),
+                ("submitted", C.c_uint64), ("completed", C.c_uint64), ("batches", C.c_uint64),
+                ("graphs_captured", C.c_uint64), ("graph_launches", C.c_uint64),
+                ("max_batch_requests", C.c_int32)]
 
 
 def lib():
@@ -84,8 +106,14 @@ def lib():
             L.chem_integrate_cells.argtypes = [P, I64, P, P, P, I64, C.c_double, C.c_double,
                                                C.c_double, C.POINTER(_IntegOpts), P, P]
             L.chem_rosenbrock_tableau.argtypes = [C.POINTER(I32), P, P, P, P, P]
+            L.chem_serve_create.argtypes = [C.POINTER(P), I32, C.c_size_t, C.POINTER(P)]
+            L.chem_serve_submit.argtypes = [P, C.POINTER(_Request), C.POINTER(C.c_uint64)]
+            L.chem_serve_poll.argtypes = [P, C.c_uint64, C.POINTER(_Result), I64]
+            L.chem_serve_info_get.argtypes = [P, C.POINTER(_ServeInfo)]
+            L.chem_serve_destroy.argtypes = [P]
             for f in (L.chem_ode_rhs, L.chem_ode_jacobian, L.chem_integrate_cells,
-                      L.chem_rosenbrock_tableau):
+                      L.chem_rosenbrock_tableau, L.chem_serve_create, L.chem_serve_submit,
+                      L.chem_serve_poll, L.chem_serve_info_get, L.chem_serve_destroy):
                 f.restype = C.c_int
             for f in (L.chem_mechanism_load, L.chem_mechanism_free, L.chem_mechanism_info,
                       L.chem_source_term, L.chem_source_term_host, L.chem_device_status):
@@ -385,3 +413,57 @@ def rosenbrock_tableau():
     k = s.value
     return dict(stages=k, gamma_ii=g.value, alpha=alpha[:k, :k], gamma=gamma[:k, :k], b=b[:k],
                 bhat=bh[:k])
+
+
+# ---------------------------------------------------------------------------------------
+# serving (chem_serve_*)
+# ---------------------------------------------------------------------------------------
+
+class Server:
+    """A chem_serve server over loaded mechanisms; requests carry numpy host arrays."""
+
+    def __init__(self, mechs, hbm_budget: int):
+        self.mechs = list(mechs)
+        arr = (C.c_void_p * len(self.mechs))(*[m.handle.value for m in self.mechs])
+        h = C.c_void_p()
+        _check(lib().chem_serve_create(arr, len(self.mechs), int(hbm_budget), C.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, mech_index: int, kind: int, T, P, Y, precision: int = FP64, out=None,
+               dt: float = 0.0, rtol: float = 1e-6, atol: float = 1e-12, status=None,
+               T_out=None, Y_out=None) -> int:
+        """Queue a request.  SOURCE: `out` receives omega.  INTEGRATE: T_out / Y_out (default:
+        T, Y in place) receive the state after dt; `status` the per-cell status."""
+        req = _Request(int(mech_index), int(kind), int(precision), 0, int(T.shape[0]),
+                       _ptr(T), _ptr(P), _ptr(Y), _ptr(out),
+                       _ptr(T if T_out is None else T_out), _ptr(Y if Y_out is None else Y_out),
+                       _ptr(status), float(dt), float(rtol), float(atol))
+        t = C.c_uint64()
+        _check(lib().chem_serve_submit(self._h, C.byref(req), C.byref(t)))
+        self._keep[t.value] = (T, P, Y, out, status, T_out, Y_out)
+        return t.value
+
+    def poll(self, ticket: int, timeout_us: int = -1):
+        """dict of the request's chem_result; raises ChemError on ETIMEOUT / ENOTREADY."""
+        r = _Result()
+        _check(lib().chem_serve_poll(self._h, int(ticket), C.byref(r), int(timeout_us)))
+        self._keep.pop(ticket, None)
+        return {f: getattr(r, f) for f, _ in _Result._fields_}
+
+    def info(self):
+        i = _ServeInfo()
+        _check(lib().chem_serve_info_get(self._h, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in _ServeInfo._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _check(lib().chem_serve_destroy(self._h))
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

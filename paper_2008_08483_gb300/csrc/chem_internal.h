@@ -126,6 +126,17 @@ void fold_kc(const chem_mech_desc *d, int j, int r, double out[7]);
 void clear_error();
 extern std::atomic<uint64_t> g_launches;
 
+// Reactor integration without allocation or synchronisation (kern_integrate.cu): the
+// workspace size for up to n_max cells, the argument checks of chem_integrate_cells, and the
+// launch itself (header clear + persistent kernel; n_dev optionally holds the cell count).
+size_t integrate_workspace_bytes(const chem_mech *m, int64_t n_max);
+chem_status integrate_checks(const chem_mech *m, int64_t n, const double *T, const double *P,
+                             const double *Y, int64_t ldY, double t_end, double rtol, double atol);
+chem_status integrate_launch(const chem_mech *m, int64_t n_max, const int64_t *n_dev, double *T,
+                             const double *P, double *Y, int64_t ldY, double t_end, double rtol,
+                             double atol, const chem_integrate_opts *opts, int32_t *cell_status,
+                             void *ws, size_t ws_bytes, cudaStream_t s);
+
 chem_status launch_source_fp64(const chem_mech *m, int64_t n, const double *T, const double *P,
                                const double *Y, int64_t ldY, double *om, int64_t ldO,
                                cudaStream_t s);

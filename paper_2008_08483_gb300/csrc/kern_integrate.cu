@@ -164,6 +164,7 @@ struct IntegParams {
     int64_t max_steps;
     int32_t *status, *nacc, *nrej;
     double *t_ign;
+    const int64_t *n_dev;     // integrate: cell count read on the device (NULL: use n)
     unsigned int *queue;      // [0] next cell, [1] failed cells
     double *gmat;             // per-warp matrices when they do not fit in shared memory
     WarpLayout L;
@@ -561,18 +562,20 @@ __global__ void __launch_bounds__(256) k_reactor(MechViewF64 mv, IntView iv, Int
     }
 
     const RosCoef &rc = p.rc;
+    const int64_t ncell = p.n_dev ? *p.n_dev : p.n;
     for (;;) {
         int64_t i = 0;
         if (lane == 0) i = atomicAdd(p.queue, 1u);
         i = __shfl_sync(0xffffffffu, (long long)i, 0);
-        if (i >= p.n) break;
+        if (i >= ncell) break;
         for (int k = lane; k < ns; k += 32) c.y[1 + k] = p.Y[i * p.ldY + k];
         if (lane == 0) c.y[0] = p.T[i];
         __syncwarp();
         const double Pi = p.P[i];
         const double T0 = c.y[0];
         const double Tign = T0 + p.ign_dT;
-        double t = 0.0, h = p.h0, t_ign = -1.0;
+        double t = 0.0, h = p.h0 > 0.0 ? p.h0 : p.t_end, t_ign = -1.0;
+        bool first = true;
         int nacc = 0, nrej = 0, status = CHEM_CELL_OK;
         bool after_reject = false;
         while (t < p.t_end) {
@@ -586,12 +589,29 @@ __global__ void __launch_bounds__(256) k_reactor(MechViewF64 mv, IntView iv, Int
                 h = p.t_end - t;
                 last = true;
             }
-            if (h < p.hmin) {
+            if (h < fmax(p.hmin, fmax(1e-290, 8.0 * 2.220446049250313e-16 * t))) {
                 status = CHEM_CELL_STEP_UNDERFLOW;
                 break;
             }
             // Jacobian and f(y) (the first stage's right-hand side)
             reactor_eval<true>(mv, iv, L, c, Pi, c.y, c.r, lane);
+            if (first && p.h0 <= 0.0) {
+                // starting step: 0.01 |y| / |f| in the weighted RMS norm (Hairer, Norsett &
+                // Wanner, Solving ODEs I, Sec. II.4), at most the interval
+                double a0 = 0.0, a1 = 0.0;
+                for (int k = lane; k < n; k += 32) {
+                    const double sc = p.atol + p.rtol * fabs(c.y[k]);
+                    a0 += (c.y[k] / sc) * (c.y[k] / sc);
+                    a1 += (c.r[k] / sc) * (c.r[k] / sc);
+                }
+                const double d0 = sqrt(warp_sum(a0) / n), d1 = sqrt(warp_sum(a1) / n);
+                const double hs = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
+                if (isfinite(hs) && hs < h) {
+                    h = hs;
+                    last = false;
+                }
+            }
+            first = false;
             const double dg = 1.0 / (h * rc.gamma);
             for (int r = 0; r < n; ++r)
                 for (int col = lane; col < n; col += 32) {
@@ -818,23 +838,10 @@ extern "C" chem_status chem_ode_jacobian(const chem_mech *m, int64_t n, const do
     return launch_pointwise<kModeJac>(m, p, (cudaStream_t)stream, "ode_jacobian");
 }
 
-extern "C" chem_status chem_integrate_cells(const chem_mech *m, int64_t n, double *T, const double *P,
-                                            double *Y, int64_t ldY, double t_end, double rtol,
-                                            double atol, const chem_integrate_opts *opts,
-                                            int32_t *cell_status, void *stream)
+namespace chem {
+
+static int64_t integrate_blocks(const LaunchShape &sh, int64_t n_max)
 {
-    clear_error();
-    chem_status st = common_checks(m, n, T, P, Y, ldY);
-    if (st != CHEM_OK) return st;
-    if (!(t_end >= 0.0) || !isfinite(t_end)) return set_error(CHEM_EINVAL, "t_end must be finite, >= 0");
-    if (!(rtol > 0.0) || !(atol >= 0.0)) return set_error(CHEM_EINVAL, "need rtol > 0 and atol >= 0");
-    if (n == 0) return CHEM_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    LaunchShape sh;
-    st = shape_for(m, &sh);
-    if (st != CHEM_OK) return st;
-    st = set_smem_attr<kModeIntegrate>();
-    if (st != CHEM_OK) return st;
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -842,12 +849,45 @@ extern "C" chem_status chem_integrate_cells(const chem_mech *m, int64_t n, doubl
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_reactor<kModeIntegrate>, sh.wpb * 32, sh.smem);
     if (per_sm < 1) per_sm = 1;
     int64_t blocks = (int64_t)nsm * per_sm;
-    const int64_t need = (n + sh.wpb - 1) / sh.wpb;
-    if (blocks > need) blocks = need;
+    const int64_t need = (n_max + sh.wpb - 1) / sh.wpb;
+    return blocks > need ? need : blocks;
+}
 
+static constexpr size_t kIntegHead = 256;   // cell queue and failure count
+
+size_t integrate_workspace_bytes(const chem_mech *m, int64_t n_max)
+{
+    LaunchShape sh;
+    if (!m || n_max < 1 || shape_for(m, &sh) != CHEM_OK) {
+        clear_error();
+        return 0;
+    }
+    const int64_t blocks = integrate_blocks(sh, n_max);
+    const size_t mat = sh.L.oMat < 0 ? (size_t)blocks * sh.wpb * sh.L.n * sh.L.ldw * sizeof(double) : 0;
+    return kIntegHead + mat;
+}
+
+// Enqueue one integration on `s`: clear the workspace header, launch the persistent kernel.
+// No allocation and no synchronisation, so the two operations can be captured in a graph.
+// With n_dev the kernel takes the cell count from device memory (at most n_max cells).
+chem_status integrate_launch(const chem_mech *m, int64_t n_max, const int64_t *n_dev, double *T,
+                             const double *P, double *Y, int64_t ldY, double t_end, double rtol,
+                             double atol, const chem_integrate_opts *opts, int32_t *cell_status,
+                             void *ws, size_t ws_bytes, cudaStream_t s)
+{
+    LaunchShape sh;
+    chem_status st = shape_for(m, &sh);
+    if (st != CHEM_OK) return st;
+    st = set_smem_attr<kModeIntegrate>();
+    if (st != CHEM_OK) return st;
+    const int64_t blocks = integrate_blocks(sh, n_max);
+    const size_t mat = sh.L.oMat < 0 ? (size_t)blocks * sh.wpb * sh.L.n * sh.L.ldw * sizeof(double) : 0;
+    if (!ws || ws_bytes < kIntegHead + mat)
+        return set_error(CHEM_EINVAL, "integrate: workspace below %zu bytes", kIntegHead + mat);
     IntegParams p;
     memset(&p, 0, sizeof p);
-    p.n = n;
+    p.n = n_max;
+    p.n_dev = n_dev;
     p.T = T;
     p.P = P;
     p.Y = Y;
@@ -857,8 +897,8 @@ extern "C" chem_status chem_integrate_cells(const chem_mech *m, int64_t n, doubl
     p.t_end = t_end;
     p.rtol = rtol;
     p.atol = atol;
-    p.h0 = (opts && opts->h_init > 0.0) ? opts->h_init : fmin(1e-10, t_end);
-    p.hmin = (opts && opts->h_min > 0.0) ? opts->h_min : 1e-20;
+    p.h0 = (opts && opts->h_init > 0.0) ? opts->h_init : 0.0;
+    p.hmin = (opts && opts->h_min > 0.0) ? opts->h_min : 0.0;
     p.hmax = (opts && opts->h_max > 0.0) ? opts->h_max : t_end;
     p.max_steps = (opts && opts->max_steps > 0) ? opts->max_steps : 100000;
     p.ign_dT = (opts && opts->ign_dT > 0.0) ? opts->ign_dT : 400.0;
@@ -868,29 +908,57 @@ extern "C" chem_status chem_integrate_cells(const chem_mech *m, int64_t n, doubl
     p.status = cell_status;
     p.L = sh.L;
     p.rc = coef();
-
-    // workspace: the cell queue and failure count, then the per-warp matrices if they do
-    // not fit in shared memory
-    const size_t head = 256;
-    const size_t mat = sh.L.oMat < 0 ? (size_t)blocks * sh.wpb * sh.L.n * sh.L.ldw * sizeof(double) : 0;
-    void *ws = nullptr;
-    cudaError_t e = cudaMallocAsync(&ws, head + mat, s);
-    if (e != cudaSuccess) return set_error(CHEM_ENOMEM, "integrate: workspace of %zu bytes: %s", head + mat, cudaGetErrorString(e));
     p.queue = (unsigned int *)ws;
-    p.gmat = mat ? (double *)((char *)ws + head) : nullptr;
-    unsigned int h_fail = 0;
-    e = cudaMemsetAsync(ws, 0, head, s);
+    p.gmat = mat ? (double *)((char *)ws + kIntegHead) : nullptr;
+    cudaError_t e = cudaMemsetAsync(ws, 0, kIntegHead, s);
     if (e == cudaSuccess) {
         k_reactor<kModeIntegrate><<<(unsigned)blocks, sh.wpb * 32, sh.smem, s>>>(m->v64, m->vint, p);
         g_launches.fetch_add(1);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_fail, p.queue + 1, sizeof h_fail, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return set_error(CHEM_ECUDA, "integrate launch: %s", cudaGetErrorString(e));
+    return CHEM_OK;
+}
+
+chem_status integrate_checks(const chem_mech *m, int64_t n, const double *T, const double *P,
+                             const double *Y, int64_t ldY, double t_end, double rtol, double atol)
+{
+    chem_status st = common_checks(m, n, T, P, Y, ldY);
+    if (st != CHEM_OK) return st;
+    if (!(t_end >= 0.0) || !isfinite(t_end)) return set_error(CHEM_EINVAL, "t_end must be finite, >= 0");
+    if (!(rtol > 0.0) || !(atol >= 0.0)) return set_error(CHEM_EINVAL, "need rtol > 0 and atol >= 0");
+    if (n >= (int64_t)1 << 31) return set_error(CHEM_EINVAL, "integrate: at most 2^31 - 1 cells per call");
+    LaunchShape sh;
+    return shape_for(m, &sh);
+}
+
+}  // namespace chem
+
+extern "C" chem_status chem_integrate_cells(const chem_mech *m, int64_t n, double *T, const double *P,
+                                            double *Y, int64_t ldY, double t_end, double rtol,
+                                            double atol, const chem_integrate_opts *opts,
+                                            int32_t *cell_status, void *stream)
+{
+    clear_error();
+    chem_status st = integrate_checks(m, n, T, P, Y, ldY, t_end, rtol, atol);
+    if (st != CHEM_OK) return st;
+    if (n == 0) return CHEM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t wsb = integrate_workspace_bytes(m, n);
+    void *ws = nullptr;
+    cudaError_t e = cudaMallocAsync(&ws, wsb, s);
+    if (e != cudaSuccess) return set_error(CHEM_ENOMEM, "integrate: workspace of %zu bytes: %s", wsb, cudaGetErrorString(e));
+    unsigned int h_fail = 0;
+    st = integrate_launch(m, n, nullptr, T, P, Y, ldY, t_end, rtol, atol, opts, cell_status, ws, wsb, s);
+    if (st == CHEM_OK) {
+        e = cudaMemcpyAsync(&h_fail, (unsigned int *)ws + 1, sizeof h_fail, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) st = set_error(CHEM_ECUDA, "integrate: %s", cudaGetErrorString(e));
+    }
     cudaError_t e2 = cudaFreeAsync(ws, s);
     cudaError_t e3 = cudaStreamSynchronize(s);
-    if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = e3;
-    if (e != cudaSuccess) return set_error(CHEM_ECUDA, "integrate: %s", cudaGetErrorString(e));
+    if (st != CHEM_OK) return st;
+    if (e2 != cudaSuccess || e3 != cudaSuccess)
+        return set_error(CHEM_ECUDA, "integrate: %s", cudaGetErrorString(e2 != cudaSuccess ? e2 : e3));
     if (h_fail) return set_error(CHEM_ENONCONV, "integrate: %u of %lld cells failed", h_fail, (long long)n);
     return CHEM_OK;
 }
