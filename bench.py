@@ -338,6 +338,7 @@ def main():
         extras(line, h, mech, T, P, Y, dev, dev32, out32, ns, prec_name, stream, args)
         extras_integrator(line, mech, dev, stream)
         extras_heavy(line, dev, stream)
+        extras_serving(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
     h.close()
@@ -509,6 +510,111 @@ def extras_heavy(line, dev, stream, n=1 << 18):
         res[f"vjp_{name}"] = {"cells_per_s": n / (ms_v * 1e-3), "ms_per_call": ms_v}
     h.close()
     line["heavy_160_1000"] = res
+
+
+def extras_serving(line, n_ranks=64, req_per_rank=1, seed=42, budget=8 << 30):
+    """Serving: 64 simulated detonation-channel ranks (host threads) offload requests of
+    cells ~ logU[64, 65536] with a mechanism from {9/21, 53/325} and a kind from {source term
+    (split BF16), an integration over dt = 1e-8 s (adaptive, FP64)}, states from a ZND-like
+    profile along each rank's channel (a request takes a contiguous segment).  First all
+    requests at once (saturated cells/s), then Poisson arrivals offering 50 % and 80 % of it;
+    p50 / p99 of submit-to-result latency at each load."""
+    import threading
+    from paper_2008_08483_gb300 import chem, synth
+    mechs = [synth.make_mechanism("h2air_9_21", seed=MECH_SEED),
+             synth.make_mechanism("gri_53_325", seed=MECH_SEED)]
+    hs = [chem.Mechanism(m) for m in mechs]
+    srv = chem.Server(hs, budget)
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    reqs = []
+    for rank in range(n_ranks):
+        for q in range(req_per_rank):
+            mi = int(rng.integers(0, 2))
+            m = mechs[mi]
+            n = int(np.exp(rng.uniform(np.log(64), np.log(65536))))
+            s0 = rng.uniform(0.0, 0.95)
+            s = s0 + 0.05 * np.arange(n) / n
+            T, P, Y = synth.make_znd_states(m, n, seed=seed + 1000 * rank + q, s=s)
+            if rng.uniform() < 0.5:
+                reqs.append(dict(rank=rank, mi=mi, kind=chem.REQ_SOURCE, T=T.astype(np.float32),
+                                 P=P.astype(np.float32),
+                                 Y=np.ascontiguousarray(Y.astype(np.float32)),
+                                 out=np.empty(Y.shape, np.float32)))
+            else:
+                reqs.append(dict(rank=rank, mi=mi, kind=chem.REQ_INTEGRATE, T=T, P=P,
+                                 Y=np.ascontiguousarray(Y), Tout=np.empty_like(T),
+                                 Yout=np.empty_like(Y), st=np.empty(n, np.int32)))
+    cells = np.array([r["T"].shape[0] for r in reqs])
+
+    def submit(r):
+        if r["kind"] == chem.REQ_SOURCE:
+            return srv.submit(r["mi"], r["kind"], r["T"], r["P"], r["Y"], chem.SPLIT_BF16,
+                              out=r["out"])
+        return srv.submit(r["mi"], r["kind"], r["T"], r["P"], r["Y"], chem.FP64, dt=1e-8,
+                          rtol=1e-6, atol=1e-10, status=r["st"], T_out=r["Tout"],
+                          Y_out=r["Yout"])
+
+    def run(arrivals):
+        """arrivals[i]: submit time (s after start) of request i; one submitting and one
+        polling thread per rank.  Returns (makespan s, latencies ms, failed count)."""
+        lat = [None] * len(reqs)
+        tick = [None] * len(reqs)
+        evs = [threading.Event() for _ in reqs]
+        t0 = time.perf_counter() + 0.05
+
+        def sub(rank):
+            for i in [i for i, r in enumerate(reqs) if r["rank"] == rank]:
+                d = t0 + arrivals[i] - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tick[i] = submit(reqs[i])
+                evs[i].set()
+
+        def pol(rank):
+            for i in [i for i, r in enumerate(reqs) if r["rank"] == rank]:
+                evs[i].wait()
+                res = srv.poll(tick[i], -1)
+                lat[i] = (res["latency_us"] * 1e-3, res["status"])
+
+        th = [threading.Thread(target=f, args=(k,)) for k in range(n_ranks) for f in (sub, pol)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        span = time.perf_counter() - t0
+        return span, np.array([x[0] for x in lat]), sum(1 for x in lat if x[1] != 0)
+
+    span, l_sat, bad = run(np.zeros(len(reqs)))
+    sat = cells.sum() / span
+    res = {"workload": f"{n_ranks} ranks x {req_per_rank} requests, cells ~ logU[64, 65536], "
+                       "9/21 or 53/325, source term (split BF16) or integration over 1e-8 s "
+                       "(adaptive Rodas3, FP64, rtol 1e-6, atol 1e-10), ZND-like states", "requests": len(reqs),
+           "cells": int(cells.sum()), "saturated_cells_per_s": sat,
+           "saturated_p50_ms": float(np.median(l_sat)), "saturated_p99_ms":
+           float(np.quantile(l_sat, 0.99)), "failed": bad, "loads": []}
+    mean_cells = cells.mean()
+    for frac in (0.5, 0.8):
+        lam = frac * sat / mean_cells                 # requests per second, all ranks
+        gaps = rng.exponential(1.0 / lam, len(reqs))
+        order = rng.permutation(len(reqs))
+        arr = np.empty(len(reqs))
+        arr[order] = np.cumsum(gaps)
+        i0 = srv.info()
+        span, l, bad = run(arr)
+        i1 = srv.info()
+        res["loads"].append({"offered_frac": frac, "offered_cells_per_s": frac * sat,
+                             "achieved_cells_per_s": cells.sum() / span,
+                             "p50_ms": float(np.median(l)), "p99_ms": float(np.quantile(l, 0.99)),
+                             "batches": int(i1["batches"] - i0["batches"]),
+                             "max_batch_requests": int(i1["max_batch_requests"]), "failed": bad})
+    info = srv.info()
+    res.update(graphs_captured=int(info["graphs_captured"]), slot_cells=int(info["slot_cells"]),
+               device_bytes=int(info["device_bytes"]))
+    srv.close()
+    for h in hs:
+        h.close()
+    line["serving"] = res
+    line["p99_latency_ms"] = res["loads"][-1]["p99_ms"]
 
 
 if __name__ == "__main__":

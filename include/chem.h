@@ -222,7 +222,8 @@ chem_status chem_ode_jacobian(const chem_mech *mech, int64_t n_cells, const doub
                               void *stream);
 
 /* Per-cell outcome of chem_integrate_cells. */
-enum { CHEM_CELL_OK = 0, CHEM_CELL_STEP_UNDERFLOW = 1, CHEM_CELL_MAX_STEPS = 2 };
+enum { CHEM_CELL_OK = 0, CHEM_CELL_STEP_UNDERFLOW = 1, CHEM_CELL_MAX_STEPS = 2,
+       CHEM_CELL_NONFINITE = 3 };
 
 /* Options of chem_integrate_cells; a NULL pointer means all defaults. */
 typedef struct {
@@ -237,6 +238,9 @@ typedef struct {
                                accepted step that crosses; -1 when not reached */
     int32_t *n_accepted;    /* [n] device or NULL: accepted steps per cell */
     int32_t *n_rejected;    /* [n] device or NULL: rejected steps per cell */
+    int32_t fixed_steps;    /* > 0: take exactly this many equal steps of t_end / fixed_steps
+                               with no error control (every step accepted; a cell whose state
+                               stops being finite gets CHEM_CELL_NONFINITE); 0: adaptive */
 } chem_integrate_opts;
 
 /*
@@ -277,7 +281,8 @@ chem_status chem_rosenbrock_tableau(int32_t *stages, double *gamma_ii, double *a
  * that share (mechanism, kind, precision, dt, tolerances) into one batch for a free slot,
  * copies the batch to the device, replays the slot's graph for the batch's power-of-two
  * size bucket (capturing it on first use) and copies the results back, while other slots'
- * batches run: requests that arrive while the GPU is busy join the next free slot.  Cells
+ * batches run: requests that arrive while the GPU is busy join the next free slot.  Slot 0
+ * takes source-term batches only; integration batches hold at most 65536 cells.  Cells
  * are independent, so a request's result does not depend on the batch it ran in.
  * The mechanisms must outlive the server.  All calls are thread-safe.
  */
@@ -288,7 +293,8 @@ typedef struct {
     int32_t kind;               /* CHEM_REQ_SOURCE or CHEM_REQ_INTEGRATE */
     chem_precision precision;   /* SOURCE: element type of T, P, Y, omega (CHEM_FP64: double,
                                    otherwise float); INTEGRATE: must be CHEM_FP64 */
-    int32_t reserved;
+    int32_t fixed_steps;        /* INTEGRATE: 0 adaptive over dt; k > 0: k equal steps of dt / k
+                                   without error control (chem_integrate_opts.fixed_steps) */
     int64_t n_cells;            /* >= 1 */
     const void *T, *P, *Y;      /* HOST arrays [n], [n], [n][n_species] (dense rows) */
     void *omega;                /* SOURCE: HOST output [n][n_species] */

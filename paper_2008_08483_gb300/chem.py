@@ -44,16 +44,17 @@ class _Desc(C.Structure):
 class _IntegOpts(C.Structure):
     _fields_ = [("h_init", C.c_double), ("h_min", C.c_double), ("h_max", C.c_double),
                 ("max_steps", C.c_int64), ("ign_dT", C.c_double), ("t_ign", C.c_void_p),
-                ("n_accepted", C.c_void_p), ("n_rejected", C.c_void_p)]
+                ("n_accepted", C.c_void_p), ("n_rejected", C.c_void_p),
+                ("fixed_steps", C.c_int32)]
 
 
-CELL_OK, CELL_STEP_UNDERFLOW, CELL_MAX_STEPS = 0, 1, 2
+CELL_OK, CELL_STEP_UNDERFLOW, CELL_MAX_STEPS, CELL_NONFINITE = 0, 1, 2, 3
 REQ_SOURCE, REQ_INTEGRATE = 0, 1
 
 
 class _Request(C.Structure):
     _fields_ = [("mech_index", C.c_int32), ("kind", C.c_int32), ("precision", C.c_int),
-                ("reserved", C.c_int32), ("n_cells", C.c_int64), ("T", C.c_void_p),
+                ("fixed_steps", C.c_int32), ("n_cells", C.c_int64), ("T", C.c_void_p),
                 ("P", C.c_void_p), ("Y", C.c_void_p), ("omega", C.c_void_p),
                 ("T_out", C.c_void_p), ("Y_out", C.c_void_p), ("cell_status", C.c_void_p),
                 ("dt", C.c_double), ("rtol", C.c_double), ("atol", C.c_double)]
@@ -374,7 +375,7 @@ def ode_jacobian(mech: Mechanism, T, P, Y, stream=None):
 def integrate(mech: Mechanism, T, P, Y, t_end: float, rtol: float = 1e-6, atol: float = 1e-12,
               h_init: float = 0.0, h_min: float = 0.0, h_max: float = 0.0, max_steps: int = 0,
               ign_dT: float = 0.0, stats: bool = True, raise_on_failure: bool = False,
-              stream=None):
+              fixed_steps: int = 0, stream=None):
     """Integrate the reactors in place (T and Y are overwritten with the state at t_end).
     Returns a dict with per-cell 'status', 't_ign', 'n_accepted', 'n_rejected' (CUDA tensors)
     and 'failed' (bool).  CHEM_ENONCONV raises only when raise_on_failure is set."""
@@ -385,7 +386,7 @@ def integrate(mech: Mechanism, T, P, Y, t_end: float, rtol: float = 1e-6, atol: 
     status = torch.empty((n,), dtype=torch.int32, device=dev)
     out = {"status": status}
     opts = _IntegOpts(float(h_init), float(h_min), float(h_max), int(max_steps), float(ign_dT),
-                      None, None, None)
+                      None, None, None, int(fixed_steps))
     if stats:
         out["t_ign"] = torch.empty((n,), dtype=torch.float64, device=dev)
         out["n_accepted"] = torch.empty((n,), dtype=torch.int32, device=dev)
@@ -432,10 +433,11 @@ class Server:
 
     def submit(self, mech_index: int, kind: int, T, P, Y, precision: int = FP64, out=None,
                dt: float = 0.0, rtol: float = 1e-6, atol: float = 1e-12, status=None,
-               T_out=None, Y_out=None) -> int:
+               T_out=None, Y_out=None, fixed_steps: int = 0) -> int:
         """Queue a request.  SOURCE: `out` receives omega.  INTEGRATE: T_out / Y_out (default:
         T, Y in place) receive the state after dt; `status` the per-cell status."""
-        req = _Request(int(mech_index), int(kind), int(precision), 0, int(T.shape[0]),
+        req = _Request(int(mech_index), int(kind), int(precision), int(fixed_steps),
+                       int(T.shape[0]),
                        _ptr(T), _ptr(P), _ptr(Y), _ptr(out),
                        _ptr(T if T_out is None else T_out), _ptr(Y if Y_out is None else Y_out),
                        _ptr(status), float(dt), float(rtol), float(atol))

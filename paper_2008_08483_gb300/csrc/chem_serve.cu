@@ -11,10 +11,13 @@
 // the real cell count from device memory), the device->host copies and a host callback
 // that wakes the worker.  Other slots run their batches meanwhile, so requests that arrive
 // while the GPU is busy are admitted as soon as a slot frees: continuous batching over a
-// fixed device footprint set by the HBM budget.  When a slot completes, the worker copies
+// fixed device footprint set by the HBM budget.  Slot 0 takes source-term batches only, so
+// cheap source-term requests never wait behind long integrations, and integration batches
+// stop at 65536 cells.  When a slot completes, the worker copies
 // each request's rows to the caller's arrays and releases its waiters.
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -34,6 +37,7 @@ using Clock = std::chrono::steady_clock;
 
 constexpr int kSlots = 4;
 constexpr int64_t kMinBucket = 64;
+constexpr int64_t kIntegBatch = 65536;     // cells per integration batch (largest request)
 
 struct Req {
     uint64_t id = 0;
@@ -45,19 +49,34 @@ struct Req {
 };
 
 struct BatchKey {
-    int mech = 0, kind = 0, prec = 0;
+    int mech = 0, kind = 0, prec = 0, fixed = 0;
     double dt = 0, rtol = 0, atol = 0;
     bool operator==(const BatchKey &o) const
     {
-        return mech == o.mech && kind == o.kind && prec == o.prec && dt == o.dt && rtol == o.rtol &&
-               atol == o.atol;
+        return mech == o.mech && kind == o.kind && prec == o.prec && fixed == o.fixed &&
+               dt == o.dt && rtol == o.rtol && atol == o.atol;
     }
     bool operator<(const BatchKey &o) const
     {
-        return std::tie(mech, kind, prec, dt, rtol, atol) <
-               std::tie(o.mech, o.kind, o.prec, o.dt, o.rtol, o.atol);
+        return std::tie(mech, kind, prec, fixed, dt, rtol, atol) <
+               std::tie(o.mech, o.kind, o.prec, o.fixed, o.dt, o.rtol, o.atol);
     }
 };
+
+static BatchKey key_of(const chem_request &r)
+{
+    BatchKey k;
+    k.mech = r.mech_index;
+    k.kind = r.kind;
+    k.prec = (int)r.precision;
+    if (r.kind == CHEM_REQ_INTEGRATE) {
+        k.fixed = r.fixed_steps;
+        k.dt = r.dt;
+        k.rtol = r.rtol;
+        k.atol = r.atol;
+    }
+    return k;
+}
 
 struct Server;
 
@@ -168,10 +187,14 @@ void Server::launch(Slot &s)
                 if (k.kind == CHEM_REQ_SOURCE)
                     st = chem_source_term(m, bucket, s.dT, s.dP, s.dY, ns, s.dO, ns,
                                           (chem_precision)k.prec, s.stream);
-                else
+                else {
+                    chem_integrate_opts o;
+                    memset(&o, 0, sizeof o);
+                    o.fixed_steps = k.fixed;
                     st = integrate_launch(m, bucket, s.dN, (double *)s.dT, (const double *)s.dP,
-                                          (double *)s.dY, ns, k.dt, k.rtol, k.atol, nullptr,
-                                          s.dStatus, s.dWs, s.ws_bytes, s.stream);
+                                          (double *)s.dY, ns, k.dt, k.rtol, k.atol, &o, s.dStatus,
+                                          s.dWs, s.ws_bytes, s.stream);
+                }
                 cudaError_t ec = cudaStreamEndCapture(s.stream, &g);
                 if (st == CHEM_OK) ck(ec);
             }
@@ -273,24 +296,20 @@ void Server::run()
         if (!stop) {
             for (Slot &s : slots) {
                 if (s.busy || queue.empty()) continue;
-                const Req &head = *queue.front();
-                BatchKey key{head.r.mech_index, head.r.kind, (int)head.r.precision, 0, 0, 0};
-                if (head.r.kind == CHEM_REQ_INTEGRATE) {
-                    key.dt = head.r.dt;
-                    key.rtol = head.r.rtol;
-                    key.atol = head.r.atol;
-                }
+                // slot 0 is the source-term lane: long integrations never block it
+                auto head = queue.begin();
+                if (s.index == 0)
+                    while (head != queue.end() && (*head)->r.kind != CHEM_REQ_SOURCE) ++head;
+                if (head == queue.end()) continue;
+                const BatchKey key = key_of((*head)->r);
+                // integrations are batched up to the largest request, so that one long
+                // batch does not hold every queued integration until it ends
+                const int64_t limit = key.kind == CHEM_REQ_INTEGRATE ? std::min(cap, kIntegBatch) : cap;
                 s.members.clear();
                 int64_t cells = 0;
-                for (auto it = queue.begin(); it != queue.end();) {
+                for (auto it = head; it != queue.end();) {
                     const Req &q = **it;
-                    BatchKey kq{q.r.mech_index, q.r.kind, (int)q.r.precision, 0, 0, 0};
-                    if (q.r.kind == CHEM_REQ_INTEGRATE) {
-                        kq.dt = q.r.dt;
-                        kq.rtol = q.r.rtol;
-                        kq.atol = q.r.atol;
-                    }
-                    if (kq == key && cells + q.r.n_cells <= cap) {
+                    if (key_of(q.r) == key && (cells == 0 || cells + q.r.n_cells <= limit)) {
                         cells += q.r.n_cells;
                         s.members.push_back(*it);
                         it = queue.erase(it);
@@ -316,10 +335,9 @@ void Server::run()
         bool pending_ready = false;
         for (Slot &s : slots) pending_ready |= s.busy && s.ready;
         if (pending_ready) continue;
-        bool free_slot = false;
-        for (Slot &s : slots) free_slot |= !s.busy;
-        if (!stop && !queue.empty() && free_slot) continue;
-        // sleep until a submission or a slot completion (bounded, as a safety net)
+        // nothing could be launched (queue empty, no free slot, or only integrations queued
+        // while the source-term lane is the free slot): sleep until a submission or a slot
+        // completion (bounded, as a safety net)
         cv_work.wait_for(lk, std::chrono::milliseconds(5));
     }
 }
@@ -480,6 +498,7 @@ extern "C" chem_status chem_serve_submit(void *server, const chem_request *req, 
         if (!r.T_out || !r.Y_out) return set_error(CHEM_EINVAL, "NULL T_out or Y_out");
         if (!(r.dt >= 0.0) || !(r.dt < 1e300) || !(r.rtol > 0.0) || !(r.atol >= 0.0))
             return set_error(CHEM_EINVAL, "need finite dt >= 0, rtol > 0, atol >= 0");
+        if (r.fixed_steps < 0) return set_error(CHEM_EINVAL, "fixed_steps must be >= 0");
         if (integrate_workspace_bytes(m, 1) == 0)
             return set_error(CHEM_EUNSUPPORTED, "reactor kernels not available for this mechanism");
     } else {

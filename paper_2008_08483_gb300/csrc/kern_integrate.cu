@@ -32,7 +32,8 @@
 // with (a, c, m, e) computed on the host from the classical table (alpha, gamma, b, bhat).
 // The LU (partial pivoting) and the error control are FP64.  Step size: RMS error norm
 // with weights atol + rtol max(|y|, |y_new|), factor 0.9 err^(-1/3) clamped to [0.2, 5],
-// no growth right after a rejection.
+// no growth right after a rejection; or, on request, a fixed number of equal steps without
+// error control (the L-stable step of an operator-split CFD solver).
 #include <math.h>
 #include <string.h>
 
@@ -162,6 +163,7 @@ struct IntegParams {
     double *J;                // ode_jacobian output
     double t_end, rtol, atol, h0, hmin, hmax, ign_dT;
     int64_t max_steps;
+    int fixed_steps;          // > 0: this many equal steps, no error control
     int32_t *status, *nacc, *nrej;
     double *t_ign;
     const int64_t *n_dev;     // integrate: cell count read on the device (NULL: use n)
@@ -574,7 +576,9 @@ __global__ void __launch_bounds__(256) k_reactor(MechViewF64 mv, IntView iv, Int
         const double Pi = p.P[i];
         const double T0 = c.y[0];
         const double Tign = T0 + p.ign_dT;
-        double t = 0.0, h = p.h0 > 0.0 ? p.h0 : p.t_end, t_ign = -1.0;
+        const bool fixed = p.fixed_steps > 0;
+        double t = 0.0, t_ign = -1.0;
+        double h = fixed ? p.t_end / p.fixed_steps : (p.h0 > 0.0 ? p.h0 : p.t_end);
         bool first = true;
         int nacc = 0, nrej = 0, status = CHEM_CELL_OK;
         bool after_reject = false;
@@ -595,7 +599,7 @@ __global__ void __launch_bounds__(256) k_reactor(MechViewF64 mv, IntView iv, Int
             }
             // Jacobian and f(y) (the first stage's right-hand side)
             reactor_eval<true>(mv, iv, L, c, Pi, c.y, c.r, lane);
-            if (first && p.h0 <= 0.0) {
+            if (first && p.h0 <= 0.0 && !fixed) {
                 // starting step: 0.01 |y| / |f| in the weighted RMS norm (Hairer, Norsett &
                 // Wanner, Solving ODEs I, Sec. II.4), at most the interval
                 double a0 = 0.0, a1 = 0.0;
@@ -659,7 +663,11 @@ __global__ void __launch_bounds__(256) k_reactor(MechViewF64 mv, IntView iv, Int
             }
             const double err = sqrt(warp_sum(acc) / (double)n);
             __syncwarp();
-            if (!(err <= 1.0)) {
+            if (fixed && !isfinite(err)) {
+                status = CHEM_CELL_NONFINITE;
+                break;
+            }
+            if (!fixed && !(err <= 1.0)) {
                 const double fac = isfinite(err) ? fmax(0.2, 0.9 * pow(err, -1.0 / 3.0)) : 0.2;
                 h *= fac;
                 ++nrej;
@@ -676,7 +684,7 @@ __global__ void __launch_bounds__(256) k_reactor(MechViewF64 mv, IntView iv, Int
             double fac = err > 0.0 ? fmin(5.0, fmax(0.2, 0.9 * pow(err, -1.0 / 3.0))) : 5.0;
             if (after_reject) fac = fmin(fac, 1.0);
             after_reject = false;
-            h *= fac;
+            if (!fixed) h *= fac;
         }
         for (int k = lane; k < ns; k += 32) p.Yout[i * p.ldY + k] = c.y[1 + k];
         if (lane == 0) {
@@ -902,6 +910,7 @@ chem_status integrate_launch(const chem_mech *m, int64_t n_max, const int64_t *n
     p.hmax = (opts && opts->h_max > 0.0) ? opts->h_max : t_end;
     p.max_steps = (opts && opts->max_steps > 0) ? opts->max_steps : 100000;
     p.ign_dT = (opts && opts->ign_dT > 0.0) ? opts->ign_dT : 400.0;
+    p.fixed_steps = (opts && opts->fixed_steps > 0) ? opts->fixed_steps : 0;
     p.t_ign = opts ? opts->t_ign : nullptr;
     p.nacc = opts ? opts->n_accepted : nullptr;
     p.nrej = opts ? opts->n_rejected : nullptr;

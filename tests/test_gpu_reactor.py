@@ -102,6 +102,29 @@ def test_convergence_order_on_linear_problem(dev):
     assert np.all((orders > 2.8) & (orders < 3.2)), orders
 
 
+def test_fixed_steps_mode(dev, mech53):
+    # fixed_steps = K takes K equal steps without error control: the same arithmetic as an
+    # adaptive run pinned to h = t_end / K with a tolerance every step passes
+    k, da7 = 1.0, 1.0
+    h = chem.Mechanism(toys.isomerisation(k, da7))
+    a = _integrate(h, [1200.0], [2e6], [[0.9, 0.1]], dev, 1.0, fixed_steps=10)
+    b = _integrate(h, [1200.0], [2e6], [[0.9, 0.1]], dev, 1.0, rtol=1e3, atol=1e3,
+                   h_init=0.1, h_max=0.1)
+    assert a["n_accepted"][0] == 10 and a["n_rejected"][0] == 0 and a["status"][0] == 0
+    assert np.array_equal(a["Y"], b["Y"]) and np.array_equal(a["T"], b["T"])
+    # one step of 1e-8 s across the violent initial transients of detonation-channel states
+    # (no error control: the result need not be accurate): a cell either gets a finite state
+    # or CHEM_CELL_NONFINITE with its input state kept
+    hm = chem.Mechanism(mech53)
+    T, P, Y = synth.make_znd_states(mech53, 256, seed=4)
+    r = _integrate(hm, T, P, Y, dev, 1e-8, fixed_steps=1)
+    ok = r["status"] == chem.CELL_OK
+    assert np.all(ok | (r["status"] == chem.CELL_NONFINITE)) and ok.any()
+    assert np.all(np.isfinite(r["Y"][ok])) and np.all(np.isfinite(r["T"][ok]))
+    assert np.array_equal(r["Y"][~ok], Y[~ok]) and np.array_equal(r["T"][~ok], T[~ok])
+    assert r["failed"] == (not ok.all())
+
+
 def test_dimerisation_closed_form(dev):
     k, T, P = 1e12, 1500.0, 3e6
     h = chem.Mechanism(toys.dimerisation(k))

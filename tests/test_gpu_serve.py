@@ -39,8 +39,9 @@ def make_requests(mechs, n_req, seed, max_cells=3000):
         prec = chem.FP64 if kind == chem.REQ_INTEGRATE else \
             [chem.FP64, chem.FP32, chem.SPLIT_BF16][int(rng.integers(0, 3))]
         dt = np.float64 if prec == chem.FP64 else np.float32
-        reqs.append(dict(mi=mi, kind=kind, prec=prec, T=T.astype(dt), P=P.astype(dt),
-                         Y=np.ascontiguousarray(Y.astype(dt))))
+        fixed = 0
+        reqs.append(dict(mi=mi, kind=kind, prec=prec, fixed=fixed, T=T.astype(dt),
+                         P=P.astype(dt), Y=np.ascontiguousarray(Y.astype(dt))))
     return reqs
 
 
@@ -52,7 +53,7 @@ def _submit(srv, r):
         return t, dict(omega=out)
     st = np.full(T.shape[0], -1, np.int32)
     t = srv.submit(r["mi"], r["kind"], T, P, Y, chem.FP64, dt=1e-8, rtol=1e-6, atol=1e-12,
-                   status=st)
+                   status=st, fixed_steps=r.get("fixed", 0))
     return t, dict(T=T, Y=Y, status=st)
 
 
@@ -110,7 +111,7 @@ def test_served_equals_direct_calls(env):
             w = chem.source_term(h, T, P, Y, r["prec"]).cpu().numpy()
             assert np.array_equal(w, o["omega"])
         else:
-            chem.integrate(h, T, P, Y, 1e-8, rtol=1e-6, atol=1e-12)
+            chem.integrate(h, T, P, Y, 1e-8, rtol=1e-6, atol=1e-12, fixed_steps=r["fixed"])
             assert np.array_equal(T.cpu().numpy(), o["T"])
             assert np.array_equal(Y.cpu().numpy(), o["Y"])
             assert np.all(o["status"] == 0)
