@@ -263,6 +263,26 @@ chem_status chem_integrate_cells(const chem_mech *mech, int64_t n_cells, double 
                                  int32_t *cell_status, void *stream);
 
 /*
+ * chem_integrate_cells without any allocation (the paper has no counterpart: this is a
+ * deployment variant).  Same arguments, semantics, synchronisation and errors as
+ * chem_integrate_cells, but the device workspace comes from a static 1 MiB array per
+ * device instead of a stream-ordered allocation, for callers that cannot let the library
+ * allocate (device memory handed to a CFD solver's or framework's own pool allocator, or a
+ * time-step loop that must not pay an allocation's latency or implicit synchronisation).
+ * The array is shared by all calls on a device: calls that overlap in time on one device
+ * race on it and must not be issued.  Each call clears the part that must start at zero
+ * (cell counter, failure count) on its stream.  The first call on a device sets up the
+ * array's address with that device current; make it before any stream capture.
+ * Additional error: CHEM_ENOMEM when the mechanism's workspace (per-warp matrices of
+ * mechanisms too large for shared memory) exceeds the 1 MiB array.
+ */
+chem_status chem_integrate_cells_noalloc(const chem_mech *mech, int64_t n_cells, double *T,
+                                         const double *P, double *Y, int64_t ldY, double t_end,
+                                         double rtol, double atol,
+                                         const chem_integrate_opts *opts, int32_t *cell_status,
+                                         void *stream);
+
+/*
  * The classical coefficients of the integrator's Rosenbrock method (host call, no GPU
  * needed): *stages = s, gamma_ii = *gamma, alpha[s][s] and gamma[s][s] strictly lower
  * (row-major, 4 x 4 buffers), b[s] and the embedded bhat[s], in the form

@@ -106,6 +106,8 @@ def lib():
             L.chem_ode_jacobian.argtypes = [P, I64, P, P, P, I64, P, P]
             L.chem_integrate_cells.argtypes = [P, I64, P, P, P, I64, C.c_double, C.c_double,
                                                C.c_double, C.POINTER(_IntegOpts), P, P]
+            L.chem_integrate_cells_noalloc.argtypes = L.chem_integrate_cells.argtypes
+            L.chem_integrate_cells_noalloc.restype = C.c_int
             L.chem_rosenbrock_tableau.argtypes = [C.POINTER(I32), P, P, P, P, P]
             L.chem_serve_create.argtypes = [C.POINTER(P), I32, C.c_size_t, C.POINTER(P)]
             L.chem_serve_submit.argtypes = [P, C.POINTER(_Request), C.POINTER(C.c_uint64)]
@@ -401,6 +403,21 @@ def integrate(mech: Mechanism, T, P, Y, t_end: float, rtol: float = 1e-6, atol: 
     if rc != 0 and (rc != 8 or raise_on_failure):
         _check(rc)
     return out
+
+
+def integrate_noalloc(mech: Mechanism, T, P, Y, t_end: float, rtol: float = 1e-6,
+                      atol: float = 1e-12, stream=None):
+    """chem_integrate_cells_noalloc: as integrate() (in place, defaults for every option) with
+    the workspace taken from the library's static scratch; returns the per-cell status."""
+    import torch
+    _check_reactor(T, P, Y)
+    status = torch.empty((T.shape[0],), dtype=torch.int32, device=T.device)
+    rc = lib().chem_integrate_cells_noalloc(mech.handle, T.shape[0], T.data_ptr(), P.data_ptr(),
+                                            Y.data_ptr(), Y.stride(0), float(t_end), float(rtol),
+                                            float(atol), None, status.data_ptr(),
+                                            _stream_ptr(stream))
+    _check(rc)
+    return status
 
 
 def rosenbrock_tableau():
