@@ -17,6 +17,9 @@
 //   contraction 2 (Eq. 2):  omega += q_net . nu^T          (M=128, N=NSP, K=RC)
 // omega accumulates in tensor memory across the chunks and is written once per tile.
 //
+// Tiles overlap: the next tile's prologue runs as soon as every contraction 1 of the current
+// tile has completed (A1FREE), before the current tile's omega is read out of tensor memory
+// and written to global memory, so that the next tile's contraction 1 starts meanwhile.
 // Warp roles (576 threads): warp 0 bulk-copies the T, P, Y tile into shared memory;
 // warp 1 owns tensor memory and issues every MMA from one thread; warps 2-17 form four
 // epilogue warpgroups: warpgroups 0-1 take the even chunks and 2-3 the odd ones, each
@@ -65,7 +68,7 @@ struct alignas(16) FallBF {
 };
 
 struct Bf16Tables {
-    int nsp, nch, nfall, ntb, nfac;
+    int nsp, nch, nfall, ntb, nfac, fac_chunk0;
     size_t b1_bytes, b2_bytes, tab_bytes;        // tab = everything after B1 | B2
     uint32_t o_coef, o_hmask, o_fall, o_tbe, o_tbsp, o_gib;   // offsets from the blob start
     void *d_blob;
@@ -79,7 +82,10 @@ struct Bf16Params {
     float *om;
     int64_t n, ldY, ldO;
     int ns, nch, ntiles, nfac;
-    int stage_y;
+    int fac_chunk0;            // first chunk holding a third-body / falloff reaction
+    int stage_y;               // T, P, Y tiles staged in shared memory (the Y buffer then also
+                               // stages omega on its way out)
+    int bulk_out;              // omega rows contiguous (ldO == ns) and 16-byte aligned
     const uint16_t *btab;
     uint32_t blob_bytes;
     const float *invW;
@@ -89,13 +95,12 @@ struct Bf16Params {
     // holds B1, B2, coefficients, third-body masks, falloff records and third-body lists
     uint32_t o_b2, o_coef, o_hmask, o_fall, o_tbe, o_tbsp, o_gib, o_y, o_t, o_p, o_xw, o_iw, o_psum,
         o_bar;
-    int bulk_out;              // omega rows contiguous (ldO == ns) and 16-byte aligned
 };
 
 enum {
     BAR_BTAB, BAR_YFULL, BAR_YEMPTY, BAR_A1FULL, BAR_D1FULL0, BAR_D1FULL1, BAR_D1EMPTY0,
     BAR_D1EMPTY1, BAR_A2FULL0, BAR_A2FULL1, BAR_A2EMPTY0, BAR_A2EMPTY1, BAR_D2FULL, BAR_D2EMPTY,
-    BAR_XREADY, BAR_WREADY, BAR_STDONE, BAR_DRAIN, BAR_FREADY, BAR_COUNT
+    BAR_XREADY, BAR_A1FREE, BAR_DRAIN, BAR_FREADY, BAR_WREADY, BAR_COUNT
 };
 
 struct SmemCtl {
@@ -255,8 +260,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
     float *Ys = (float *)(sm + p.o_y);
     float *Ts = (float *)(sm + p.o_t);
     float *Ps = (float *)(sm + p.o_p);
-    float *Xs = (float *)(sm + p.o_xw);           // X [species][128] while the chunks run
-    float *Ws = (float *)(sm + p.o_xw);           // omega [128][ns] while the tile is stored
+    float *Xs = (float *)(sm + p.o_xw);           // X [species][128] of the current tile
+    float *Ws = (float *)(sm + p.o_y);            // omega [128][ns], in the Y buffer between
+                                                  // the next tile's prologue and its reload
     float *iW = (float *)(sm + p.o_iw);
     float *Psum = (float *)(sm + p.o_psum);      // [4][128] partial sums of z_k per warpgroup
     uint64_t *bars = (uint64_t *)(sm + p.o_bar);
@@ -265,7 +271,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        const uint32_t cnt[BAR_COUNT] = {1, 1, 16, 16, 1, 1, 8, 8, 8, 8, 1, 1, 1, 16, 16, 16, 16, 1, 16};
+        const uint32_t cnt[BAR_COUNT] = {1, 1, 16, 16, 1, 1, 8, 8, 8, 8, 1, 1, 1, 16, 16, 1, 1, 16, 16};
         for (int i = 0; i < BAR_COUNT; ++i) tc::mbar_init(BAR(i), cnt[i]);
         tc::mbar_fence_init();
         ctl->abort = 0;
@@ -365,10 +371,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 // soon as its epilogue pair has read it, contraction 2 strictly in chunk order
                 // (the omega accumulation order, hence the rounding, is fixed).
                 int c1[2] = {0, 1}, c2 = 0;
-                bool d2_free = false;
+                bool d2_free = false, a1_freed = false;
                 long long t0 = clock64();
                 while (c2 < p.nch) {
                     bool prog = false;
+                    // contraction 2 first: it frees an epilogue pair's q_net buffer, while a
+                    // ready contraction 1 only runs ahead
+                    if (!d2_free) d2_free = tc::mbar_test_wait(BAR(BAR_D2EMPTY), (it & 1) ^ 1);
+                    const int b2c = c2 & 1;
+                    if (d2_free && tc::mbar_test_wait(BAR(BAR_A2FULL0 + b2c), u_a2[b2c] & 1)) {
+                        tc::fence_after();
+                        mma2(c2);
+                        ++c2;
+                        prog = true;
+                    }
 #pragma unroll
                     for (int b = 0; b < 2; ++b) {
                         if (c1[b] < p.nch &&
@@ -379,18 +395,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                             prog = true;
                         }
                     }
-                    if (!d2_free) d2_free = tc::mbar_test_wait(BAR(BAR_D2EMPTY), (it & 1) ^ 1);
-                    const int b2c = c2 & 1;
-                    if (d2_free && tc::mbar_test_wait(BAR(BAR_A2FULL0 + b2c), u_a2[b2c] & 1)) {
-                        tc::fence_after();
-                        mma2(c2);
-                        ++c2;
-                        prog = true;
+                    if (!a1_freed && c1[0] >= p.nch && c1[1] >= p.nch) {
+                        // completes when every contraction 1 of the tile has read its operands
+                        tc::commit(BAR(BAR_A1FREE));
+                        a1_freed = true;
                     }
                     if (prog) {
                         t0 = clock64();
                     } else if (clock64() - t0 < (1ll << 31) && !ctl->abort) {
-                        __nanosleep(100);               // back off: the epilogue warps share this SM
+                        __nanosleep(32);                // back off: the epilogue warps share this SM
                     } else if (ctl->abort || clock64() - t0 > (1ll << 31)) {
                         ctl->abort = 1;
                         atomicCAS(p.status, 0, 2);
@@ -415,13 +428,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
         const int ns = p.ns;
         int it = 0, u = 0;
         bool ok = wait_bar(BAR(BAR_BTAB), 0, ctl, p.status, 3);   // coefficients in smem
-        for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x, ++it) {
+        CellF cf;
+        // ---- prologue of tile t: features, X and split log2 X (Eq. 4 input layer); ends
+        // with the tile's contraction-1 operands in tensor memory (A1FULL)
+        auto prologue = [&](int t, int itp) -> bool {
             const int64_t i0 = (int64_t)t * 128;
             const int64_t ci = i0 + row;
             const bool full = p.stage_y && i0 + 128 <= n;
-            if (!(ok = wait_bar(BAR(BAR_YFULL), it & 1, ctl, p.status, 3))) break;
-            // the previous tile's omega has left the shared buffer that X reuses
-            if (it > 0 && !(ok = wait_bar(BAR(BAR_STDONE), (it - 1) & 1, ctl, p.status, 3))) break;
+            if (!wait_bar(BAR(BAR_YFULL), itp & 1, ctl, p.status, 3)) return false;
             // ---- prologue: features, X and split log2 X (Eq. 4 input layer)
             float Tc = 1000.0f, Pc = 1.0e6f;
             const float *yrow = nullptr;
@@ -434,7 +448,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 Pc = __ldg(p.P + ci);
                 yrow = p.Y + ci * p.ldY;
             }
-            CellF cf;
             cf.lg2T = log2f(Tc);
             cf.invT = 1.0f / Tc;
             cf.tau = Tc * 1e-3f;
@@ -472,6 +485,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 split3x2(lx[0], lx[1], wh[e], wm[e], wl[e]);
                 split3x2(gk[0], gk[1], gh[e], gm[e], gl[e]);
             }
+            // the previous tile's contractions 1 have read their operands
+            if (itp > 0 && !wait_bar(BAR(BAR_A1FREE), (itp - 1) & 1, ctl, p.status, 3)) return false;
+            tc::fence_after();
             const uint32_t a1 = tmem + lane_off + CL::A1 + g * (SQ / 2);
             const uint32_t ag = tmem + lane_off + CL::AG + g * (SQ / 2);
             if constexpr (SQ / 2 == 8) {
@@ -494,10 +510,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
             Psum[g * 128 + row] = psum;
             __syncwarp();
             if (lane == 0) {
-                tc::mbar_arrive(BAR(BAR_YEMPTY));
+                // the first tile's Y buffer is free now; later ones hold omega of the tile
+                // before until it has been stored
+                if (itp == 0) tc::mbar_arrive(BAR(BAR_YEMPTY));
                 tc::mbar_arrive(BAR(BAR_XREADY));
             }
-            if (!(ok = wait_bar(BAR(BAR_XREADY), it & 1, ctl, p.status, 3))) break;
+            if (!wait_bar(BAR(BAR_XREADY), itp & 1, ctl, p.status, 3)) return false;
             {
                 const float sum = Psum[row] + Psum[128 + row] + Psum[256 + row] + Psum[384 + row];
                 cf.inv_sum = sum > 0.0f ? 1.0f / sum : 0.0f;
@@ -523,42 +541,71 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 tc::fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(BAR(BAR_A1FULL));
-                // Third-body / falloff multipliers of this tile, a quarter per warpgroup, while
-                // the first contractions run.  They are read after this warp's own wait for
-                // contraction 1, which orders them after every warp's A1FULL arrival below.
-                // warpgroup g takes entries g, g + 4, g + 8, ... of the kind-sorted list
-                const int n_g = (p.nfac - g + 3) / 4;
-                for (int i0 = 0; i0 < n_g; i0 += 4) {
-                    int sl[4];
+            }
+            return true;
+        };
+        if ((int)blockIdx.x < p.ntiles) ok = ok && prologue(blockIdx.x, 0);
+        for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x, ++it) {
+            const int64_t i0 = (int64_t)t * 128;
+            const int64_t ci = i0 + row;
+            // Third-body / falloff multipliers of this tile (Sec. 2.4): warpgroup g evaluates
+            // entries g, g + 4, g + 8, ... of the kind-sorted list, four at a time, in the
+            // waits between its first chunks (the reactions that need them sit in the last
+            // chunks).  All of them are in tensor memory (FREADY: every epilogue warp has
+            // stored its share) before the first chunk that reads one.
+            const int n_g = (p.nfac - g + 3) / 4;
+            int gi = 0;
+            bool fready = false;
+            auto mult_group = [&]() {
+                int sl[4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) sl[u] = tabs.fslot[g + 4 * min(i0 + u, n_g - 1)];
-                    bool fall = false;
+                for (int e = 0; e < 4; ++e) sl[e] = tabs.fslot[g + 4 * min(gi + e, n_g - 1)];
+                bool fall = false;
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        fall |= __float_as_int(tabs.coef[sl[u]].kf.w) >= 2;
-                    float v[4];
-                    tb_factor4(tabs, sl, fall, cf, Xs, row, v);
+                for (int e = 0; e < 4; ++e) fall |= __float_as_int(tabs.coef[sl[e]].kf.w) >= 2;
+                float v[4];
+                tb_factor4(tabs, sl, fall, cf, Xs, row, v);
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (i0 + u < n_g)
-                            tc::tmem_st1(tmem + lane_off + CL::FC + tabs.fcol[g + 4 * (i0 + u)],
-                                         __float_as_uint(v[u]));
-                }
+                for (int e = 0; e < 4; ++e)
+                    if (gi + e < n_g)
+                        tc::tmem_st1(tmem + lane_off + CL::FC + tabs.fcol[g + 4 * (gi + e)],
+                                     __float_as_uint(v[e]));
+                gi += 4;
+            };
+            auto mult_finish = [&]() -> bool {
+                while (gi < n_g) mult_group();
                 tc::tmem_wait_st();
                 tc::fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(BAR(BAR_FREADY));
-            }
-            if (!(ok = wait_bar(BAR(BAR_FREADY), it & 1, ctl, p.status, 3))) break;
-            tc::fence_after();
+                const bool w = wait_bar(BAR(BAR_FREADY), it & 1, ctl, p.status, 3);
+                tc::fence_after();
+                fready = true;
+                return w;
+            };
+            // two groups while contraction 1 of the first chunks runs
+            for (int pre = 0; pre < 2 && gi < n_g; ++pre) mult_group();
             // ---- this pair's chunks, this warpgroup's half of each
             for (int c = pr; c < p.nch; c += 2, ++u) {
+                if (!fready && c >= p.fac_chunk0 && !(ok = mult_finish())) break;
                 if (!(ok = wait_bar(BAR(BAR_D1FULL0 + pr), u & 1, ctl, p.status, 3))) break;
                 tc::fence_after();
-                uint32_t sf[RH], sr[RH];
+                uint32_t sf[RH], sr[RH], fv[8];
                 const uint32_t d1 = tmem + lane_off + CL::D1 + pr * 2 * RC + hf * RH;
-                tc::tmem_ld16(d1, sf);
-                tc::tmem_ld16(d1 + RC, sr);
+                // both halves of contraction 1 and this half chunk's (at most 4) multipliers,
+                // consecutive columns, behind one completion wait
+                const uint32_t hm = tabs.hmask[c * 2 + hf];
+                const int fb = hm ? tabs.fbase[c * 2 + hf] : 0;
+                const int lb = min(fb, CL::kMaxFactors - 8);
+                tc::tmem_ld16_nw(d1, sf);
+                tc::tmem_ld16_nw(d1 + RC, sr);
+                if (hm) {
+                    tc::tmem_ld8_nw(tmem + lane_off + CL::FC + lb, fv);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) fv[e] = 0u;
+                }
+                tc::tmem_wait_ld_tie(sf, sr, fv);
                 tc::fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(BAR(BAR_D1EMPTY0 + pr));
@@ -570,13 +617,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                     q[r] = ((lm >> r) & 1u) ? rate_plain(tabs.coef + j0 + r, __uint_as_float(sf[r]),
                                                         __uint_as_float(sr[r]), (rm >> r) & 1u, cf)
                                             : 0.0f;
-                const uint32_t hm = tabs.hmask[c * 2 + hf];
                 if (hm) {
-                    // the (at most 4) multipliers of this half chunk are consecutive columns
-                    const int fb = tabs.fbase[c * 2 + hf];
-                    const int lb = min(fb, CL::kMaxFactors - 8);
-                    uint32_t fv[8];
-                    tc::tmem_ld8(tmem + lane_off + CL::FC + lb, fv);
 #pragma unroll
                     for (int r = 0; r < RH; ++r) {
                         if ((hm >> r) & 1u) {
@@ -606,9 +647,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 tc::fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(BAR(BAR_A2FULL0 + pr));
+                if (!fready && gi < n_g) mult_group();   // while the tensor pipe works
             }
             if (!ok) break;
-            // ---- omega of the tile: tensor memory -> shared -> global (coalesced)
+            if (!fready && !(ok = mult_finish())) break;
+            // ---- the next tile's prologue first: it needs none of this tile's tensor memory
+            // (every contraction 1 of this tile has completed), so its contraction 1 can
+            // start while this tile's omega is read out
+            const int t_next = t + gridDim.x;
+            if (t_next < p.ntiles && !(ok = prologue(t_next, it + 1))) break;
+            // ---- omega of the tile: tensor memory -> shared (the Y buffer, read by the next
+            // tile's prologue already) -> one coalesced bulk store; then the buffer is free
+            // for the tile after next (YEMPTY)
             if (!(ok = wait_bar(BAR(BAR_D2FULL), it & 1, ctl, p.status, 3))) break;
             tc::fence_after();
             {
@@ -619,33 +669,43 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 tc::fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(BAR(BAR_D2EMPTY));
+                if (p.stage_y) {
 #pragma unroll
-                for (int e = 0; e < SQ; ++e) {
-                    const int k = g * SQ + e;
-                    if (k < ns) Ws[row * ns + k] = __uint_as_float(w[e]);
+                    for (int e = 0; e < SQ; ++e) {
+                        const int k = g * SQ + e;
+                        if (k < ns) Ws[row * ns + k] = __uint_as_float(w[e]);
+                    }
+                } else if (ci < n) {                  // no staging buffer: direct stores
+                    float *orow = p.om + ci * p.ldO;
+#pragma unroll
+                    for (int e = 0; e < SQ; ++e) {
+                        const int k = g * SQ + e;
+                        if (k < ns) orow[k] = __uint_as_float(w[e]);
+                    }
                 }
             }
-            tc::fence_proxy_async_smem();            // visible to the bulk store
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(BAR(BAR_WREADY));
-            if (!(ok = wait_bar(BAR(BAR_WREADY), it & 1, ctl, p.status, 3))) break;
-            if (p.bulk_out && i0 + 128 <= n) {
-                // one bulk store of the tile; the shared buffer is reused after it is read
-                if (ew == 0 && lane == 0) {
-                    tc::bulk_s2g(p.om + i0 * p.ldO, sbase + p.o_xw, (uint32_t)(128 * ns * 4));
-                    tc::bulk_commit();
-                    tc::bulk_wait_read0();
-                }
-            } else {
-                for (int r = ew; r < 128; r += kEpiWarps) {
-                    const int64_t i = i0 + r;
-                    if (i >= n) break;
-                    float *orow = p.om + i * p.ldO;
-                    for (int k = lane; k < ns; k += 32) orow[k] = Ws[r * ns + k];
+            if (p.stage_y) {
+                tc::fence_proxy_async_smem();            // visible to the bulk store
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(BAR(BAR_WREADY));
+                if (!(ok = wait_bar(BAR(BAR_WREADY), it & 1, ctl, p.status, 3))) break;
+                if (p.bulk_out && i0 + 128 <= n) {
+                    if (ew == 0 && lane == 0) {
+                        tc::bulk_s2g(p.om + i0 * p.ldO, sbase + p.o_y, (uint32_t)(128 * ns * 4));
+                        tc::bulk_commit();
+                        tc::bulk_wait_read0();
+                    }
+                } else {
+                    for (int r = ew; r < 128; r += kEpiWarps) {
+                        const int64_t i = i0 + r;
+                        if (i >= n) break;
+                        float *orow = p.om + i * p.ldO;
+                        for (int k = lane; k < ns; k += 32) orow[k] = Ws[r * ns + k];
+                    }
                 }
             }
             __syncwarp();
-            if (lane == 0) tc::mbar_arrive(BAR(BAR_STDONE));
+            if (lane == 0) tc::mbar_arrive(BAR(BAR_YEMPTY));
         }
     }
     if (warp == kEpiWarp0 && lane == 0) tc::bulk_wait0();   // omega stores have landed
@@ -683,20 +743,32 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
     int nch = (nr + RC - 1) / RC;
     if (nch > 1 && (nch & 1)) ++nch;
     const int nrp = nch * RC;
-    // Reactions that need a third-body or falloff factor are spread evenly over the
-    // reaction sequence, and the sequence evenly over the slots (padding in between).
+    // Reactions without a third-body or falloff factor fill the first chunks (spread evenly
+    // over their slots); those with one go to the last K chunks, round-robin over their
+    // half chunks (at most 8 per half chunk, one 8-column multiplier load), with the rest
+    // of the plain reactions.  The epilogue evaluates the multipliers in the waits of its
+    // first chunks, before they are needed.
     std::vector<int> plain, special;
     for (int j = 0; j < nr; ++j) (d->kind[j] == 0 ? plain : special).push_back(j);
-    std::vector<int> seq(nr, -1);
-    for (size_t i = 0; i < special.size(); ++i)
-        seq[(size_t)(((double)i + 0.5) * nr / special.size())] = special[i];
-    {
-        size_t pi = 0;
-        for (int jj = 0; jj < nr; ++jj)
-            if (seq[jj] < 0) seq[jj] = plain[pi++];
-    }
+    const int S = (int)special.size();
+    int K = S ? (S + 2 * 8 - 1) / (2 * 8) : 0;
+    if (K > nch) return set_error(CHEM_EUNSUPPORTED, "split-BF16 path: too many third-body reactions");
+    while (K < nch && (nch - K) * RC + K * RC - S < (int)plain.size()) ++K;   // room for all
     std::vector<int> order(nrp, -1);        // slot -> reaction (-1: padding)
-    for (int i = 0; i < nr; ++i) order[(size_t)((int64_t)i * nrp / nr)] = seq[i];
+    size_t pi = 0;
+    {
+        const int head_slots = (nch - K) * RC;
+        const int n_head = std::min((int)plain.size(), head_slots);
+        for (int i = 0; i < n_head; ++i)
+            order[(size_t)((int64_t)i * head_slots / n_head)] = plain[pi++];
+        for (int i = 0; i < S; ++i) {                    // round-robin over the tail half chunks
+            const int hc = (nch - K) * 2 + i % (2 * K), pos = i / (2 * K);
+            order[(size_t)hc * RH + pos] = special[i];
+        }
+        for (int jj = head_slots; jj < nrp && pi < plain.size(); ++jj)
+            if (order[jj] < 0) order[jj] = plain[pi++];
+    }
+    if (pi != plain.size()) return set_error(CHEM_EUNSUPPORTED, "split-BF16 path: slot layout");
     std::vector<uint16_t> b1((size_t)nch * 2 * RC * nsp, 0), b2((size_t)nch * nsp * RC, 0);
     std::vector<CoefS> cf(nrp);
     // per half chunk: third-body, live and reversible masks, then the multiplier base index;
@@ -808,8 +880,8 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
             return set_error(CHEM_EUNSUPPORTED,
                              "split-BF16 path holds at most %d third-body/falloff reactions", max_fac);
         for (size_t h2 = 0; h2 < (size_t)nch * 2; ++h2)
-            if (__builtin_popcount(hmask[h2]) > 4)
-                return set_error(CHEM_EUNSUPPORTED, "more than 4 third-body reactions in a chunk half");
+            if (__builtin_popcount(hmask[h2]) > 8)
+                return set_error(CHEM_EUNSUPPORTED, "more than 8 third-body reactions in a chunk half");
         // evaluation order: third-body multipliers first, then falloff (their columns stay
         // in slot order, so each half chunk reads consecutive columns)
         std::vector<uint32_t> ord_slot, ord_col;
@@ -825,6 +897,7 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
         hmask.insert(hmask.end(), ord_col.begin(), ord_col.end());
     }
     const int nfac = (int)fslot.size();
+    const int fac_chunk0 = nfac ? (int)(fslot[0] / RC) : nch;
     if (tbsp.empty()) {
         tbsp.push_back(0);
         tbe.push_back(0.f);
@@ -883,6 +956,7 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
     t->o_tbsp = (uint32_t)otbs;
     t->o_gib = (uint32_t)ogb;
     t->nfac = nfac;
+    t->fac_chunk0 = fac_chunk0;
     t->btab = (const uint16_t *)(base + ob1);
     t->invW = (const float *)(base + oiw);
     t->status = (int *)(base + ost);
@@ -957,6 +1031,8 @@ chem_status launch_source_bf16(const chem_mech *m, int64_t n, const float *T, co
     prm.ns = m->ns;
     prm.nch = t->nch;
     prm.nfac = t->nfac;
+    prm.bulk_out = (ldO == m->ns && (uintptr_t)om % 16 == 0) ? 1 : 0;
+    prm.fac_chunk0 = t->fac_chunk0;
     prm.ntiles = (int)((n + 127) / 128);
     prm.btab = t->btab;
     prm.blob_bytes = (uint32_t)(t->b1_bytes + t->b2_bytes + t->tab_bytes);
@@ -980,7 +1056,6 @@ chem_status launch_source_bf16(const chem_mech *m, int64_t n, const float *T, co
     const size_t fixed = 2 * 512 + xw + al(m->ns * 4, 128) + 2048 + BAR_COUNT * 8 + 64 + 1024;
     const bool aligned = ((uintptr_t)Y % 16 == 0) && ((uintptr_t)T % 16 == 0) && ((uintptr_t)P % 16 == 0);
     prm.stage_y = aligned && (off + ybytes + fixed <= 227 * 1024) ? 1 : 0;
-    prm.bulk_out = (ldO == m->ns && (uintptr_t)om % 16 == 0) ? 1 : 0;
     prm.o_y = (uint32_t)off;
     if (prm.stage_y) off = al(off + ybytes, 128);
     prm.o_t = (uint32_t)off;

@@ -209,6 +209,44 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t *r)
         : "r"(taddr)
         : "memory");
 }
+// Loads without the completion wait, for several loads behind one tmem_wait_ld_tie.
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t *r)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%16];"
+        : CHEM_R8(0), CHEM_R8(8)
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld8_nw(uint32_t taddr, uint32_t *r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : CHEM_R8(0)
+                 : "r"(taddr)
+                 : "memory");
+}
+#define CHEM_T8(b) "+r"(r[b + 0]), "+r"(r[b + 1]), "+r"(r[b + 2]), "+r"(r[b + 3]), \
+                   "+r"(r[b + 4]), "+r"(r[b + 5]), "+r"(r[b + 6]), "+r"(r[b + 7])
+// Completion of the loads issued so far; the registers of two 16-column loads and one
+// 8-column load are tied to it, so no use of them can be scheduled before the wait.
+__device__ __forceinline__ void tmem_wait_ld_tie(uint32_t *a, uint32_t *b, uint32_t *c)
+{
+    {
+        uint32_t *r = a;
+        asm volatile("tcgen05.wait::ld.sync.aligned;" : CHEM_T8(0), CHEM_T8(8) : : "memory");
+    }
+    {
+        uint32_t *r = b;
+        asm volatile("" : CHEM_T8(0), CHEM_T8(8) : : "memory");
+    }
+    {
+        uint32_t *r = c;
+        asm volatile("" : CHEM_T8(0) : : "memory");
+    }
+}
+#undef CHEM_T8
+
 // 16 / 8 / 4 consecutive 32-bit columns; completion awaited with tmem_wait_st.
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *v)
 {
