@@ -1,10 +1,10 @@
 // kern_bf16.cu -- split-BF16 source term on tcgen05 tensor cores (sm_103a).
 //
-// Per tile of 128 cells (one cell per tensor-memory lane), for reaction chunks of RC:
-//   contraction 1 (Eqs. 4, 11): S = log2 X . [nu' | nu''] (M=128, N=2 RC, K=NSP), and the
-//       reverse half also accumulates G . nu, the Gibbs layer of Eq. 11 (G_k = g_k/(RT) log2 e
-//       - log2(p_ref/(RT)), per cell and species, three BF16 terms in tensor memory; nu is
-//       contraction 2's table read as an MN-major operand), so that S'' + log2 k_f =
+// Per tile of 128 cells (one cell per tensor-memory lane), for reaction chunks of RC = 64:
+//   contraction 1 (Eqs. 4, 11): S = log2 X . [nu' | nu''] (M=128, N=2 RC=128, K=NSP), and
+//       the reverse half also accumulates G . nu, the Gibbs layer of Eq. 11 (G_k = g_k/(RT)
+//       log2 e - log2(p_ref/(RT)), per cell and species, three BF16 terms in tensor memory;
+//       nu is contraction 2's table read as an MN-major operand), so that S'' + log2 k_f =
 //       sum_k nu''_k log2 C_k + log2 k_r
 //       A = log2 X in tensor memory as three BF16 terms (hi + mid + lo); the extra
 //       column NSP_extra = log2 c_tot carries the reaction orders (and the third-body
@@ -16,16 +16,18 @@
 //       (Eq. 3), split into two BF16 terms written to tensor memory.
 //   contraction 2 (Eq. 2):  omega += q_net . nu^T          (M=128, N=NSP, K=RC)
 // omega accumulates in tensor memory across the chunks and is written once per tile.
+// Contraction 1 of chunk c + 1 runs while the epilogue works on chunk c (it starts as soon
+// as chunk c's S has been read out), contraction 2 of chunk c as soon as its q_net is in.
 //
 // Tiles overlap: the next tile's prologue runs as soon as every contraction 1 of the current
 // tile has completed (A1FREE), before the current tile's omega is read out of tensor memory
-// and written to global memory, so that the next tile's contraction 1 starts meanwhile.
+// and stored, so that the next tile's contraction 1 starts meanwhile.
 // Warp roles (576 threads): warp 0 bulk-copies the T, P, Y tile into shared memory;
 // warp 1 owns tensor memory and issues every MMA from one thread; warps 2-17 form four
-// epilogue warpgroups: warpgroups 0-1 take the even chunks and 2-3 the odd ones, each
-// warpgroup of a pair handling half of the chunk's reactions (warp w reaches tensor-memory
-// lanes 32 (w % 4) .. 32 (w % 4) + 31).  Per-reaction coefficients live in shared memory;
-// third-body and falloff factors are computed out of line.
+// epilogue warpgroups, warpgroup g taking reactions 16 g .. 16 g + 15 of every chunk (warp
+// w reaches tensor-memory lanes 32 (w % 4) .. 32 (w % 4) + 31).  Per-reaction coefficients
+// live in shared memory; third-body and falloff factors are evaluated four at a time in the
+// epilogue's waits of the first chunks (the reactions that need them sit in the last ones).
 // Every mbarrier wait is bounded: on timeout the kernel records an error code in the
 // mechanism's device status word and all roles wind down.
 #include <math.h>
@@ -39,8 +41,9 @@
 
 namespace chem {
 
-constexpr int RC = 32;                 // reactions per chunk
-constexpr int RH = RC / 2;             // reactions per warpgroup and chunk
+constexpr int RC = 64;                 // reactions per chunk
+constexpr int RH = RC / 4;             // reactions per warpgroup and chunk
+constexpr int NQ = RC / RH;            // warpgroups (chunk quarters)
 constexpr int kEpiWarp0 = 2;           // first epilogue warp
 constexpr int kEpiWarps = 16;
 constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);
@@ -98,9 +101,8 @@ struct Bf16Params {
 };
 
 enum {
-    BAR_BTAB, BAR_YFULL, BAR_YEMPTY, BAR_A1FULL, BAR_D1FULL0, BAR_D1FULL1, BAR_D1EMPTY0,
-    BAR_D1EMPTY1, BAR_A2FULL0, BAR_A2FULL1, BAR_A2EMPTY0, BAR_A2EMPTY1, BAR_D2FULL, BAR_D2EMPTY,
-    BAR_XREADY, BAR_A1FREE, BAR_DRAIN, BAR_FREADY, BAR_WREADY, BAR_COUNT
+    BAR_BTAB, BAR_YFULL, BAR_YEMPTY, BAR_A1FULL, BAR_D1FULL, BAR_D1EMPTY, BAR_A2FULL, BAR_A2EMPTY,
+    BAR_D2FULL, BAR_D2EMPTY, BAR_XREADY, BAR_A1FREE, BAR_DRAIN, BAR_FREADY, BAR_WREADY, BAR_COUNT
 };
 
 struct SmemCtl {
@@ -130,9 +132,9 @@ template <int NSP>
 struct Cols {                                     // tensor-memory column map
     static constexpr uint32_t A1 = 0;             // log2 z: 3 splits x NSP/2 columns
     static constexpr uint32_t AG = ((3 * NSP / 2 + 31) / 32) * 32;   // G: 3 splits x NSP/2
-    static constexpr uint32_t D1 = AG + ((3 * NSP / 2 + 31) / 32) * 32;   // 2 buffers x 2 RC
-    static constexpr uint32_t A2 = D1 + 4 * RC;   // 2 buffers x (2 splits x RC/2)
-    static constexpr uint32_t D2 = A2 + 2 * RC;   // NSP columns
+    static constexpr uint32_t D1 = AG + ((3 * NSP / 2 + 31) / 32) * 32;   // 2 RC: S', S''
+    static constexpr uint32_t A2 = D1 + 2 * RC;   // 2 splits x RC/2
+    static constexpr uint32_t D2 = A2 + RC;       // NSP columns
     static constexpr uint32_t FC = D2 + NSP;      // third-body / falloff multipliers
     static constexpr int kMaxFactors = (int)(kTmemCols - FC);
     static_assert(kMaxFactors >= 16, "tensor memory over budget");
@@ -248,10 +250,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
     SmemTabs tabs;
     tabs.coef = (const CoefS *)(sm + p.o_coef);
     tabs.hmask = (const uint32_t *)(sm + p.o_hmask);
-    tabs.lmask = tabs.hmask + 2 * p.nch;
-    tabs.rmask = tabs.hmask + 4 * p.nch;
-    tabs.fbase = (const int *)(tabs.hmask + 6 * p.nch);
-    tabs.fslot = tabs.fbase + 2 * p.nch;
+    tabs.lmask = tabs.hmask + NQ * p.nch;
+    tabs.rmask = tabs.hmask + 2 * NQ * p.nch;
+    tabs.fbase = (const int *)(tabs.hmask + 3 * NQ * p.nch);
+    tabs.fslot = tabs.fbase + NQ * p.nch;
     tabs.fcol = tabs.fslot + p.nfac;
     const GibbsS *gib = (const GibbsS *)(sm + p.o_gib);
     tabs.fall = (const FallBF *)(sm + p.o_fall);
@@ -271,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        const uint32_t cnt[BAR_COUNT] = {1, 1, 16, 16, 1, 1, 8, 8, 8, 8, 1, 1, 1, 16, 16, 1, 1, 16, 16};
+        const uint32_t cnt[BAR_COUNT] = {1, 1, 16, 16, 1, 16, 16, 1, 1, 16, 16, 1, 1, 16, 16};
         for (int i = 0; i < BAR_COUNT; ++i) tc::mbar_init(BAR(i), cnt[i]);
         tc::mbar_fence_init();
         ctl->abort = 0;
@@ -322,17 +324,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
             constexpr uint32_t id1 = tc::idesc_bf16_f32(128, 2 * RC);
             constexpr uint32_t id2 = tc::idesc_bf16_f32(128, NSP);
             const uint32_t b1 = sbase, b2 = sbase + p.o_b2;
-            uint32_t u_d1[2] = {0, 0}, u_a2[2] = {0, 0};
+            uint32_t u_d1 = 0, u_a2 = 0;        // contractions 1 and 2 issued so far
             bool ok = wait_bar(BAR(BAR_BTAB), 0, ctl, p.status, 2);
             constexpr uint32_t id1g = tc::idesc_bf16_f32(128, RC, true);
             auto issue_mma1 = [&](int c) {
-                const int b = c & 1;
                 const uint32_t bc = b1 + (uint32_t)c * (2 * RC * NSP * 2);
 #pragma unroll
                 for (int s = 0; s < 3; ++s)
 #pragma unroll
                     for (int kk = 0; kk < NSP / 16; ++kk)
-                        tc::mma_ts(tmem + CL::D1 + b * 2 * RC, tmem + CL::A1 + s * (NSP / 2) + kk * 8,
+                        tc::mma_ts(tmem + CL::D1, tmem + CL::A1 + s * (NSP / 2) + kk * 8,
                                    tc::sdesc_noswz(bc + kk * 256, 128, (NSP / 8) * 128), id1,
                                    (s | kk) != 0);
                 // Gibbs layer into the reverse half: B = nu of contraction 2 ([species][reaction]
@@ -342,60 +343,51 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 for (int s = 0; s < 3; ++s)
 #pragma unroll
                     for (int kk = 0; kk < NSP / 16; ++kk)
-                        tc::mma_ts(tmem + CL::D1 + b * 2 * RC + RC,
-                                   tmem + CL::AG + s * (NSP / 2) + kk * 8,
+                        tc::mma_ts(tmem + CL::D1 + RC, tmem + CL::AG + s * (NSP / 2) + kk * 8,
                                    tc::sdesc_noswz(bg + kk * 2 * (RC / 8) * 128, (RC / 8) * 128, 128),
                                    id1g, 1);
-                tc::commit(BAR(BAR_D1FULL0 + b));
-                ++u_d1[b];
+                tc::commit(BAR(BAR_D1FULL));
+                ++u_d1;
             };
             auto mma2 = [&](int c) {
-                const int b = c & 1;
                 const uint32_t bc = b2 + (uint32_t)c * (NSP * RC * 2);
 #pragma unroll
                 for (int s = 0; s < 2; ++s)
 #pragma unroll
                     for (int kk = 0; kk < RC / 16; ++kk)
-                        tc::mma_ts(tmem + CL::D2, tmem + CL::A2 + b * RC + s * (RC / 2) + kk * 8,
+                        tc::mma_ts(tmem + CL::D2, tmem + CL::A2 + s * (RC / 2) + kk * 8,
                                    tc::sdesc_noswz(bc + kk * 256, 128, (RC / 8) * 128), id2,
                                    (c | s | kk) != 0);
-                tc::commit(BAR(BAR_A2EMPTY0 + b));
-                ++u_a2[b];
+                tc::commit(BAR(BAR_A2EMPTY));
+                ++u_a2;
                 if (c == p.nch - 1) tc::commit(BAR(BAR_D2FULL));
             };
             int it = 0;
             for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x, ++it) {
                 if (!(ok = wait_bar(BAR(BAR_A1FULL), it & 1, ctl, p.status, 2))) break;
                 tc::fence_after();
-                // Issue whatever is ready: contraction 1 into either tensor-memory buffer as
-                // soon as its epilogue pair has read it, contraction 2 strictly in chunk order
-                // (the omega accumulation order, hence the rounding, is fixed).
-                int c1[2] = {0, 1}, c2 = 0;
+                // Contraction 1 of the next chunk as soon as the epilogue has read the current
+                // one; contraction 2 strictly in chunk order (the omega accumulation order,
+                // hence the rounding, is fixed), first when both are ready.
+                int c1 = 0, c2 = 0;
                 bool d2_free = false, a1_freed = false;
                 long long t0 = clock64();
                 while (c2 < p.nch) {
                     bool prog = false;
-                    // contraction 2 first: it frees an epilogue pair's q_net buffer, while a
-                    // ready contraction 1 only runs ahead
                     if (!d2_free) d2_free = tc::mbar_test_wait(BAR(BAR_D2EMPTY), (it & 1) ^ 1);
-                    const int b2c = c2 & 1;
-                    if (d2_free && tc::mbar_test_wait(BAR(BAR_A2FULL0 + b2c), u_a2[b2c] & 1)) {
+                    if (d2_free && c2 < c1 && tc::mbar_test_wait(BAR(BAR_A2FULL), u_a2 & 1)) {
                         tc::fence_after();
                         mma2(c2);
                         ++c2;
                         prog = true;
                     }
-#pragma unroll
-                    for (int b = 0; b < 2; ++b) {
-                        if (c1[b] < p.nch &&
-                            tc::mbar_test_wait(BAR(BAR_D1EMPTY0 + b), (u_d1[b] & 1) ^ 1)) {
-                            tc::fence_after();
-                            issue_mma1(c1[b]);
-                            c1[b] += 2;
-                            prog = true;
-                        }
+                    if (c1 < p.nch && tc::mbar_test_wait(BAR(BAR_D1EMPTY), (u_d1 & 1) ^ 1)) {
+                        tc::fence_after();
+                        issue_mma1(c1);
+                        ++c1;
+                        prog = true;
                     }
-                    if (!a1_freed && c1[0] >= p.nch && c1[1] >= p.nch) {
+                    if (!a1_freed && c1 >= p.nch) {
                         // completes when every contraction 1 of the tile has read its operands
                         tc::commit(BAR(BAR_A1FREE));
                         a1_freed = true;
@@ -419,9 +411,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
     } else {
         // ------------------------------------------------------------- epilogue
         const int ew = warp - kEpiWarp0;             // 0..15
-        const int g = ew >> 2;                        // warpgroup 0..3
-        const int pr = g >> 1;                        // chunk parity of this warpgroup pair
-        const int hf = g & 1;                         // half of the chunk's reactions
+        const int g = ew >> 2;                        // warpgroup 0..3: quarter of each chunk
         const int q = warp & 3;                       // lane quarter of tensor memory
         const int row = q * 32 + lane;
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
@@ -585,17 +575,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
             };
             // two groups while contraction 1 of the first chunks runs
             for (int pre = 0; pre < 2 && gi < n_g; ++pre) mult_group();
-            // ---- this pair's chunks, this warpgroup's half of each
-            for (int c = pr; c < p.nch; c += 2, ++u) {
+            // ---- every chunk, this warpgroup's quarter of its reactions
+            for (int c = 0; c < p.nch; ++c, ++u) {
                 if (!fready && c >= p.fac_chunk0 && !(ok = mult_finish())) break;
-                if (!(ok = wait_bar(BAR(BAR_D1FULL0 + pr), u & 1, ctl, p.status, 3))) break;
+                if (!(ok = wait_bar(BAR(BAR_D1FULL), u & 1, ctl, p.status, 3))) break;
                 tc::fence_after();
                 uint32_t sf[RH], sr[RH], fv[8];
-                const uint32_t d1 = tmem + lane_off + CL::D1 + pr * 2 * RC + hf * RH;
-                // both halves of contraction 1 and this half chunk's (at most 4) multipliers,
+                const uint32_t d1 = tmem + lane_off + CL::D1 + g * RH;
+                // both halves of contraction 1 and this quarter's (at most 8) multipliers,
                 // consecutive columns, behind one completion wait
-                const uint32_t hm = tabs.hmask[c * 2 + hf];
-                const int fb = hm ? tabs.fbase[c * 2 + hf] : 0;
+                const int mq = c * NQ + g;
+                const uint32_t hm = tabs.hmask[mq];
+                const int fb = hm ? tabs.fbase[mq] : 0;
                 const int lb = min(fb, CL::kMaxFactors - 8);
                 tc::tmem_ld16_nw(d1, sf);
                 tc::tmem_ld16_nw(d1 + RC, sr);
@@ -608,9 +599,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 tc::tmem_wait_ld_tie(sf, sr, fv);
                 tc::fence_before();
                 __syncwarp();
-                if (lane == 0) tc::mbar_arrive(BAR(BAR_D1EMPTY0 + pr));
-                const int j0 = c * RC + hf * RH;
-                const uint32_t lm = tabs.lmask[c * 2 + hf], rm = tabs.rmask[c * 2 + hf];
+                if (lane == 0) tc::mbar_arrive(BAR(BAR_D1EMPTY));
+                const int j0 = c * RC + g * RH;
+                const uint32_t lm = tabs.lmask[mq], rm = tabs.rmask[mq];
                 float q[RH];
 #pragma unroll
                 for (int r = 0; r < RH; ++r)
@@ -638,15 +629,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                     hw[r / 2] = h;
                     lw[r / 2] = tc::pack_bf16x2(r0, r1);
                 }
-                if (!(ok = wait_bar(BAR(BAR_A2EMPTY0 + pr), (u & 1) ^ 1, ctl, p.status, 3))) break;
+                if (!(ok = wait_bar(BAR(BAR_A2EMPTY), (u & 1) ^ 1, ctl, p.status, 3))) break;
                 tc::fence_after();
-                const uint32_t a2 = tmem + lane_off + CL::A2 + pr * RC + hf * (RH / 2);
+                const uint32_t a2 = tmem + lane_off + CL::A2 + g * (RH / 2);
                 tc::tmem_st8(a2, hw);
                 tc::tmem_st8(a2 + RC / 2, lw);
                 tc::tmem_wait_st();
                 tc::fence_before();
                 __syncwarp();
-                if (lane == 0) tc::mbar_arrive(BAR(BAR_A2FULL0 + pr));
+                if (lane == 0) tc::mbar_arrive(BAR(BAR_A2FULL));
                 if (!fready && gi < n_g) mult_group();   // while the tensor pipe works
             }
             if (!ok) break;
@@ -739,19 +730,17 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
     if (nsp <= 32) nsp = 32;
     else if (nsp <= 64) nsp = 64;
     else return set_error(CHEM_EUNSUPPORTED, "split-BF16 path supports up to 62 species");
-    // an even number of chunks keeps both epilogue warpgroup pairs equally busy
-    int nch = (nr + RC - 1) / RC;
-    if (nch > 1 && (nch & 1)) ++nch;
+    const int nch = (nr + RC - 1) / RC;
     const int nrp = nch * RC;
     // Reactions without a third-body or falloff factor fill the first chunks (spread evenly
     // over their slots); those with one go to the last K chunks, round-robin over their
-    // half chunks (at most 8 per half chunk, one 8-column multiplier load), with the rest
-    // of the plain reactions.  The epilogue evaluates the multipliers in the waits of its
-    // first chunks, before they are needed.
+    // chunk quarters (at most 8 per quarter, one 8-column multiplier load), with the rest
+    // of the plain reactions.  The epilogue evaluates the multipliers while the tensor pipe
+    // works on the first chunks, before they are needed.
     std::vector<int> plain, special;
     for (int j = 0; j < nr; ++j) (d->kind[j] == 0 ? plain : special).push_back(j);
     const int S = (int)special.size();
-    int K = S ? (S + 2 * 8 - 1) / (2 * 8) : 0;
+    int K = S ? (S + NQ * 8 - 1) / (NQ * 8) : 0;
     if (K > nch) return set_error(CHEM_EUNSUPPORTED, "split-BF16 path: too many third-body reactions");
     while (K < nch && (nch - K) * RC + K * RC - S < (int)plain.size()) ++K;   // room for all
     std::vector<int> order(nrp, -1);        // slot -> reaction (-1: padding)
@@ -761,8 +750,8 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
         const int n_head = std::min((int)plain.size(), head_slots);
         for (int i = 0; i < n_head; ++i)
             order[(size_t)((int64_t)i * head_slots / n_head)] = plain[pi++];
-        for (int i = 0; i < S; ++i) {                    // round-robin over the tail half chunks
-            const int hc = (nch - K) * 2 + i % (2 * K), pos = i / (2 * K);
+        for (int i = 0; i < S; ++i) {                    // round-robin over the tail quarters
+            const int hc = (nch - K) * NQ + i % (NQ * K), pos = i / (NQ * K);
             order[(size_t)hc * RH + pos] = special[i];
         }
         for (int jj = head_slots; jj < nrp && pi < plain.size(); ++jj)
@@ -773,7 +762,7 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
     std::vector<CoefS> cf(nrp);
     // per half chunk: third-body, live and reversible masks, then the multiplier base index;
     // then the slot of every multiplier
-    std::vector<uint32_t> hmask((size_t)nch * 8, 0);
+    std::vector<uint32_t> hmask((size_t)nch * 4 * NQ, 0);
     std::vector<uint32_t> fslot;
     std::vector<FallBF> fl;
     std::vector<uint16_t> tbsp;
@@ -793,14 +782,14 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
         CoefS &C = cf[jj];
         memset(&C, 0, sizeof C);
         const int c = jj / RC, r = jj % RC;
-        const size_t mslot = (size_t)c * 2 + r / RH;
+        const size_t mslot = (size_t)c * NQ + r / RH;
         if (order[jj] < 0) {                    // padding slot: skipped by the epilogue
             C.kf = make_float4(kDead, 0, 0, 0);
             continue;
         }
         const int j = order[jj];
-        hmask[(size_t)nch * 2 + mslot] |= 1u << (r % RH);
-        if (d->reversible[j]) hmask[(size_t)nch * 4 + mslot] |= 1u << (r % RH);
+        hmask[(size_t)nch * NQ + mslot] |= 1u << (r % RH);
+        if (d->reversible[j]) hmask[(size_t)nch * 2 * NQ + mslot] |= 1u << (r % RH);
         const int kind = d->kind[j];
         const double *ar = d->arrh + (size_t)j * 3;
         int ordf = 0, ordr = 0;
@@ -820,7 +809,7 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
         C.kf = make_float4((float)(ar[0] * kLog2e), (float)ar[1], (float)(-ar[2] * kLog2e),
                            fbits(kind));
         if (kind >= 1) {
-            if (!hmask[mslot]) hmask[(size_t)nch * 6 + mslot] = (uint32_t)fslot.size();
+            if (!hmask[mslot]) hmask[(size_t)nch * 3 * NQ + mslot] = (uint32_t)fslot.size();
             hmask[mslot] |= 1u << (r % RH);
             fslot.push_back((uint32_t)jj);
             C.meta.x = (int)tbsp.size();
@@ -879,9 +868,9 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
         if ((int)fslot.size() > max_fac)
             return set_error(CHEM_EUNSUPPORTED,
                              "split-BF16 path holds at most %d third-body/falloff reactions", max_fac);
-        for (size_t h2 = 0; h2 < (size_t)nch * 2; ++h2)
+        for (size_t h2 = 0; h2 < (size_t)nch * NQ; ++h2)
             if (__builtin_popcount(hmask[h2]) > 8)
-                return set_error(CHEM_EUNSUPPORTED, "more than 8 third-body reactions in a chunk half");
+                return set_error(CHEM_EUNSUPPORTED, "more than 8 third-body reactions in a chunk quarter");
         // evaluation order: third-body multipliers first, then falloff (their columns stay
         // in slot order, so each half chunk reads consecutive columns)
         std::vector<uint32_t> ord_slot, ord_col;
