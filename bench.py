@@ -190,7 +190,7 @@ def run_reference(args):
     t0 = time.perf_counter()
     O.source_term(om, T[:1024], P[:1024], Y[:1024], nthreads=nth)
     rate = 1024 / max(time.perf_counter() - t0, 1e-6)
-    per_step = max(256, int(rate * 60.0 / max(1, args.steps + args.warmup)))
+    per_step = max(256, int(rate * args.ref_seconds / max(1, args.steps + args.warmup)))
     per_step = min(per_step, N_CELLS)
     for w in range(args.warmup):
         lo = (w * per_step) % (N_CELLS - per_step + 1)
@@ -246,6 +246,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "split_bf16", "fp32", "fp64"])
     ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--ref-seconds", type=float, default=60.0,
+                    help="reference arm: oracle seconds for the whole run (sample size)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the secondary precision paths and the CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
