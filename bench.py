@@ -340,6 +340,7 @@ def main():
         extras(line, h, mech, T, P, Y, dev, dev32, out32, ns, prec_name, stream, args)
         extras_integrator(line, mech, dev, stream)
         extras_heavy(line, dev, stream)
+        extras_kc_ann(line, dev, stream)
         extras_serving(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -512,6 +513,45 @@ def extras_heavy(line, dev, stream, n=1 << 18):
         res[f"vjp_{name}"] = {"cells_per_s": n / (ms_v * 1e-3), "ms_per_call": ms_v}
     h.close()
     line["heavy_160_1000"] = res
+
+
+def extras_kc_ann(line, dev, stream, n=100_000):
+    """Approximate-ANN ln K_c (Sec. 2.3, the paper's Fig. 10 comparison at N_C = 1e5): the FP32
+    source term with the exact ln K_c against the same kernel with ln K_c from LF (1 x 8) and
+    HF (3 x 32) ELU networks trained on a temperature sweep of the exact ln K_c (1e6 samples);
+    errors against the FP64 path on the same inputs."""
+    import torch
+    from paper_2008_08483_gb300 import chem, kc_ann, synth
+    res = {"cells": n}
+    for size in ("gri_53_325", "heavy_160_1000"):
+        mech = synth.make_mechanism(size, seed=MECH_SEED)
+        h = chem.Mechanism(mech)
+        T, P, Y = synth.make_states(mech, n, seed=STATE_SEED)
+        din = [torch.as_tensor(a, dtype=torch.float32, device=dev) for a in (T, P, Y)]
+        o = torch.empty((n, mech.n_species), dtype=torch.float32, device=dev)
+        ms_exact = time_device(lambda: chem.source_term(h, *din, chem.FP32, out=o, stream=stream),
+                               20, 3, stream, 1, dev)
+        ref = chem.source_term(h, *[t.double() for t in din], chem.FP64)
+        scale = ref.abs().max(1).values
+        Ts = torch.linspace(400.0, 3000.0, 1001, dtype=torch.float64, device=dev)
+        exact_kc = chem.log_kc(h, Ts).cpu().numpy()
+        r = {"fp32_exact": {"ms": ms_exact, "cells_per_s": n / (ms_exact * 1e-3)}}
+        for name, (nl, nh) in (("LF_1x8", (1, 8)), ("HF_3x32", (3, 32))):
+            params, hist = kc_ann.train_kc_ann(h, nl, nh, "elu", steps=2000)
+            ann = chem.KcAnn(h, params)
+            ms = time_device(lambda: chem.source_term_kc_ann(h, ann, *din, out=o, stream=stream),
+                             20, 3, stream, 1, dev)
+            err = ((o.double() - ref).abs().max(1).values / scale).cpu().numpy()
+            kc_err = np.abs(kc_ann.forward_np(params, Ts.cpu().numpy()) - exact_kc)
+            r[name] = {"ms": ms, "cells_per_s": n / (ms * 1e-3), "speedup_vs_exact": ms_exact / ms,
+                       "err_cell_median": float(np.median(err)),
+                       "err_cell_p99": float(np.quantile(err, 0.99)),
+                       "lnkc_max_abs_err": float(kc_err.max()),
+                       "lnkc_mean_abs_err": float(kc_err.mean()), "final_loss": hist[-1][1]}
+            ann.close()
+        res[size] = r
+        h.close()
+    line["kc_ann"] = res
 
 
 def extras_serving(line, n_ranks=64, req_per_rank=1, seed=42, budget=8 << 30):

@@ -194,6 +194,47 @@ chem_status chem_source_term_jacobian(const chem_mech *mech, int64_t n_cells, co
                                       chem_precision precision, void *stream);
 
 /*
+ * Exact equilibrium constants: lnKc[i * ldK + j] = ln K_c of reaction j at T[i] (Eqs. 8-11,
+ * the Gibbs layer folded through the net stoichiometry in FP64 at load), FP64 device arrays,
+ * ldK >= n_reactions.  The training targets of the approximate network below.
+ * Asynchronous on `stream`.  Errors: CHEM_EINVAL, CHEM_ECUDA.
+ */
+chem_status chem_log_kc(const chem_mech *mech, int64_t n, const double *T, double *lnKc,
+                        int64_t ldK, void *stream);
+
+/*
+ * Approximate-ANN equilibrium constants (Sec. 2.3, Eqs. 12-14; the paper's "Arch 2": the
+ * only input is ln T).  x = (ln T - x_mean) / x_std; a_1 = act(w_in x + b_in);
+ * a_{l+1} = act(W_l a_l + b_l) for l = 1 .. n_layers - 1; ln K_c,j = y_mean_j + y_std_j
+ * (w_out,j . a + b_out,j).  All arrays are HOST float arrays copied by chem_kc_ann_load:
+ * w_in, b_in [n_hidden]; w_hid [n_layers - 1][n_hidden][n_hidden] (row: output unit) and
+ * b_hid [n_layers - 1][n_hidden] (may be NULL for one layer); w_out [n_reactions][n_hidden],
+ * b_out, y_mean, y_std [n_reactions].  n_hidden <= 32.
+ */
+enum { CHEM_ACT_RELU = 0, CHEM_ACT_ELU = 1 };
+typedef struct {
+    int32_t n_layers, n_hidden, activation;
+    float x_mean, x_std;
+    const float *w_in, *b_in, *w_hid, *b_hid, *w_out, *b_out, *y_mean, *y_std;
+} chem_kc_ann_desc;
+typedef struct chem_kc_ann chem_kc_ann;       /* opaque, device-resident, immutable */
+
+chem_status chem_kc_ann_load(const chem_mech *mech, const chem_kc_ann_desc *desc,
+                             chem_kc_ann **out);
+chem_status chem_kc_ann_free(chem_kc_ann *ann);
+
+/*
+ * chem_source_term's CHEM_FP32 path (float arrays, same layouts) with ln K_c of every
+ * reversible reaction taken from the network instead of the Gibbs layer: an approximation
+ * (its error is the network's), evaluated once per cell before the reaction loop.
+ * Errors: as chem_source_term, plus CHEM_EINVAL for a network of another mechanism.
+ */
+chem_status chem_source_term_kc_ann(const chem_mech *mech, const chem_kc_ann *ann,
+                                    int64_t n_cells, const float *T, const float *P,
+                                    const float *Y, int64_t ldY, float *omega, int64_t ldO,
+                                    void *stream);
+
+/*
  * Constant-pressure adiabatic 0-D reactor: the stiff time integration the paper names as
  * future work for the source term (Conclusion; its own test integrates the same reactor
  * explicitly, Sec. 3.1.2).  Per cell the state is y = (T, Y_1 .. Y_ns) at fixed P and

@@ -106,9 +106,25 @@ double orc_troe_F(const double *tp, double T, double Pr)
  * the falloff factor applied), q_f and q_r.  Then omega (Eq. 2).  Any output
  * pointer may be NULL.  g_RT is scratch of ns doubles.
  */
+static void orc_cell_detail_kc(const orc_mech *m, double T, const double *C, double *g_RT,
+                               const double *lnKc_in, double *lnkf_out, double *lnKc_out,
+                               double *M_out, double *kf_out, double *kr_out, double *qf_out,
+                               double *qr_out, double *omega);
+
 void orc_cell_detail(const orc_mech *m, double T, const double *C, double *g_RT,
                      double *lnkf_out, double *lnKc_out, double *M_out, double *kf_out,
                      double *kr_out, double *qf_out, double *qr_out, double *omega)
+{
+    orc_cell_detail_kc(m, T, C, g_RT, NULL, lnkf_out, lnKc_out, M_out, kf_out, kr_out, qf_out,
+                       qr_out, omega);
+}
+
+/* As orc_cell_detail, with ln K_c of every reaction given (lnKc_in, e.g. from the
+ * approximate network of Sec. 2.3) instead of computed from the thermo (Eq. 8). */
+static void orc_cell_detail_kc(const orc_mech *m, double T, const double *C, double *g_RT,
+                               const double *lnKc_in, double *lnkf_out, double *lnKc_out,
+                               double *M_out, double *kf_out, double *kr_out, double *qf_out,
+                               double *qr_out, double *omega)
 {
     const int ns = m->ns;
     orc_thermo(m, T, NULL, NULL, NULL, g_RT);
@@ -151,6 +167,7 @@ void orc_cell_detail(const orc_mech *m, double T, const double *C, double *g_RT,
             }
         }
         lnKc += dnu * ln_pref_RT;
+        if (lnKc_in) lnKc = lnKc_in[j];
         /* Eq. 7 and the irreversibility indicator of Sec. 2.4 */
         double kr = m->rev[j] ? kf / exp(lnKc) : 0.0;
         /* Eq. 3 */
@@ -574,4 +591,22 @@ void orc_ode_jac(const orc_mech *m, double P, const double *y, double *J)
         J[1 + nn] = -dQ / rc + Q * drc / (rc * rc);
     }
     free(buf);
+}
+
+/* omega [n][ldO] from (T, P, Y) with ln K_c given per cell and reaction, lnKc [n][ldK]
+ * (one thread; for checks of the approximate-network path). */
+int orc_source_term_tpy_kc(const orc_mech *m, int64_t n, const double *T, const double *P,
+                           const double *Y, int64_t ldY, const double *lnKc, int64_t ldK,
+                           double *omega, int64_t ldO)
+{
+    double *C = (double *)malloc(sizeof(double) * (size_t)m->ns * 2);
+    if (!C) return -1;
+    double *g = C + m->ns;
+    for (int64_t i = 0; i < n; ++i) {
+        orc_concentrations(m, T[i], P[i], Y + i * ldY, C);
+        orc_cell_detail_kc(m, T[i], C, g, lnKc + i * ldK, NULL, NULL, NULL, NULL, NULL, NULL,
+                           NULL, omega + i * ldO);
+    }
+    free(C);
+    return 0;
 }

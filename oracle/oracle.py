@@ -60,6 +60,9 @@ def _load():
             lib.orc_cell_detail.argtypes = [P, C.c_double, P, P, P, P, P, P, P, P, P, P]
             lib.orc_jacobian_tc.argtypes = [P, C.c_double, P, P, P, P, P]
             lib.orc_dwdC.argtypes = [P, C.c_double, P, P, P]
+            lib.orc_source_term_tpy_kc.argtypes = [P, C.c_int64, P, P, P, C.c_int64, P,
+                                                   C.c_int64, P, C.c_int64]
+            lib.orc_source_term_tpy_kc.restype = C.c_int
             lib.orc_ode_rhs.argtypes = [P, C.c_double, P, P]
             lib.orc_ode_jac.argtypes = [P, C.c_double, P, P]
             for f in (lib.orc_source_term_tpy, lib.orc_source_term_tc):
@@ -237,3 +240,17 @@ def integrate_reactor(mech, T0: float, P: float, Y0, t_end: float, rtol: float =
     t_ign = float(sol.t_events[0][0]) if len(sol.t_events[0]) else float("nan")
     return dict(y_end=sol.y[:, -1].copy(), t_ign=t_ign, nfev=int(sol.nfev),
                 njev=int(sol.njev), nsteps=int(len(sol.t) - 1) if t_eval is None else -1, sol=sol)
+
+
+def source_term_kc(mech, T, P, Y, lnKc) -> np.ndarray:
+    """omega [n, ns] with the ln K_c of every cell and reaction given, lnKc [n, nr]."""
+    om = _om(mech)
+    T = np.ascontiguousarray(T, np.float64)
+    P = np.ascontiguousarray(P, np.float64)
+    Y = np.ascontiguousarray(Y, np.float64)
+    K = np.ascontiguousarray(lnKc, np.float64)
+    out = np.zeros((T.shape[0], om.ns))
+    if _load().orc_source_term_tpy_kc(om.ref, T.shape[0], _ptr(T), _ptr(P), _ptr(Y), Y.shape[1],
+                                      _ptr(K), K.shape[1], _ptr(out), om.ns) != 0:
+        raise RuntimeError("oracle source term failed")
+    return out

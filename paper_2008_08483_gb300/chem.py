@@ -41,6 +41,14 @@ class _Desc(C.Structure):
                 ("p_ref", C.c_double)]
 
 
+class _KcAnnDesc(C.Structure):
+    _fields_ = [("n_layers", C.c_int32), ("n_hidden", C.c_int32), ("activation", C.c_int32),
+                ("x_mean", C.c_float), ("x_std", C.c_float), ("w_in", C.c_void_p),
+                ("b_in", C.c_void_p), ("w_hid", C.c_void_p), ("b_hid", C.c_void_p),
+                ("w_out", C.c_void_p), ("b_out", C.c_void_p), ("y_mean", C.c_void_p),
+                ("y_std", C.c_void_p)]
+
+
 class _IntegOpts(C.Structure):
     _fields_ = [("h_init", C.c_double), ("h_min", C.c_double), ("h_max", C.c_double),
                 ("max_steps", C.c_int64), ("ign_dT", C.c_double), ("t_ign", C.c_void_p),
@@ -109,6 +117,13 @@ def lib():
             L.chem_integrate_cells_noalloc.argtypes = L.chem_integrate_cells.argtypes
             L.chem_integrate_cells_noalloc.restype = C.c_int
             L.chem_rosenbrock_tableau.argtypes = [C.POINTER(I32), P, P, P, P, P]
+            L.chem_log_kc.argtypes = [P, I64, P, P, I64, P]
+            L.chem_kc_ann_load.argtypes = [P, C.POINTER(_KcAnnDesc), C.POINTER(P)]
+            L.chem_kc_ann_free.argtypes = [P]
+            L.chem_source_term_kc_ann.argtypes = [P, P, I64, P, P, P, I64, P, I64, P]
+            for f in (L.chem_log_kc, L.chem_kc_ann_load, L.chem_kc_ann_free,
+                      L.chem_source_term_kc_ann):
+                f.restype = C.c_int
             L.chem_serve_create.argtypes = [C.POINTER(P), I32, C.c_size_t, C.POINTER(P)]
             L.chem_serve_submit.argtypes = [P, C.POINTER(_Request), C.POINTER(C.c_uint64)]
             L.chem_serve_poll.argtypes = [P, C.c_uint64, C.POINTER(_Result), I64]
@@ -486,3 +501,70 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------------------
+# equilibrium constants: exact table and the approximate network (chem_log_kc, chem_kc_ann_*)
+# ---------------------------------------------------------------------------------------
+
+def log_kc(mech: Mechanism, T, stream=None):
+    """ln K_c [n, n_reactions] (FP64) at the temperatures T (CUDA float64 tensor)."""
+    import torch
+    if not T.is_cuda or T.dtype != torch.float64 or T.stride(0) != 1:
+        raise ChemError(1, "T must be a contiguous CUDA float64 tensor")
+    out = torch.empty((T.shape[0], mech.n_reactions), dtype=torch.float64, device=T.device)
+    _check(lib().chem_log_kc(mech.handle, T.shape[0], T.data_ptr(), out.data_ptr(),
+                             out.stride(0), _stream_ptr(stream)))
+    return out
+
+
+class KcAnn:
+    """An approximate-ANN ln K_c network loaded for one mechanism (chem_kc_ann_load).
+    `params`: dict with n_layers, n_hidden, activation ('relu' | 'elu'), x_mean, x_std and
+    float32 arrays w_in, b_in, w_hid, b_hid, w_out, b_out, y_mean, y_std."""
+
+    def __init__(self, mech: Mechanism, params):
+        self.mech = mech
+        f = lambda k: None if params.get(k) is None else np.ascontiguousarray(params[k], np.float32)
+        self._keep = {k: f(k) for k in ("w_in", "b_in", "w_hid", "b_hid", "w_out", "b_out",
+                                         "y_mean", "y_std")}
+        act = {"relu": 0, "elu": 1}[params["activation"]]
+        d = _KcAnnDesc(int(params["n_layers"]), int(params["n_hidden"]), act,
+                       float(params["x_mean"]), float(params["x_std"]),
+                       *(_ptr(self._keep[k]) for k in ("w_in", "b_in", "w_hid", "b_hid",
+                                                       "w_out", "b_out", "y_mean", "y_std")))
+        h = C.c_void_p()
+        _check(lib().chem_kc_ann_load(mech.handle, C.byref(d), C.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ChemError(1, "network was freed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _check(lib().chem_kc_ann_free(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def source_term_kc_ann(mech: Mechanism, ann: KcAnn, T, P, Y, out=None, stream=None):
+    """omega [n, ns] (float32) on the FP32 path with ln K_c from the network."""
+    import torch
+    for name, t in (("T", T), ("P", P), ("Y", Y)):
+        if not t.is_cuda or t.dtype != torch.float32:
+            raise ChemError(1, f"{name} must be a CUDA float32 tensor")
+    n = T.shape[0]
+    if out is None:
+        out = torch.empty((n, mech.n_species), dtype=torch.float32, device=T.device)
+    _check(lib().chem_source_term_kc_ann(mech.handle, ann.handle, n, T.data_ptr(), P.data_ptr(),
+                                         Y.data_ptr(), Y.stride(0), out.data_ptr(), out.stride(0),
+                                         _stream_ptr(stream)))
+    return out

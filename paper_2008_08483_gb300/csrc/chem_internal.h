@@ -93,6 +93,18 @@ struct MechViewF64 {
     double t_mid;
 };
 
+// Approximate-ANN ln K_c (Sec. 2.3, Eqs. 12-14): standardised ln T -> N_L hidden layers of
+// N_H units (ReLU or ELU) -> N_R standardised ln K_c, all weights FP32 in device memory.
+constexpr int kAnnMaxHidden = 32;
+struct KcAnnView {
+    int nl, nh, act;             // act: 0 ReLU, 1 ELU
+    float x_mean, x_inv_std;
+    const float *w_in, *b_in;    // [nh], [nh]
+    const float *w_hid, *b_hid;  // [nl-1][nh][nh] (row = output unit), [nl-1][nh]
+    const float *w_out, *b_out;  // [nr][nh], [nr]
+    const float *y_mean, *y_std; // [nr]
+};
+
 struct MechViewF32 {
     int ns, nr;
     const RxnF32 *rxn;
@@ -143,5 +155,10 @@ chem_status launch_source_fp64(const chem_mech *m, int64_t n, const double *T, c
 chem_status launch_source_fp32(const chem_mech *m, int64_t n, const float *T, const float *P,
                                const float *Y, int64_t ldY, float *om, int64_t ldO,
                                cudaStream_t s);
+chem_status launch_source_fp32_ann(const chem_mech *m, const KcAnnView &av, int64_t n,
+                                   const float *T, const float *P, const float *Y, int64_t ldY,
+                                   float *om, int64_t ldO, cudaStream_t s);
+chem_status launch_log_kc(const chem_mech *m, int64_t n, const double *T, double *lnkc,
+                          int64_t ldK, cudaStream_t s);
 
 }  // namespace chem

@@ -10,6 +10,7 @@
 //   ln q_r = sum_k nu''_kj ln C_k + ln k_inf,j - ln K_c,j + (same factor)   [reversible]
 //   omega_k += (nu''_kj - nu'_kj) (exp(ln q_f) - exp(ln q_r))
 #include <math.h>
+#include <string.h>
 
 #include "chem_internal.h"
 
@@ -160,9 +161,16 @@ __device__ __forceinline__ float df_exp2(df x)
 
 constexpr float kLg2Floor = -1000.0f;        // log2 X of an absent species (2^x underflows to 0)
 
-template <int BLK>
+__device__ __forceinline__ float ann_act(float x, int act)
+{
+    return act ? (x > 0.0f ? x : expm1f(x)) : fmaxf(x, 0.0f);
+}
+
+// With ANN, ln K_c of every reversible reaction comes from the approximate network
+// (Sec. 2.3, Eqs. 12-14) evaluated once per cell, instead of the Gibbs layer.
+template <int BLK, bool ANN>
 __global__ void __launch_bounds__(BLK)
-k_source_f32(MechViewF32 mv, int64_t n, const float *__restrict__ T,
+k_source_f32(MechViewF32 mv, KcAnnView av, int64_t n, const float *__restrict__ T,
              const float *__restrict__ P, const float *__restrict__ Y, int64_t ldY,
              float *__restrict__ om, int64_t ldO)
 {
@@ -176,6 +184,7 @@ k_source_f32(MechViewF32 mv, int64_t n, const float *__restrict__ T,
     float *sGl = smem32 + 3 * ns * BLK + tid;
     float *sWs = smem32 + 4 * ns * BLK + tid;  // omega_k, compensated sum
     float *sWc = smem32 + 5 * ns * BLK + tid;
+    float *sH = smem32 + 6 * ns * BLK + tid;   // ANN: two layers of hidden units
     const float Tf = T[i], Pf = P[i];
     const float *Yi = Y + i * ldY;
     double sum = 0.0;
@@ -217,13 +226,30 @@ k_source_f32(MechViewF32 mv, int64_t n, const float *__restrict__ T,
         }
         sE[k * BLK] = e;
         sF[k * BLK] = f;
-        const float2 *c = mv.spec[k].gl[rg];
-        df g = mkdf(c[0]);
-        for (int m = 1; m < 7; ++m) g = df_add(g, df_mul(mkdf(c[m]), phi[m]));
-        sGh[k * BLK] = g.h;
-        sGl[k * BLK] = g.l;
+        if (!ANN) {
+            const float2 *c = mv.spec[k].gl[rg];
+            df g = mkdf(c[0]);
+            for (int m = 1; m < 7; ++m) g = df_add(g, df_mul(mkdf(c[m]), phi[m]));
+            sGh[k * BLK] = g.h;
+            sGl[k * BLK] = g.l;
+        }
         sWs[k * BLK] = 0.0f;
         sWc[k * BLK] = 0.0f;
+    }
+    int cur = 0;                               // ANN: layer buffer holding the last layer
+    if (ANN) {
+        const float x = (logf(Tf) - av.x_mean) * av.x_inv_std;
+        for (int h = 0; h < av.nh; ++h) sH[h * BLK] = ann_act(fmaf(av.w_in[h], x, av.b_in[h]), av.act);
+        for (int l = 0; l + 1 < av.nl; ++l) {
+            const float *W = av.w_hid + (size_t)l * av.nh * av.nh;
+            for (int o = 0; o < av.nh; ++o) {
+                float a = av.b_hid[l * av.nh + o];
+                for (int h = 0; h < av.nh; ++h)
+                    a = fmaf(W[o * av.nh + h], sH[(cur * kAnnMaxHidden + h) * BLK], a);
+                sH[((cur ^ 1) * kAnnMaxHidden + o) * BLK] = ann_act(a, av.act);
+            }
+            cur ^= 1;
+        }
     }
     for (int j = 0; j < mv.nr; ++j) {
         const RxnF32 *R = mv.rxn + j;
@@ -283,20 +309,36 @@ k_source_f32(MechViewF32 mv, int64_t n, const float *__restrict__ T,
             xf = df_add_f(df_add_f(xf, ei), fs);
             qn = df_exp2(xf);
             if (R->rev) {
-                // log2 K_c = sum_k nu_kj (-g_k/RT) + dnu log2(p_ref/RT) (Eqs. 8-9)
-                df lkc = df_mul_f(lgpRT, (float)R->dnu);
+                df lkc;
                 float er = 0.0f, fr = 0.0f;
-                for (int t = 0; t < R->nr; ++t) {
-                    const int k = R->spr[t];
-                    const float nu = (float)R->nur[t];
-                    lkc = df_add(lkc, df_mul_f(mkdf(sGh[k * BLK], sGl[k * BLK]), nu));
-                    er = fmaf(nu, sE[k * BLK], er);
-                    fr = fmaf(nu, sF[k * BLK], fr);
-                }
-                for (int t = 0; t < R->nf; ++t) {
-                    const int k = R->spf[t];
-                    lkc = df_add(lkc, df_mul_f(mkdf(sGh[k * BLK], sGl[k * BLK]),
-                                               -(float)R->nuf[t]));
+                if (ANN) {
+                    // ln K_c = y_mean + y_std (b + sum_h w_h a_h) (Eq. 14), in log2 units
+                    const float *w = av.w_out + (size_t)j * av.nh;
+                    float a = av.b_out[j];
+                    for (int h = 0; h < av.nh; ++h)
+                        a = fmaf(w[h], sH[(cur * kAnnMaxHidden + h) * BLK], a);
+                    lkc = mkdf(fmaf(av.y_std[j], a, av.y_mean[j]) * 1.4426950408889634f, 0.0f);
+                    for (int t = 0; t < R->nr; ++t) {
+                        const int k = R->spr[t];
+                        const float nu = (float)R->nur[t];
+                        er = fmaf(nu, sE[k * BLK], er);
+                        fr = fmaf(nu, sF[k * BLK], fr);
+                    }
+                } else {
+                    // log2 K_c = sum_k nu_kj (-g_k/RT) + dnu log2(p_ref/RT) (Eqs. 8-9)
+                    lkc = df_mul_f(lgpRT, (float)R->dnu);
+                    for (int t = 0; t < R->nr; ++t) {
+                        const int k = R->spr[t];
+                        const float nu = (float)R->nur[t];
+                        lkc = df_add(lkc, df_mul_f(mkdf(sGh[k * BLK], sGl[k * BLK]), nu));
+                        er = fmaf(nu, sE[k * BLK], er);
+                        fr = fmaf(nu, sF[k * BLK], fr);
+                    }
+                    for (int t = 0; t < R->nf; ++t) {
+                        const int k = R->spf[t];
+                        lkc = df_add(lkc, df_mul_f(mkdf(sGh[k * BLK], sGl[k * BLK]),
+                                                   -(float)R->nuf[t]));
+                    }
                 }
                 df xr = df_add(df_add(tf, df_mul_f(lgct, (float)R->ordr)), fac);
                 xr = df_add(xr, mkdf(-lkc.h, -lkc.l));
@@ -377,13 +419,57 @@ chem_status launch_source_fp32(const chem_mech *m, int64_t n, const float *T, co
 {
     static std::atomic<uint32_t> m64{0}, m32{0};
     const size_t per = 6 * sizeof(float) * (size_t)m->ns;
+    KcAnnView none;
+    memset(&none, 0, sizeof none);
     if (per * 64 <= 200 * 1024)
-        return launch_rows<64>(k_source_f32<64>, m64, per * 64, n, s, "fp32", m->v32, n, T, P,
-                               Y, ldY, om, ldO);
+        return launch_rows<64>(k_source_f32<64, false>, m64, per * 64, n, s, "fp32", m->v32,
+                               none, n, T, P, Y, ldY, om, ldO);
     if (per * 32 <= kMaxDynSmem)
-        return launch_rows<32>(k_source_f32<32>, m32, per * 32, n, s, "fp32", m->v32, n, T, P,
-                               Y, ldY, om, ldO);
+        return launch_rows<32>(k_source_f32<32, false>, m32, per * 32, n, s, "fp32", m->v32,
+                               none, n, T, P, Y, ldY, om, ldO);
     return set_error(CHEM_EUNSUPPORTED, "fp32: %d species exceed the SIMT kernel", m->ns);
+}
+
+chem_status launch_source_fp32_ann(const chem_mech *m, const KcAnnView &av, int64_t n,
+                                   const float *T, const float *P, const float *Y, int64_t ldY,
+                                   float *om, int64_t ldO, cudaStream_t s)
+{
+    static std::atomic<uint32_t> m64{0}, m32{0};
+    const size_t per = sizeof(float) * (6 * (size_t)m->ns + 2 * kAnnMaxHidden);
+    if (per * 64 <= 200 * 1024)
+        return launch_rows<64>(k_source_f32<64, true>, m64, per * 64, n, s, "fp32 ann", m->v32,
+                               av, n, T, P, Y, ldY, om, ldO);
+    if (per * 32 <= kMaxDynSmem)
+        return launch_rows<32>(k_source_f32<32, true>, m32, per * 32, n, s, "fp32 ann", m->v32,
+                               av, n, T, P, Y, ldY, om, ldO);
+    return set_error(CHEM_EUNSUPPORTED, "fp32 ann: %d species exceed the SIMT kernel", m->ns);
+}
+
+// Exact ln K_c of every reaction (Eqs. 8-11, the FP64 folded Gibbs layer), one thread per
+// cell: lnkc[i * ldK + j].
+__global__ void k_log_kc(MechViewF64 mv, int64_t n, const double *__restrict__ T,
+                         double *__restrict__ lnkc, int64_t ldK)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double Ti = T[i], lnT = log(Ti), invT = 1.0 / Ti, tau = Ti * 1e-3;
+    const int rg = Ti >= mv.t_mid ? 1 : 0;
+    for (int j = 0; j < mv.nr; ++j) {
+        const double *kc = mv.rxn[j].kc[rg];
+        lnkc[i * ldK + j] = kc[0] + kc[1] * lnT +
+                            tau * (kc[2] + tau * (kc[3] + tau * (kc[4] + tau * kc[5]))) +
+                            kc[6] * invT;
+    }
+}
+
+chem_status launch_log_kc(const chem_mech *m, int64_t n, const double *T, double *lnkc,
+                          int64_t ldK, cudaStream_t s)
+{
+    k_log_kc<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(m->v64, n, T, lnkc, ldK);
+    g_launches.fetch_add(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(CHEM_ECUDA, "log_kc launch: %s", cudaGetErrorString(e));
+    return CHEM_OK;
 }
 
 }  // namespace chem

@@ -372,3 +372,27 @@ def test_jacobian_detailed_balance_structure():
     assert np.abs(J - expect).max() <= 1e-10 * np.abs(expect).max()
     E = m.elem_comp.astype(float)
     assert np.abs(E.T @ J).max() <= 1e-10 * np.abs(J).max()
+
+
+def test_given_lnkc_reproduces_the_thermo_path(mech53):
+    # with ln K_c supplied equal to the thermo value (Eq. 8), the result is unchanged; with
+    # ln K_c shifted by d for one reaction, only its reverse rate scales by e^-d
+    om = O.OracleMechanism(mech53)
+    T, P, Y = synth.make_states(mech53, 6, seed=21)
+    ref = O.source_term(om, T, P, Y)
+    K = np.zeros((6, mech53.n_reactions))
+    for i in range(6):
+        C = O.concentrations(om, T[i], P[i], Y[i])
+        K[i] = O.cell_detail(om, T[i], C)["lnKc"]
+    w = O.source_term_kc(om, T, P, Y, K)
+    assert np.max(np.abs(w - ref) / np.abs(ref).max(1, keepdims=True)) < 1e-14
+    j = int(np.nonzero(mech53.reversible)[0][0])
+    K2 = K.copy()
+    K2[:, j] += 0.5
+    w2 = O.source_term_kc(om, T, P, Y, K2)
+    nu = (mech53.nu_r[j] - mech53.nu_f[j]).astype(float)
+    for i in range(6):
+        C = O.concentrations(om, T[i], P[i], Y[i])
+        d = O.cell_detail(om, T[i], C)
+        expect = ref[i] + nu * d["qr"][j] * (1.0 - np.exp(-0.5))
+        assert np.max(np.abs(w2[i] - expect)) <= 1e-12 * np.abs(ref[i]).max()
