@@ -143,7 +143,7 @@ chem_status chem_source_term(const chem_mech *mech, int64_t n_cells, const void 
 
 /*
  * Device workspace (bytes) that chem_source_term_host needs for a given chunk size:
- * two stages of T, P, Y and omega rows of chunk_cells cells each.
+ * three stages of T, P, Y and omega rows of chunk_cells cells each.
  */
 size_t chem_source_term_host_workspace(const chem_mech *mech, int64_t chunk_cells,
                                        int64_t ldY, chem_precision precision);
@@ -151,7 +151,7 @@ size_t chem_source_term_host_workspace(const chem_mech *mech, int64_t chunk_cell
 /*
  * chem_source_term with HOST arrays (same layouts and element types): the cells are
  * processed in chunks of chunk_cells; each chunk is copied host->device, evaluated and
- * copied back, with the copies of one chunk overlapping the kernel of the next on two
+ * copied back, with the copies of one chunk overlapping the kernel of the next on three
  * library-owned streams.  Host arrays should be page-locked for the copies to overlap.
  * `workspace` is caller-owned device memory of at least
  * chem_source_term_host_workspace(mech, chunk_cells, ldY, precision) bytes, 256-byte

@@ -52,16 +52,18 @@ extern "C" chem_status chem_source_term(const chem_mech *m, int64_t n, const voi
 }
 
 // ---------------------------------------------------------------------------------------
-// host-buffer entry: chunked H2D -> kernel -> D2H on two library-owned streams
+// host-buffer entry: chunked H2D -> kernel -> D2H on three library-owned streams
 // ---------------------------------------------------------------------------------------
 
 #include <mutex>
 
 namespace {
 
+constexpr int kPipe = 3;         // stages: H2D of chunk i + 2, kernel of i + 1, D2H of i
+
 struct HostPipe {
-    cudaStream_t st[2] = {nullptr, nullptr};
-    cudaEvent_t ev_in = nullptr, ev_out[2] = {nullptr, nullptr};
+    cudaStream_t st[kPipe] = {};
+    cudaEvent_t ev_in = nullptr, ev_out[kPipe] = {};
     bool ok = false;
 };
 
@@ -74,7 +76,7 @@ chem_status get_pipe(int dev, HostPipe **out)
     std::lock_guard<std::mutex> g(g_pipe_mu);
     HostPipe &p = g_pipes[dev];
     if (!p.ok) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < kPipe; ++i) {
             if (cudaStreamCreateWithFlags(&p.st[i], cudaStreamNonBlocking) != cudaSuccess ||
                 cudaEventCreateWithFlags(&p.ev_out[i], cudaEventDisableTiming) != cudaSuccess)
                 return set_error(CHEM_ECUDA, "stream/event creation failed");
@@ -101,7 +103,7 @@ extern "C" size_t chem_source_term_host_workspace(const chem_mech *m, int64_t ch
 {
     if (!m || chunk < 1 || ldY < 1) return 0;
     size_t elt = prec == CHEM_FP64 ? 8 : 4;
-    return 2 * stage_bytes(m->ns, chunk, ldY, elt);
+    return kPipe * stage_bytes(m->ns, chunk, ldY, elt);
 }
 
 extern "C" chem_status chem_source_term_host(const chem_mech *m, int64_t n, const void *T,
@@ -135,12 +137,13 @@ extern "C" chem_status chem_source_term_host(const chem_mech *m, int64_t n, cons
     const int ns = m->ns;
     cudaStream_t user = (cudaStream_t)stream;
     cudaError_t e = cudaEventRecord(pp->ev_in, user);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(pp->st[i], pp->ev_in, 0);
+    for (int i = 0; i < kPipe && e == cudaSuccess; ++i)
+        e = cudaStreamWaitEvent(pp->st[i], pp->ev_in, 0);
     const size_t sb = stage_bytes(ns, chunk, ldY, elt);
     int64_t c = 0;
     for (int64_t lo = 0; lo < n && e == cudaSuccess; lo += chunk, ++c) {
         const int64_t cnt = (n - lo < chunk) ? n - lo : chunk;
-        const int b = (int)(c & 1);
+        const int b = (int)(c % kPipe);
         cudaStream_t s = pp->st[b];
         unsigned char *base = (unsigned char *)ws + sb * b;
         void *dT = base;
@@ -168,11 +171,17 @@ extern "C" chem_status chem_source_term_host(const chem_mech *m, int64_t n, cons
                                     (const float *)dY, ldY, (float *)dO, ns, s);
         }
         if (st != CHEM_OK) break;
-        e = cudaMemcpy2DAsync((char *)om + lo * ldO * elt, ldO * elt, dO, ns * elt, ns * elt, cnt,
-                              cudaMemcpyDeviceToHost, s);
+        // contiguous rows (ldO == n_species): one linear copy; a pitched copy of narrow rows
+        // moves far fewer bytes per second
+        if (ldO == ns)
+            e = cudaMemcpyAsync((char *)om + lo * ldO * elt, dO, cnt * ns * elt,
+                                cudaMemcpyDeviceToHost, s);
+        else
+            e = cudaMemcpy2DAsync((char *)om + lo * ldO * elt, ldO * elt, dO, ns * elt, ns * elt,
+                                  cnt, cudaMemcpyDeviceToHost, s);
     }
     // the caller's stream waits for both pipeline streams, even after an error
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kPipe; ++i) {
         cudaEventRecord(pp->ev_out[i], pp->st[i]);
         cudaStreamWaitEvent(user, pp->ev_out[i], 0);
     }
