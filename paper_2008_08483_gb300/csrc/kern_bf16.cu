@@ -55,8 +55,8 @@ constexpr int kTbList = 8;             // third-body efficiency entries per reac
 // per-reaction coefficients, copied to shared memory with the stoichiometric tables
 struct alignas(16) CoefS {
     float4 kf;         // Arrhenius layer (Eq. 6): log2 k_inf = x + y log2 T + z / T;
-                       // w = reaction kind (int bits)
-    int4 meta;         // third-body list begin, end; falloff record; unused
+                       // w = 1 for a reversible reaction, 0 otherwise (Sec. 2.4)
+    int4 meta;         // third-body list begin, end; falloff record; reaction kind
 };
 // per species: G_k = g_k/(RT) log2 e - log2(p_ref/(RT)) on [1, log2 T, tau, tau^2, tau^3,
 // tau^4, 1/T] (tau = T/1000), one set per temperature range (Eq. 10 with the standard
@@ -182,13 +182,13 @@ __device__ __forceinline__ void tb_factor4(const SmemTabs &tb, const int (&slot)
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const CoefS &C = tb.coef[slot[u]];
-        if (__float_as_int(C.kf.w) < 2) continue;    // third-body entry: out[u] = M / c_tot
+        if (C.meta.w < 2) continue;                  // third-body entry: out[u] = M / c_tot
         const FallBF &F = tb.fall[C.meta.z];
         const float lkf = fmaf(C.kf.z, c.invT, fmaf(C.kf.y, c.lg2T, C.kf.x));
         const float lk0 = fmaf(F.k0.z, c.invT, fmaf(F.k0.y, c.lg2T, F.k0.x));
         const float lpr = lk0 - lkf + c.lgct + tc::lg2(s[u]);      // log2 Pr
         float fac = -tc::lg2(1.0f + tc::ex2(-lpr));               // log2(Pr / (1 + Pr))
-        if (__float_as_int(C.kf.w) == 3) {
+        if (C.meta.w == 3) {
             const float Tn = c.tau * 1000.0f;
             float fc = F.troe.x * tc::ex2(-Tn * F.troe.z) + F.troe.y * tc::ex2(-Tn * F.troe.w);
             if (F.t2.x > 0.0f) fc += tc::ex2(-F.t2.x * c.invT);
@@ -205,13 +205,13 @@ __device__ __forceinline__ void tb_factor4(const SmemTabs &tb, const int (&slot)
 
 // q_net of one reaction for one cell before any third-body / falloff factor (Eqs. 3-7),
 // log2 domain: the contraction already holds sum nu' log2 C and sum nu'' log2 C - log2 K_c.
-__device__ __forceinline__ float rate_plain(const CoefS *C, float sf, float sr, bool rev,
-                                            const CellF &c)
+// Branch-free: kf.w zeroes the reverse rate of an irreversible reaction, and an empty slot's
+// log2 k_f of -1e4 with S = 0 gives q = 0.
+__device__ __forceinline__ float rate_plain(const CoefS *C, float sf, float sr, const CellF &c)
 {
     const float4 kf = C->kf;
     const float lkf = fmaf(kf.z, c.invT, fmaf(kf.y, c.lg2T, kf.x));
-    const float qf = tc::ex2(sf + lkf);
-    return rev ? qf - tc::ex2(sr + lkf) : qf;
+    return fmaf(-kf.w, tc::ex2(sr + lkf), tc::ex2(sf + lkf));
 }
 
 // two values -> three packed BF16x2 words (hi, mid, lo terms; value a in the low halves)
@@ -417,6 +417,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         const int ns = p.ns;
         int it = 0, u = 0;
+        if (g == 0) {
+            // multiplier columns start at 1 (the slots without a factor keep it)
+            uint32_t one[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) one[e] = 0x3f800000u;
+            for (int c0 = 0; c0 + 16 <= CL::kMaxFactors; c0 += 16)
+                tc::tmem_st16(tmem + lane_off + CL::FC + c0, one);
+            tc::tmem_wait_st();
+        }
         bool ok = wait_bar(BAR(BAR_BTAB), 0, ctl, p.status, 3);   // coefficients in smem
         CellF cf;
         // ---- prologue of tile t: features, X and split log2 X (Eq. 4 input layer); ends
@@ -552,7 +561,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 for (int e = 0; e < 4; ++e) sl[e] = tabs.fslot[g + 4 * min(gi + e, n_g - 1)];
                 bool fall = false;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) fall |= __float_as_int(tabs.coef[sl[e]].kf.w) >= 2;
+                for (int e = 0; e < 4; ++e) fall |= tabs.coef[sl[e]].meta.w >= 2;
                 float v[4];
                 tb_factor4(tabs, sl, fall, cf, Xs, row, v);
 #pragma unroll
@@ -586,8 +595,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 // consecutive columns, behind one completion wait
                 const int mq = c * NQ + g;
                 const uint32_t hm = tabs.hmask[mq];
-                const int fb = hm ? tabs.fbase[mq] : 0;
-                const int lb = min(fb, CL::kMaxFactors - 8);
+                const int lb = hm ? tabs.fbase[mq] : 0;
                 tc::tmem_ld16_nw(d1, sf);
                 tc::tmem_ld16_nw(d1 + RC, sr);
                 if (hm) {
@@ -601,24 +609,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(BAR(BAR_D1EMPTY));
                 const int j0 = c * RC + g * RH;
-                const uint32_t lm = tabs.lmask[mq], rm = tabs.rmask[mq];
                 float q[RH];
 #pragma unroll
                 for (int r = 0; r < RH; ++r)
-                    q[r] = ((lm >> r) & 1u) ? rate_plain(tabs.coef + j0 + r, __uint_as_float(sf[r]),
-                                                        __uint_as_float(sr[r]), (rm >> r) & 1u, cf)
-                                            : 0.0f;
+                    q[r] = rate_plain(tabs.coef + j0 + r, __uint_as_float(sf[r]),
+                                      __uint_as_float(sr[r]), cf);
                 if (hm) {
+                    // the quarter's third-body / falloff reactions sit in its first 8 slots;
+                    // their multipliers are 8 consecutive columns (1 for the other slots)
 #pragma unroll
-                    for (int r = 0; r < RH; ++r) {
-                        if ((hm >> r) & 1u) {
-                            const int pos = __popc(hm & ((1u << r) - 1u)) + fb - lb;
-                            uint32_t w = fv[0];
-#pragma unroll
-                            for (int e = 1; e < 8; ++e) w = pos == e ? fv[e] : w;
-                            q[r] *= __uint_as_float(w);
-                        }
-                    }
+                    for (int r = 0; r < 8; ++r) q[r] *= __uint_as_float(fv[r]);
                 }
                 uint32_t hw[RH / 2], lw[RH / 2];
 #pragma unroll
@@ -773,11 +773,6 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
     auto b2_at = [&](int c, int nrow, int r) -> uint16_t & {
         return b2[(size_t)c * nsp * RC + ((nrow / 8) * (RC / 8) + r / 8) * 64 + (nrow % 8) * 8 + r % 8];
     };
-    auto fbits = [](int v) {
-        float f;
-        memcpy(&f, &v, sizeof f);
-        return f;
-    };
     for (int jj = 0; jj < nrp; ++jj) {
         CoefS &C = cf[jj];
         memset(&C, 0, sizeof C);
@@ -807,9 +802,9 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
         b1_at(c, r, ns + 1) = bf16_of_int(ordf);
         b1_at(c, RC + r, ns + 1) = bf16_of_int(ordr);
         C.kf = make_float4((float)(ar[0] * kLog2e), (float)ar[1], (float)(-ar[2] * kLog2e),
-                           fbits(kind));
+                           d->reversible[j] ? 1.0f : 0.0f);
+        C.meta.w = kind;
         if (kind >= 1) {
-            if (!hmask[mslot]) hmask[(size_t)nch * 3 * NQ + mslot] = (uint32_t)fslot.size();
             hmask[mslot] |= 1u << (r % RH);
             fslot.push_back((uint32_t)jj);
             C.meta.x = (int)tbsp.size();
@@ -865,21 +860,33 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
     }
     {
         const int max_fac = nsp == 32 ? Cols<32>::kMaxFactors : Cols<64>::kMaxFactors;
-        if ((int)fslot.size() > max_fac)
-            return set_error(CHEM_EUNSUPPORTED,
-                             "split-BF16 path holds at most %d third-body/falloff reactions", max_fac);
         for (size_t h2 = 0; h2 < (size_t)nch * NQ; ++h2)
             if (__builtin_popcount(hmask[h2]) > 8)
                 return set_error(CHEM_EUNSUPPORTED, "more than 8 third-body reactions in a chunk quarter");
-        // evaluation order: third-body multipliers first, then falloff (their columns stay
-        // in slot order, so each half chunk reads consecutive columns)
+        // each quarter holding third-body / falloff reactions (in its first 8 slots) owns 8
+        // consecutive multiplier columns; the unused ones stay 1
+        std::vector<int> qrank((size_t)nch * NQ, -1);
+        int nq_special = 0;
+        for (size_t h2 = 0; h2 < (size_t)nch * NQ; ++h2)
+            if (hmask[h2]) {
+                qrank[h2] = nq_special++;
+                hmask[(size_t)nch * 3 * NQ + h2] = (uint32_t)(8 * qrank[h2]);
+            }
+        if (nq_special * 8 > max_fac)
+            return set_error(CHEM_EUNSUPPORTED,
+                             "split-BF16 path holds at most %d third-body/falloff reactions", max_fac);
+        auto col_of = [&](uint32_t slot) { return (uint32_t)(8 * qrank[slot / RH] + slot % RH); };
+        for (uint32_t sl : fslot)
+            if (sl % RH >= 8)
+                return set_error(CHEM_EUNSUPPORTED, "split-BF16 path: multiplier slot layout");
+        // evaluation order: third-body multipliers first, then falloff
         std::vector<uint32_t> ord_slot, ord_col;
         for (int pass = 0; pass < 2; ++pass)
             for (size_t f = 0; f < fslot.size(); ++f) {
                 const int kd = d->kind[order[fslot[f]]];
                 if ((pass == 0) == (kd == CHEM_RXN_THIRD_BODY)) {
                     ord_slot.push_back(fslot[f]);
-                    ord_col.push_back((uint32_t)f);
+                    ord_col.push_back(col_of(fslot[f]));
                 }
             }
         hmask.insert(hmask.end(), ord_slot.begin(), ord_slot.end());
