@@ -582,8 +582,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 fready = true;
                 return w;
             };
-            // two groups while contraction 1 of the first chunks runs
-            for (int pre = 0; pre < 2 && gi < n_g; ++pre) mult_group();
             // ---- every chunk, this warpgroup's quarter of its reactions
             for (int c = 0; c < p.nch; ++c, ++u) {
                 if (!fready && c >= p.fac_chunk0 && !(ok = mult_finish())) break;
@@ -608,6 +606,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 tc::fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(BAR(BAR_D1EMPTY));
+                // one group of multipliers while contraction 1 of the next chunk runs
+                if (!fready && gi < n_g) mult_group();
                 const int j0 = c * RC + g * RH;
                 float q[RH];
 #pragma unroll
@@ -638,7 +638,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 tc::fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(BAR(BAR_A2FULL));
-                if (!fready && gi < n_g) mult_group();   // while the tensor pipe works
             }
             if (!ok) break;
             if (!fready && !(ok = mult_finish())) break;
