@@ -10,10 +10,15 @@
 //       column NSP_extra = log2 c_tot carries the reaction orders (and the third-body
 //       c_tot factor), so S = sum_k nu_k log2 C_k (+ log2 c_tot for third-body).
 //       B = the small-integer stoichiometric matrices, exact in BF16, in shared memory.
-//   epilogue (FP32, one thread per cell): log2 k_f (Eq. 6), log2 k_r = log2 k_f -
-//       log2 K_c from the Gibbs layer folded through nu in FP64 at load (Eqs. 9-11),
-//       third-body / falloff factors (Sec. 2.4), q = 2^(S + log2 k), q_net = q_f - q_r
-//       (Eq. 3), split into two BF16 terms written to tensor memory.
+//       When nine padding columns are free (NSP >= ns + 11), they carry the Arrhenius layer
+//       (Eq. 6) as well: features [1, log2 T, 1/T] (three BF16 terms each) against the
+//       coefficients [log2 A, b, -E/R log2 e] (three BF16 rows each), so that S' = log2 q_f and
+//       S'' = log2 q_r directly; an irreversible reaction's reverse column and an empty slot
+//       carry a bias of -1e4 (2^S = 0).
+//   epilogue (FP32, one thread per cell): without the folded Arrhenius layer, log2 k_f
+//       (Eq. 6) added to both halves; third-body / falloff factors (Sec. 2.4),
+//       q = 2^S' - 2^S'', q_net = q_f - q_r (Eq. 3), split into two BF16 terms written to
+//       tensor memory.
 //   contraction 2 (Eq. 2):  omega += q_net . nu^T          (M=128, N=NSP, K=RC)
 // omega accumulates in tensor memory across the chunks and is written once per tile.
 // Contraction 1 of chunk c + 1 runs while the epilogue works on chunk c (it starts as soon
@@ -51,6 +56,7 @@ constexpr uint32_t kTmemCols = 512;
 constexpr float kLog2Floor = -1000.0f; // log2 X of an absent species: 2^x underflows to 0
 constexpr float kDead = -1.0e4f;       // log2 of a rate constant that is zero
 constexpr int kTbList = 8;             // third-body efficiency entries per reaction (padded)
+constexpr int kFoldRows = 9;           // K rows of the folded Arrhenius layer: 3 features x 3 terms
 
 // per-reaction coefficients, copied to shared memory with the stoichiometric tables
 struct alignas(16) CoefS {
@@ -72,6 +78,7 @@ struct alignas(16) FallBF {
 
 struct Bf16Tables {
     int nsp, nch, nfall, ntb, nfac, fac_chunk0;
+    bool fold;                                   // Arrhenius layer folded into contraction 1
     size_t b1_bytes, b2_bytes, tab_bytes;        // tab = everything after B1 | B2
     uint32_t o_coef, o_hmask, o_fall, o_tbe, o_tbsp, o_gib;   // offsets from the blob start
     void *d_blob;
@@ -237,7 +244,7 @@ __device__ __forceinline__ void split3(float x, uint16_t &h, uint16_t &m, uint16
     l = (uint16_t)pl;
 }
 
-template <int NSP>
+template <int NSP, bool FOLD>
 __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
 {
     using CL = Cols<NSP>;
@@ -479,6 +486,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                         gk[hlf] = fmaf(pt, cf.tau, fmaf(g1.z, cf.invT, fmaf(g0.y, cf.lg2T, g0.x)));
                     } else if (k == ns) {
                         lx[hlf] = cf.lgct;            // third-body c_tot column
+                    } else if (FOLD && k >= ns + 2 && k < ns + 2 + kFoldRows) {
+                        // Arrhenius features 1, log2 T, 1/T, each against three rows
+                        const int f = (k - ns - 2) / 3;
+                        lx[hlf] = f == 0 ? 1.0f : (f == 1 ? cf.lg2T : cf.invT);
                     }
                 }
                 split3x2(lx[0], lx[1], wh[e], wm[e], wl[e]);
@@ -521,8 +532,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 const int kn = ns + 1;                    // normalisation column
                 if (kn / SQ == g) {
                     // the packed word holding column kn; its other half is column kn - 1
-                    // (= ns, log2 c_tot) or kn + 1 (padding, zero)
-                    const float other = (kn & 1) ? cf.lgct : 0.0f;
+                    // (= ns, log2 c_tot) or kn + 1 (the first Arrhenius feature, 1, or
+                    // padding, zero)
+                    const float other = (kn & 1) ? cf.lgct : (FOLD ? 1.0f : 0.0f);
                     const float vn = sum > 0.0f ? cf.lgct - log2f(sum) : 0.0f;
                     uint16_t ho, mo, lo_, hn, mn, ln;
                     split3(other, ho, mo, lo_);
@@ -610,10 +622,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 if (!fready && gi < n_g) mult_group();
                 const int j0 = c * RC + g * RH;
                 float q[RH];
+                if constexpr (FOLD) {
 #pragma unroll
-                for (int r = 0; r < RH; ++r)
-                    q[r] = rate_plain(tabs.coef + j0 + r, __uint_as_float(sf[r]),
-                                      __uint_as_float(sr[r]), cf);
+                    for (int r = 0; r < RH; ++r)
+                        q[r] = tc::ex2(__uint_as_float(sf[r])) - tc::ex2(__uint_as_float(sr[r]));
+                } else {
+#pragma unroll
+                    for (int r = 0; r < RH; ++r)
+                        q[r] = rate_plain(tabs.coef + j0 + r, __uint_as_float(sf[r]),
+                                          __uint_as_float(sr[r]), cf);
+                }
                 if (hm) {
                     // the quarter's third-body / falloff reactions sit in its first 8 slots;
                     // their multipliers are 8 consecutive columns (1 for the other slots)
@@ -720,6 +738,30 @@ static uint16_t bf16_of_int(int v)
     return (uint16_t)(u >> 16);              // exact for |v| <= 256
 }
 
+static uint16_t bf16_rn(float f)
+{
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);   // nearest, ties to even
+}
+
+static double f_of_bf16(uint16_t h)
+{
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+// x = hi + mid + lo, each term the nearest BF16 of the remaining residual
+static void bf16_split3(double x, uint16_t (&t)[3])
+{
+    for (int i = 0; i < 3; ++i) {
+        t[i] = bf16_rn((float)x);
+        x -= f_of_bf16(t[i]);
+    }
+}
+
 chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
 {
     const int ns = d->n_species, nr = d->n_reactions;
@@ -731,6 +773,9 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
     else return set_error(CHEM_EUNSUPPORTED, "split-BF16 path supports up to 62 species");
     const int nch = (nr + RC - 1) / RC;
     const int nrp = nch * RC;
+    // the Arrhenius layer rides in contraction 1 when nine padding rows are free
+    const bool fold = ns + 2 + kFoldRows <= nsp;
+    const int kf0 = ns + 2;
     // Reactions without a third-body or falloff factor fill the first chunks (spread evenly
     // over their slots); those with one go to the last K chunks, round-robin over their
     // chunk quarters (at most 8 per quarter, one 8-column multiplier load), with the rest
@@ -777,8 +822,13 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
         memset(&C, 0, sizeof C);
         const int c = jj / RC, r = jj % RC;
         const size_t mslot = (size_t)c * NQ + r / RH;
-        if (order[jj] < 0) {                    // padding slot: skipped by the epilogue
+        if (order[jj] < 0) {                    // padding slot: q = 0
             C.kf = make_float4(kDead, 0, 0, 0);
+            if (fold) {
+                uint16_t t3[3];
+                bf16_split3(kDead, t3);
+                for (int i = 0; i < 3; ++i) b1_at(c, r, kf0 + i) = b1_at(c, RC + r, kf0 + i) = t3[i];
+            }
             continue;
         }
         const int j = order[jj];
@@ -802,6 +852,23 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
         b1_at(c, RC + r, ns + 1) = bf16_of_int(ordr);
         C.kf = make_float4((float)(ar[0] * kLog2e), (float)ar[1], (float)(-ar[2] * kLog2e),
                            d->reversible[j] ? 1.0f : 0.0f);
+        if (fold) {
+            // rows kf0 + 3 f + i: term i of the coefficient of feature f (1, log2 T, 1/T)
+            const double co[3] = {ar[0] * kLog2e, ar[1], -ar[2] * kLog2e};
+            for (int f = 0; f < 3; ++f) {
+                uint16_t t3[3];
+                bf16_split3(co[f], t3);
+                for (int i = 0; i < 3; ++i) {
+                    b1_at(c, r, kf0 + 3 * f + i) = t3[i];
+                    if (d->reversible[j]) b1_at(c, RC + r, kf0 + 3 * f + i) = t3[i];
+                }
+            }
+            if (!d->reversible[j]) {
+                uint16_t t3[3];
+                bf16_split3(kDead, t3);
+                for (int i = 0; i < 3; ++i) b1_at(c, RC + r, kf0 + i) = t3[i];
+            }
+        }
         C.meta.w = kind;
         if (kind >= 1) {
             hmask[mslot] |= 1u << (r % RH);
@@ -938,6 +1005,7 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
     }
     unsigned char *base = (unsigned char *)t->d_blob;
     t->nsp = nsp;
+    t->fold = fold;
     t->nch = nch;
     t->nfall = (int)fl.size();
     t->ntb = (int)tbsp.size();
@@ -986,13 +1054,13 @@ static int sm_count(int dev)
     return cache[dev];
 }
 
-template <int NSP>
+template <int NSP, bool FOLD>
 static chem_status launch_nsp(const Bf16Params &prm, size_t smem, cudaStream_t s, int dev)
 {
     static std::atomic<uint32_t> done{0};
     const uint32_t bit = 1u << (dev & 31);
     if (!(done.load() & bit)) {
-        cudaError_t e = cudaFuncSetAttribute(k_source_bf16<NSP>,
+        cudaError_t e = cudaFuncSetAttribute(k_source_bf16<NSP, FOLD>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              227 * 1024);
         if (e != cudaSuccess)
@@ -1000,7 +1068,7 @@ static chem_status launch_nsp(const Bf16Params &prm, size_t smem, cudaStream_t s
         done.fetch_or(bit);
     }
     const int grid = std::min(prm.ntiles, sm_count(dev));
-    k_source_bf16<NSP><<<grid, kThreads, smem, s>>>(prm);
+    k_source_bf16<NSP, FOLD><<<grid, kThreads, smem, s>>>(prm);
     g_launches.fetch_add(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(CHEM_ECUDA, "split-BF16 launch: %s", cudaGetErrorString(e));
@@ -1069,10 +1137,11 @@ chem_status launch_source_bf16(const chem_mech *m, int64_t n, const float *T, co
     if (smem > 227 * 1024)
         return set_error(CHEM_EUNSUPPORTED, "split-BF16 tables need %zu bytes of shared memory",
                          smem);
-    switch (t->nsp) {
-    case 32: return launch_nsp<32>(prm, smem, s, m->device);
-    default: return launch_nsp<64>(prm, smem, s, m->device);
-    }
+    if (t->fold)
+        return t->nsp == 32 ? launch_nsp<32, true>(prm, smem, s, m->device)
+                            : launch_nsp<64, true>(prm, smem, s, m->device);
+    return t->nsp == 32 ? launch_nsp<32, false>(prm, smem, s, m->device)
+                        : launch_nsp<64, false>(prm, smem, s, m->device);
 }
 
 }  // namespace chem

@@ -172,3 +172,35 @@ def test_full_size_sampled(dev, prec):
     idx = np.concatenate([idx, [0, n - 1]])
     ref = O.source_term(om, T[idx], P[idx], Y[idx])
     assert cell_err(w[idx], ref).max() <= TOL[prec]
+
+
+def with_inert_species(m, extra):
+    """The mechanism with `extra` species appended that take part in no reaction (copies of
+    the first species' thermodynamics and composition, default third-body efficiency)."""
+    import dataclasses
+    ns, nr = m.n_species, m.n_reactions
+    pad = lambda a, v: np.concatenate([a, np.full((nr, extra), v, a.dtype)], axis=1)
+    return dataclasses.replace(
+        m, name=f"{m.name}+{extra}inert", species=m.species + [f"INERT{i}" for i in range(extra)],
+        elem_comp=np.concatenate([m.elem_comp, np.repeat(m.elem_comp[:1], extra, 0)]),
+        mol_weight=np.concatenate([m.mol_weight, np.repeat(m.mol_weight[:1], extra)]),
+        nu_f=pad(m.nu_f, 0), nu_r=pad(m.nu_r, 0), eff=pad(m.eff, 1.0),
+        nasa7=np.concatenate([m.nasa7, np.repeat(m.nasa7[:1], extra, 0)]))
+
+
+@pytest.mark.parametrize("size,extra", [("h2air_9_21", 14), ("gri_53_325", 5)])
+def test_bf16_without_folded_arrhenius_rows(dev, size, extra):
+    """Species counts that leave fewer than nine padding columns (23 of 32, 58 of 64): the
+    split-BF16 kernel adds log2 k_f in its epilogue instead of in contraction 1."""
+    base, _, _ = loaded(size)
+    m = with_inert_species(base, extra)
+    h, om = chem.Mechanism(m), O.OracleMechanism(m)
+    T, P, Yb = states(base, size, 3 * 128 + 19, seed=21)
+    rng = np.random.default_rng(5)
+    Y = np.concatenate([Yb, rng.uniform(0.0, 0.02, (len(T), extra))], axis=1)
+    Y /= Y.sum(axis=1, keepdims=True)
+    T, P, Y = (as_prec(x, chem.SPLIT_BF16) for x in (T, P, Y))
+    ref = O.source_term(om, T, P, Y)
+    w, _ = run(h, T, P, Y, chem.SPLIT_BF16, dev)
+    assert np.all(w[:, base.n_species:] == 0.0)
+    assert cell_err(w, ref).max() <= TOL[chem.SPLIT_BF16]
