@@ -20,6 +20,10 @@
 //       q = 2^S' - 2^S'', q_net = q_f - q_r (Eq. 3), split into two BF16 terms written to
 //       tensor memory.
 //   contraction 2 (Eq. 2):  omega += q_net . nu^T          (M=128, N=NSP, K=RC)
+//   contraction 0 (Sec. 2.4), once per tile before chunk 0: the third-body sums
+//       sum_k (eff_jk - 1) z_k of the reactions that need them (M=128, N=64, K=NSP), A = z as
+//       two BF16 terms in contraction 2's operand columns (free until chunk 0's q_net), B =
+//       eff - 1 as two BF16 terms (hi.hi + hi.lo + lo.hi), into the multiplier columns.
 // omega accumulates in tensor memory across the chunks and is written once per tile.
 // Contraction 1 of chunk c + 1 runs while the epilogue works on chunk c (it starts as soon
 // as chunk c's S has been read out), contraction 2 of chunk c as soon as its q_net is in.
@@ -30,9 +34,10 @@
 // Warp roles (576 threads): warp 0 bulk-copies the T, P, Y tile into shared memory;
 // warp 1 owns tensor memory and issues every MMA from one thread; warps 2-17 form four
 // epilogue warpgroups, warpgroup g taking reactions 16 g .. 16 g + 15 of every chunk (warp
-// w reaches tensor-memory lanes 32 (w % 4) .. 32 (w % 4) + 31).  Per-reaction coefficients
-// live in shared memory; third-body and falloff factors are evaluated four at a time in the
-// epilogue's waits of the first chunks (the reactions that need them sit in the last ones).
+// w reaches tensor-memory lanes 32 (w % 4) .. 32 (w % 4) + 31).  Reactions with a third-body
+// or falloff factor sit in the first 8 slots of the last chunks' quarters (falloff ones in
+// slots 0..3); the epilogue turns contraction 0's sums into M / c_tot and, for the falloff
+// slots, into Pr / (1 + Pr) F where the quarter's rates are formed.
 // Every mbarrier wait is bounded: on timeout the kernel records an error code in the
 // mechanism's device status word and all roles wind down.
 #include <math.h>
@@ -55,14 +60,15 @@ constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);
 constexpr uint32_t kTmemCols = 512;
 constexpr float kLog2Floor = -1000.0f; // log2 X of an absent species: 2^x underflows to 0
 constexpr float kDead = -1.0e4f;       // log2 of a rate constant that is zero
-constexpr int kTbList = 8;             // third-body efficiency entries per reaction (padded)
 constexpr int kFoldRows = 9;           // K rows of the folded Arrhenius layer: 3 features x 3 terms
 
-// per-reaction coefficients, copied to shared memory with the stoichiometric tables
+constexpr int kFacCols = 64;           // multiplier columns: 8 per quarter holding such reactions
+
+// per-reaction coefficients, copied to shared memory with the stoichiometric tables (read by
+// the epilogue when the Arrhenius layer is not folded into contraction 1)
 struct alignas(16) CoefS {
     float4 kf;         // Arrhenius layer (Eq. 6): log2 k_inf = x + y log2 T + z / T;
                        // w = 1 for a reversible reaction, 0 otherwise (Sec. 2.4)
-    int4 meta;         // third-body list begin, end; falloff record; reaction kind
 };
 // per species: G_k = g_k/(RT) log2 e - log2(p_ref/(RT)) on [1, log2 T, tau, tau^2, tau^3,
 // tau^4, 1/T] (tau = T/1000), one set per temperature range (Eq. 10 with the standard
@@ -70,17 +76,20 @@ struct alignas(16) CoefS {
 struct alignas(16) GibbsS {
     float c[2][8];
 };
-struct alignas(16) FallBF {
+// slot 0..3 of a chunk quarter holding third-body / falloff reactions: the falloff layer
+// (Sec. 2.4), or neutral values with kf.w = 0 (the multiplier is then M / c_tot)
+struct alignas(16) FallQ {
+    float4 kf;         // log2 k_inf = x + y log2 T + z / T; w = 1 for a falloff reaction
     float4 k0;         // log2 k0 = x + y log2 T + z / T
-    float4 troe;       // 1 - alpha, alpha, log2(e)/T***, log2(e)/T*
-    float4 t2;         // x = log2(e) T** (<= 0: absent)
+    float4 troe;       // 1 - alpha, alpha, log2(e)/T***, log2(e)/T* (Lindemann: 1, 0, 0, 0)
+    float4 t2;         // x = log2(e) T** (absent: 1e30, the term underflows to zero)
 };
 
 struct Bf16Tables {
-    int nsp, nch, nfall, ntb, nfac, fac_chunk0;
+    int nsp, nch;
     bool fold;                                   // Arrhenius layer folded into contraction 1
-    size_t b1_bytes, b2_bytes, tab_bytes;        // tab = everything after B1 | B2
-    uint32_t o_coef, o_hmask, o_fall, o_tbe, o_tbsp, o_gib;   // offsets from the blob start
+    size_t b1_bytes, blob_bytes;
+    uint32_t o_b2, o_e, o_coef, o_hmask, o_fq, o_gib;   // offsets from the blob start
     void *d_blob;
     const uint16_t *btab;     // one contiguous block copied to shared memory
     const float *invW;
@@ -91,8 +100,7 @@ struct Bf16Params {
     const float *T, *P, *Y;
     float *om;
     int64_t n, ldY, ldO;
-    int ns, nch, ntiles, nfac;
-    int fac_chunk0;            // first chunk holding a third-body / falloff reaction
+    int ns, nch, ntiles;
     int stage_y;               // T, P, Y tiles staged in shared memory (the Y buffer then also
                                // stages omega on its way out)
     int bulk_out;              // omega rows contiguous (ldO == ns) and 16-byte aligned
@@ -102,14 +110,14 @@ struct Bf16Params {
     float t_mid, lg2R;
     int *status;
     // shared-memory layout (byte offsets from the 1024-aligned base); the copied block
-    // holds B1, B2, coefficients, third-body masks, falloff records and third-body lists
-    uint32_t o_b2, o_coef, o_hmask, o_fall, o_tbe, o_tbsp, o_gib, o_y, o_t, o_p, o_xw, o_iw, o_psum,
-        o_bar;
+    // holds B1, B2, the efficiency table, coefficients, quarter masks, falloff records and
+    // the Gibbs layer
+    uint32_t o_b2, o_e, o_coef, o_hmask, o_fq, o_gib, o_y, o_t, o_p, o_iw, o_psum, o_bar;
 };
 
 enum {
     BAR_BTAB, BAR_YFULL, BAR_YEMPTY, BAR_A1FULL, BAR_D1FULL, BAR_D1EMPTY, BAR_A2FULL, BAR_A2EMPTY,
-    BAR_D2FULL, BAR_D2EMPTY, BAR_XREADY, BAR_A1FREE, BAR_DRAIN, BAR_FREADY, BAR_WREADY, BAR_COUNT
+    BAR_D2FULL, BAR_D2EMPTY, BAR_XREADY, BAR_A1FREE, BAR_DRAIN, BAR_WREADY, BAR_COUNT
 };
 
 struct SmemCtl {
@@ -142,9 +150,8 @@ struct Cols {                                     // tensor-memory column map
     static constexpr uint32_t D1 = AG + ((3 * NSP / 2 + 31) / 32) * 32;   // 2 RC: S', S''
     static constexpr uint32_t A2 = D1 + 2 * RC;   // 2 splits x RC/2
     static constexpr uint32_t D2 = A2 + RC;       // NSP columns
-    static constexpr uint32_t FC = D2 + NSP;      // third-body / falloff multipliers
-    static constexpr int kMaxFactors = (int)(kTmemCols - FC);
-    static_assert(kMaxFactors >= 16, "tensor memory over budget");
+    static constexpr uint32_t FC = D2 + NSP;      // third-body sums (contraction 0)
+    static_assert(FC + kFacCols <= kTmemCols, "tensor memory over budget");
 };
 
 // Per-cell features kept in registers by every epilogue thread.
@@ -156,57 +163,37 @@ struct CellF {
 // Shared-memory view of the per-reaction tables.
 struct SmemTabs {
     const CoefS *coef;
-    const uint32_t *hmask;     // per half chunk: bit r set if reaction r needs a factor
-    const uint32_t *lmask;     // per half chunk: bit r set if slot r holds a reaction
-    const uint32_t *rmask;     // per half chunk: bit r set if reaction r is reversible
-    const int *fbase;          // per half chunk: multiplier column of its first flagged slot
-    const int *fslot;          // per multiplier, kind-sorted: reaction slot
-    const int *fcol;           // per multiplier, kind-sorted: tensor-memory column
-    const FallBF *fall;
-    const float *tbe;          // efficiency - 1 of the listed third-body species
-    const uint16_t *tbsp;
+    const uint32_t *hmask;     // per chunk quarter: nonzero if it holds third-body / falloff
+                               // reactions (in its first 8 slots)
+    const int *fbase;          // per chunk quarter: its first multiplier column (8 each)
+    const FallQ *fq;           // per such quarter, slots 0..3
 };
 
-// Multipliers of q_net for four third-body (M / c_tot) or falloff (Pr / (1 + Pr) F)
-// reactions, Sec. 2.4, evaluated together so their dependency chains interleave.  The
-// c_tot part of a third-body factor is already in the contraction.  Third-body lists hold
-// kTbList (species, efficiency - 1) entries, padded with zero efficiencies.
-__device__ __forceinline__ void tb_factor4(const SmemTabs &tb, const int (&slot)[4], bool falloff,
-                                           const CellF &c, const float *Xs, int row, float (&out)[4])
+// Multipliers of q_net for slots 0..3 of a quarter holding third-body / falloff reactions
+// (Sec. 2.4), from s = M / c_tot: Pr / (1 + Pr) F for a falloff reaction (F = 1 for
+// Lindemann, the Troe form otherwise), s itself for the others.  Branch-free over the four
+// slots so that their dependency chains interleave.
+__device__ __forceinline__ void falloff4(const FallQ *F, const float (&s)[8], const CellF &c,
+                                         float (&out)[4])
 {
-    float s[4];
+    const float Tn = c.tau * 1000.0f;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        const int t0 = tb.coef[slot[u]].meta.x;
-        float sz = 0.0f;                          // M / c_tot = 1 + sum_k (eff_k - 1) X_k,
-#pragma unroll
-        for (int t = 0; t < kTbList; ++t)         // X_k = z_k / sum_k z_k
-            sz = fmaf(tb.tbe[t0 + t], Xs[(int)tb.tbsp[t0 + t] * 128 + row], sz);
-        s[u] = fmaf(sz, c.inv_sum, 1.0f);
-        out[u] = s[u];
-    }
-    if (!falloff) return;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const CoefS &C = tb.coef[slot[u]];
-        if (C.meta.w < 2) continue;                  // third-body entry: out[u] = M / c_tot
-        const FallBF &F = tb.fall[C.meta.z];
-        const float lkf = fmaf(C.kf.z, c.invT, fmaf(C.kf.y, c.lg2T, C.kf.x));
-        const float lk0 = fmaf(F.k0.z, c.invT, fmaf(F.k0.y, c.lg2T, F.k0.x));
-        const float lpr = lk0 - lkf + c.lgct + tc::lg2(s[u]);      // log2 Pr
+        const float4 kf = F[u].kf, k0 = F[u].k0, tr = F[u].troe;
+        const float t2 = F[u].t2.x;
+        const float lkf = fmaf(kf.z, c.invT, fmaf(kf.y, c.lg2T, kf.x));
+        const float lk0 = fmaf(k0.z, c.invT, fmaf(k0.y, c.lg2T, k0.x));
+        const float lpr = lk0 - lkf + c.lgct + tc::lg2(fmaxf(s[u], 1e-30f));   // log2 Pr
         float fac = -tc::lg2(1.0f + tc::ex2(-lpr));               // log2(Pr / (1 + Pr))
-        if (C.meta.w == 3) {
-            const float Tn = c.tau * 1000.0f;
-            float fc = F.troe.x * tc::ex2(-Tn * F.troe.z) + F.troe.y * tc::ex2(-Tn * F.troe.w);
-            if (F.t2.x > 0.0f) fc += tc::ex2(-F.t2.x * c.invT);
-            const float lfc = tc::lg2(fc);        // log2 F_cent
-            const float l10 = lfc * 0.30102999566398120f;
-            const float cc = -0.4f - 0.67f * l10, nn = 0.75f - 1.27f * l10;
-            const float x = lpr * 0.30102999566398120f + cc;
-            const float f1 = __fdividef(x, nn - 0.14f * x);
-            fac += __fdividef(lfc, 1.0f + f1 * f1);   // log2 F (Troe)
-        }
-        out[u] = tc::ex2(fac);
+        const float fc = tr.x * tc::ex2(-Tn * tr.z) + tr.y * tc::ex2(-Tn * tr.w) +
+                         tc::ex2(-t2 * c.invT);
+        const float lfc = tc::lg2(fc);                             // log2 F_cent
+        const float l10 = lfc * 0.30102999566398120f;
+        const float cc = -0.4f - 0.67f * l10, nn = 0.75f - 1.27f * l10;
+        const float x = lpr * 0.30102999566398120f + cc;
+        const float f1 = __fdividef(x, nn - 0.14f * x);
+        fac += __fdividef(lfc, 1.0f + f1 * f1);                   // log2 F (Troe)
+        out[u] = kf.w != 0.0f ? tc::ex2(fac) : s[u];
     }
 }
 
@@ -229,6 +216,13 @@ __device__ __forceinline__ void split3x2(float a, float b, uint32_t &h, uint32_t
     m = tc::pack_bf16x2(a1, b1);
     const float a2 = a1 - __uint_as_float(m << 16), b2 = b1 - __uint_as_float(m & 0xFFFF0000u);
     l = tc::pack_bf16x2(a2, b2);
+}
+
+// two values -> two packed BF16x2 words (hi, lo terms; value a in the low halves)
+__device__ __forceinline__ void split2x2(float a, float b, uint32_t &h, uint32_t &l)
+{
+    h = tc::pack_bf16x2(a, b);
+    l = tc::pack_bf16x2(a - __uint_as_float(h << 16), b - __uint_as_float(h & 0xFFFF0000u));
 }
 
 __device__ __forceinline__ void split3(float x, uint16_t &h, uint16_t &m, uint16_t &l)
@@ -257,19 +251,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
     SmemTabs tabs;
     tabs.coef = (const CoefS *)(sm + p.o_coef);
     tabs.hmask = (const uint32_t *)(sm + p.o_hmask);
-    tabs.lmask = tabs.hmask + NQ * p.nch;
-    tabs.rmask = tabs.hmask + 2 * NQ * p.nch;
-    tabs.fbase = (const int *)(tabs.hmask + 3 * NQ * p.nch);
-    tabs.fslot = tabs.fbase + NQ * p.nch;
-    tabs.fcol = tabs.fslot + p.nfac;
+    tabs.fbase = (const int *)(tabs.hmask + NQ * p.nch);
+    tabs.fq = (const FallQ *)(sm + p.o_fq);
     const GibbsS *gib = (const GibbsS *)(sm + p.o_gib);
-    tabs.fall = (const FallBF *)(sm + p.o_fall);
-    tabs.tbe = (const float *)(sm + p.o_tbe);
-    tabs.tbsp = (const uint16_t *)(sm + p.o_tbsp);
     float *Ys = (float *)(sm + p.o_y);
     float *Ts = (float *)(sm + p.o_t);
     float *Ps = (float *)(sm + p.o_p);
-    float *Xs = (float *)(sm + p.o_xw);           // X [species][128] of the current tile
     float *Ws = (float *)(sm + p.o_y);            // omega [128][ns], in the Y buffer between
                                                   // the next tile's prologue and its reload
     float *iW = (float *)(sm + p.o_iw);
@@ -280,7 +267,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        const uint32_t cnt[BAR_COUNT] = {1, 1, 16, 16, 1, 16, 16, 1, 1, 16, 16, 1, 1, 16, 16};
+        const uint32_t cnt[BAR_COUNT] = {1, 1, 16, 16, 1, 16, 16, 1, 1, 16, 16, 1, 1, 16};
         for (int i = 0; i < BAR_COUNT; ++i) tc::mbar_init(BAR(i), cnt[i]);
         tc::mbar_fence_init();
         ctl->abort = 0;
@@ -330,7 +317,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
         if (lane == 0) {
             constexpr uint32_t id1 = tc::idesc_bf16_f32(128, 2 * RC);
             constexpr uint32_t id2 = tc::idesc_bf16_f32(128, NSP);
-            const uint32_t b1 = sbase, b2 = sbase + p.o_b2;
+            constexpr uint32_t id0 = tc::idesc_bf16_f32(128, kFacCols);
+            const uint32_t b1 = sbase, b2 = sbase + p.o_b2, be = sbase + p.o_e;
             uint32_t u_d1 = 0, u_a2 = 0;        // contractions 1 and 2 issued so far
             bool ok = wait_bar(BAR(BAR_BTAB), 0, ctl, p.status, 2);
             constexpr uint32_t id1g = tc::idesc_bf16_f32(128, RC, true);
@@ -373,6 +361,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
             for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x, ++it) {
                 if (!(ok = wait_bar(BAR(BAR_A1FULL), it & 1, ctl, p.status, 2))) break;
                 tc::fence_after();
+                // contraction 0: z (hi, lo) . (eff - 1) (hi, lo) as hi.hi + hi.lo + lo.hi into
+                // the multiplier columns; complete before chunk 0's D1FULL (issue order)
+#pragma unroll
+                for (int s = 0; s < 3; ++s)
+#pragma unroll
+                    for (int kk = 0; kk < NSP / 16; ++kk)
+                        tc::mma_ts(tmem + CL::FC, tmem + CL::A2 + (s == 2 ? NSP / 2 : 0) + kk * 8,
+                                   tc::sdesc_noswz(be + (s == 1 ? kFacCols * NSP * 2 : 0) + kk * 256,
+                                                   128, (NSP / 8) * 128),
+                                   id0, (s | kk) != 0);
                 // Contraction 1 of the next chunk as soon as the epilogue has read the current
                 // one; contraction 2 strictly in chunk order (the omega accumulation order,
                 // hence the rounding, is fixed), first when both are ready.
@@ -424,15 +422,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         const int ns = p.ns;
         int it = 0, u = 0;
-        if (g == 0) {
-            // multiplier columns start at 1 (the slots without a factor keep it)
-            uint32_t one[16];
-#pragma unroll
-            for (int e = 0; e < 16; ++e) one[e] = 0x3f800000u;
-            for (int c0 = 0; c0 + 16 <= CL::kMaxFactors; c0 += 16)
-                tc::tmem_st16(tmem + lane_off + CL::FC + c0, one);
-            tc::tmem_wait_st();
-        }
         bool ok = wait_bar(BAR(BAR_BTAB), 0, ctl, p.status, 3);   // coefficients in smem
         CellF cf;
         // ---- prologue of tile t: features, X and split log2 X (Eq. 4 input layer); ends
@@ -466,18 +455,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
             float psum = 0.0f;
             uint32_t wh[SQ / 2], wm[SQ / 2], wl[SQ / 2];   // log2 z, three BF16 terms
             uint32_t gh[SQ / 2], gm[SQ / 2], gl[SQ / 2];   // G, three BF16 terms
+            uint32_t zh[SQ / 2], zl[SQ / 2];               // z, two BF16 terms (contraction 0)
 #pragma unroll
             for (int e = 0; e < SQ / 2; ++e) {
-                float lx[2], gk[2];
+                float lx[2], gk[2], zz[2];
 #pragma unroll
                 for (int hlf = 0; hlf < 2; ++hlf) {
                     const int k = g * SQ + 2 * e + hlf;
                     lx[hlf] = 0.0f;
                     gk[hlf] = 0.0f;
+                    zz[hlf] = 0.0f;
                     if (k < ns) {
                         const float z = yrow ? fmaxf(yrow[k], 0.0f) * iW[k] : 0.0f;
                         psum += z;
-                        Xs[k * 128 + row] = z;
+                        zz[hlf] = z;
                         lx[hlf] = fmaxf(tc::lg2(z), kLog2Floor);
                         // Gibbs layer (Eq. 10) for this species at this cell's temperature
                         const float4 g0 = *(const float4 *)&gib[k].c[cf.rg][0];
@@ -494,10 +485,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 }
                 split3x2(lx[0], lx[1], wh[e], wm[e], wl[e]);
                 split3x2(gk[0], gk[1], gh[e], gm[e], gl[e]);
+                split2x2(zz[0], zz[1], zh[e], zl[e]);
             }
             // the previous tile's contractions 1 have read their operands
             if (itp > 0 && !wait_bar(BAR(BAR_A1FREE), (itp - 1) & 1, ctl, p.status, 3)) return false;
+            // ... and the previous tile's last contraction 2 has read its q_net operand, whose
+            // columns take z now
+            if (!wait_bar(BAR(BAR_A2EMPTY), (u & 1) ^ 1, ctl, p.status, 3)) return false;
             tc::fence_after();
+            const uint32_t az = tmem + lane_off + CL::A2 + g * (SQ / 2);
             const uint32_t a1 = tmem + lane_off + CL::A1 + g * (SQ / 2);
             const uint32_t ag = tmem + lane_off + CL::AG + g * (SQ / 2);
             if constexpr (SQ / 2 == 8) {
@@ -507,6 +503,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 tc::tmem_st8(ag + 0 * (NSP / 2), gh);
                 tc::tmem_st8(ag + 1 * (NSP / 2), gm);
                 tc::tmem_st8(ag + 2 * (NSP / 2), gl);
+                tc::tmem_st8(az, zh);
+                tc::tmem_st8(az + NSP / 2, zl);
             } else {
                 static_assert(SQ / 2 == 4, "warpgroup species quarter of 8 or 16 columns");
                 tc::tmem_st4(a1 + 0 * (NSP / 2), wh);
@@ -515,6 +513,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 tc::tmem_st4(ag + 0 * (NSP / 2), gh);
                 tc::tmem_st4(ag + 1 * (NSP / 2), gm);
                 tc::tmem_st4(ag + 2 * (NSP / 2), gl);
+                tc::tmem_st4(az, zh);
+                tc::tmem_st4(az + NSP / 2, zl);
             }
             tc::tmem_wait_st();
             Psum[g * 128 + row] = psum;
@@ -559,44 +559,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
         for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x, ++it) {
             const int64_t i0 = (int64_t)t * 128;
             const int64_t ci = i0 + row;
-            // Third-body / falloff multipliers of this tile (Sec. 2.4): warpgroup g evaluates
-            // entries g, g + 4, g + 8, ... of the kind-sorted list, four at a time, in the
-            // waits between its first chunks (the reactions that need them sit in the last
-            // chunks).  All of them are in tensor memory (FREADY: every epilogue warp has
-            // stored its share) before the first chunk that reads one.
-            const int n_g = (p.nfac - g + 3) / 4;
-            int gi = 0;
-            bool fready = false;
-            auto mult_group = [&]() {
-                int sl[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) sl[e] = tabs.fslot[g + 4 * min(gi + e, n_g - 1)];
-                bool fall = false;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) fall |= tabs.coef[sl[e]].meta.w >= 2;
-                float v[4];
-                tb_factor4(tabs, sl, fall, cf, Xs, row, v);
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (gi + e < n_g)
-                        tc::tmem_st1(tmem + lane_off + CL::FC + tabs.fcol[g + 4 * (gi + e)],
-                                     __float_as_uint(v[e]));
-                gi += 4;
-            };
-            auto mult_finish = [&]() -> bool {
-                while (gi < n_g) mult_group();
-                tc::tmem_wait_st();
-                tc::fence_before();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(BAR(BAR_FREADY));
-                const bool w = wait_bar(BAR(BAR_FREADY), it & 1, ctl, p.status, 3);
-                tc::fence_after();
-                fready = true;
-                return w;
-            };
             // ---- every chunk, this warpgroup's quarter of its reactions
             for (int c = 0; c < p.nch; ++c, ++u) {
-                if (!fready && c >= p.fac_chunk0 && !(ok = mult_finish())) break;
                 if (!(ok = wait_bar(BAR(BAR_D1FULL), u & 1, ctl, p.status, 3))) break;
                 tc::fence_after();
                 uint32_t sf[RH], sr[RH], fv[8];
@@ -618,8 +582,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 tc::fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(BAR(BAR_D1EMPTY));
-                // one group of multipliers while contraction 1 of the next chunk runs
-                if (!fready && gi < n_g) mult_group();
                 const int j0 = c * RC + g * RH;
                 float q[RH];
                 if constexpr (FOLD) {
@@ -633,10 +595,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                                           __uint_as_float(sr[r]), cf);
                 }
                 if (hm) {
-                    // the quarter's third-body / falloff reactions sit in its first 8 slots;
-                    // their multipliers are 8 consecutive columns (1 for the other slots)
+                    // the quarter's third-body / falloff reactions sit in its first 8 slots
+                    // (falloff in 0..3); their columns hold sum_k (eff_k - 1) z_k (0 for the
+                    // other slots), so M / c_tot = 1 + that / sum_k z_k
+                    float s8[8], fo[4];
 #pragma unroll
-                    for (int r = 0; r < 8; ++r) q[r] *= __uint_as_float(fv[r]);
+                    for (int r = 0; r < 8; ++r)
+                        s8[r] = fmaf(__uint_as_float(fv[r]), cf.inv_sum, 1.0f);
+                    falloff4(tabs.fq + 4 * (lb / 8), s8, cf, fo);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) q[r] *= fo[r];
+#pragma unroll
+                    for (int r = 4; r < 8; ++r) q[r] *= s8[r];
                 }
                 uint32_t hw[RH / 2], lw[RH / 2];
 #pragma unroll
@@ -658,7 +628,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 if (lane == 0) tc::mbar_arrive(BAR(BAR_A2FULL));
             }
             if (!ok) break;
-            if (!fready && !(ok = mult_finish())) break;
             // ---- the next tile's prologue first: it needs none of this tile's tensor memory
             // (every contraction 1 of this tile has completed), so its contraction 1 can
             // start while this tile's omega is read out
@@ -777,16 +746,20 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
     const bool fold = ns + 2 + kFoldRows <= nsp;
     const int kf0 = ns + 2;
     // Reactions without a third-body or falloff factor fill the first chunks (spread evenly
-    // over their slots); those with one go to the last K chunks, round-robin over their
-    // chunk quarters (at most 8 per quarter, one 8-column multiplier load), with the rest
-    // of the plain reactions.  The epilogue evaluates the multipliers while the tensor pipe
-    // works on the first chunks, before they are needed.
-    std::vector<int> plain, special;
-    for (int j = 0; j < nr; ++j) (d->kind[j] == 0 ? plain : special).push_back(j);
-    const int S = (int)special.size();
-    int K = S ? (S + NQ * 8 - 1) / (NQ * 8) : 0;
-    if (K > nch) return set_error(CHEM_EUNSUPPORTED, "split-BF16 path: too many third-body reactions");
-    while (K < nch && (nch - K) * RC + K * RC - S < (int)plain.size()) ++K;   // room for all
+    // over their slots); those with one go to the first 8 slots of the last K chunks'
+    // quarters (falloff ones round-robin into slots 0..3, third-body ones into the least
+    // filled quarter), with the rest of the plain reactions.  Each such quarter owns 8
+    // multiplier columns: contraction 0 fills them with its third-body sums.
+    std::vector<int> plain, fall, tbr;
+    for (int j = 0; j < nr; ++j)
+        (d->kind[j] == 0 ? plain : d->kind[j] == CHEM_RXN_THIRD_BODY ? tbr : fall).push_back(j);
+    const int S = (int)(fall.size() + tbr.size());
+    int K = 0;
+    if (S) K = std::max((S + NQ * 8 - 1) / (NQ * 8), ((int)fall.size() + NQ * 4 - 1) / (NQ * 4));
+    if (K > nch || NQ * K * 8 > kFacCols)
+        return set_error(CHEM_EUNSUPPORTED,
+                         "split-BF16 path: %d third-body / falloff reactions (%d falloff) exceed "
+                         "its %d multiplier columns", S, (int)fall.size(), kFacCols);
     std::vector<int> order(nrp, -1);        // slot -> reaction (-1: padding)
     size_t pi = 0;
     {
@@ -794,34 +767,54 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
         const int n_head = std::min((int)plain.size(), head_slots);
         for (int i = 0; i < n_head; ++i)
             order[(size_t)((int64_t)i * head_slots / n_head)] = plain[pi++];
-        for (int i = 0; i < S; ++i) {                    // round-robin over the tail quarters
-            const int hc = (nch - K) * NQ + i % (NQ * K), pos = i / (NQ * K);
-            order[(size_t)hc * RH + pos] = special[i];
+        const int nqt = NQ * K;
+        std::vector<int> fill(nqt, 0);
+        for (size_t i = 0; i < fall.size(); ++i) {
+            const int qq = (int)(i % nqt);
+            order[(size_t)((nch - K) * NQ + qq) * RH + fill[qq]++] = fall[i];
+        }
+        for (size_t i = 0; i < tbr.size(); ++i) {
+            int qq = 0;
+            for (int x = 1; x < nqt; ++x)
+                if (fill[x] < fill[qq]) qq = x;
+            order[(size_t)((nch - K) * NQ + qq) * RH + fill[qq]++] = tbr[i];
         }
         for (int jj = head_slots; jj < nrp && pi < plain.size(); ++jj)
             if (order[jj] < 0) order[jj] = plain[pi++];
     }
     if (pi != plain.size()) return set_error(CHEM_EUNSUPPORTED, "split-BF16 path: slot layout");
     std::vector<uint16_t> b1((size_t)nch * 2 * RC * nsp, 0), b2((size_t)nch * nsp * RC, 0);
+    const size_t e_term = (size_t)kFacCols * nsp;
+    std::vector<uint16_t> eb(2 * e_term, 0);          // eff - 1: [term][column][species]
     std::vector<CoefS> cf(nrp);
-    // per half chunk: third-body, live and reversible masks, then the multiplier base index;
-    // then the slot of every multiplier
-    std::vector<uint32_t> hmask((size_t)nch * 4 * NQ, 0);
-    std::vector<uint32_t> fslot;
-    std::vector<FallBF> fl;
-    std::vector<uint16_t> tbsp;
-    std::vector<float> tbe;
+    // per chunk quarter: holds third-body / falloff reactions; its first multiplier column
+    std::vector<uint32_t> hmask((size_t)nch * 2 * NQ, 0);
+    std::vector<int> qrank((size_t)nch * NQ, -1);
+    int nq_special = 0;
+    for (int jj = 0; jj < nrp; ++jj)
+        if (order[jj] >= 0 && d->kind[order[jj]] != 0 && qrank[jj / RH] < 0) {
+            qrank[jj / RH] = nq_special++;
+            hmask[jj / RH] = 1;
+            hmask[(size_t)nch * NQ + jj / RH] = (uint32_t)(8 * qrank[jj / RH]);
+        }
+    FallQ neutral;
+    memset(&neutral, 0, sizeof neutral);
+    neutral.troe = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+    neutral.t2 = make_float4(1e30f, 0.0f, 0.0f, 0.0f);
+    std::vector<FallQ> fq((size_t)std::max(nq_special, 1) * 4, neutral);
     auto b1_at = [&](int c, int r, int k) -> uint16_t & {
         return b1[(size_t)c * 2 * RC * nsp + ((r / 8) * (nsp / 8) + k / 8) * 64 + (r % 8) * 8 + k % 8];
     };
     auto b2_at = [&](int c, int nrow, int r) -> uint16_t & {
         return b2[(size_t)c * nsp * RC + ((nrow / 8) * (RC / 8) + r / 8) * 64 + (nrow % 8) * 8 + r % 8];
     };
+    auto e_at = [&](int term, int n, int k) -> uint16_t & {
+        return eb[term * e_term + ((n / 8) * (nsp / 8) + k / 8) * 64 + (n % 8) * 8 + k % 8];
+    };
     for (int jj = 0; jj < nrp; ++jj) {
         CoefS &C = cf[jj];
         memset(&C, 0, sizeof C);
         const int c = jj / RC, r = jj % RC;
-        const size_t mslot = (size_t)c * NQ + r / RH;
         if (order[jj] < 0) {                    // padding slot: q = 0
             C.kf = make_float4(kDead, 0, 0, 0);
             if (fold) {
@@ -832,8 +825,6 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
             continue;
         }
         const int j = order[jj];
-        hmask[(size_t)nch * NQ + mslot] |= 1u << (r % RH);
-        if (d->reversible[j]) hmask[(size_t)nch * 2 * NQ + mslot] |= 1u << (r % RH);
         const int kind = d->kind[j];
         const double *ar = d->arrh + (size_t)j * 3;
         int ordf = 0, ordr = 0;
@@ -869,43 +860,28 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
                 for (int i = 0; i < 3; ++i) b1_at(c, RC + r, kf0 + i) = t3[i];
             }
         }
-        C.meta.w = kind;
-        if (kind >= 1) {
-            hmask[mslot] |= 1u << (r % RH);
-            fslot.push_back((uint32_t)jj);
-            C.meta.x = (int)tbsp.size();
-            int cnt = 0;
-            for (int k = 0; k < ns; ++k) {
-                const double e = d->eff ? d->eff[(size_t)j * ns + k] : 1.0;
-                if (e != 1.0) {
-                    tbsp.push_back((uint16_t)k);
-                    tbe.push_back((float)(e - 1.0));
-                    ++cnt;
-                }
-            }
-            if (cnt > kTbList)
-                return set_error(CHEM_EUNSUPPORTED,
-                                 "split-BF16 path: reaction %d lists more than %d efficiencies", j,
-                                 kTbList);
-            for (; cnt < kTbList; ++cnt) {
-                tbsp.push_back(0);
-                tbe.push_back(0.0f);
-            }
-            C.meta.y = (int)tbsp.size();
+        if (kind == 0) continue;
+        // third-body sum column (contraction 0): eff - 1 in two BF16 terms
+        const int pos = jj % RH, col = 8 * qrank[jj / RH] + pos;
+        if (pos >= 8 || (kind != CHEM_RXN_THIRD_BODY && pos >= 4))
+            return set_error(CHEM_EUNSUPPORTED, "split-BF16 path: multiplier slot layout");
+        for (int k = 0; k < ns; ++k) {
+            const double e = (d->eff ? d->eff[(size_t)j * ns + k] : 1.0) - 1.0;
+            const uint16_t hi = bf16_rn((float)e);
+            e_at(0, col, k) = hi;
+            e_at(1, col, k) = bf16_rn((float)(e - f_of_bf16(hi)));
         }
-        if (kind >= 2) {
-            FallBF F;
-            memset(&F, 0, sizeof F);
+        if (kind != CHEM_RXN_THIRD_BODY) {
+            FallQ &F = fq[(size_t)4 * qrank[jj / RH] + pos];
             const double *al = d->arrh_low + (size_t)j * 3;
+            F.kf = make_float4(C.kf.x, C.kf.y, C.kf.z, 1.0f);
             F.k0 = make_float4((float)(al[0] * kLog2e), (float)al[1], (float)(-al[2] * kLog2e), 0.f);
-            if (kind == 3) {
+            if (kind == CHEM_RXN_TROE) {
                 const double *tp = d->troe + (size_t)j * 4;
                 F.troe = make_float4((float)(1.0 - tp[0]), (float)tp[0], (float)(kLog2e / tp[1]),
                                      (float)(kLog2e / tp[2]));
-                F.t2 = make_float4(tp[3] > 0.0 ? (float)(tp[3] * kLog2e) : -1.0f, 0, 0, 0);
+                if (tp[3] > 0.0) F.t2 = make_float4((float)(tp[3] * kLog2e), 0, 0, 0);
             }
-            C.meta.z = (int)fl.size();
-            fl.push_back(F);
         }
     }
     // Gibbs layer per species (log2 units, the standard concentration folded into the bias):
@@ -924,70 +900,26 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
             for (int q = 0; q < 7; ++q) gb[k].c[rg][q] = (float)cc[q];
         }
     }
-    {
-        const int max_fac = nsp == 32 ? Cols<32>::kMaxFactors : Cols<64>::kMaxFactors;
-        for (size_t h2 = 0; h2 < (size_t)nch * NQ; ++h2)
-            if (__builtin_popcount(hmask[h2]) > 8)
-                return set_error(CHEM_EUNSUPPORTED, "more than 8 third-body reactions in a chunk quarter");
-        // each quarter holding third-body / falloff reactions (in its first 8 slots) owns 8
-        // consecutive multiplier columns; the unused ones stay 1
-        std::vector<int> qrank((size_t)nch * NQ, -1);
-        int nq_special = 0;
-        for (size_t h2 = 0; h2 < (size_t)nch * NQ; ++h2)
-            if (hmask[h2]) {
-                qrank[h2] = nq_special++;
-                hmask[(size_t)nch * 3 * NQ + h2] = (uint32_t)(8 * qrank[h2]);
-            }
-        if (nq_special * 8 > max_fac)
-            return set_error(CHEM_EUNSUPPORTED,
-                             "split-BF16 path holds at most %d third-body/falloff reactions", max_fac);
-        auto col_of = [&](uint32_t slot) { return (uint32_t)(8 * qrank[slot / RH] + slot % RH); };
-        for (uint32_t sl : fslot)
-            if (sl % RH >= 8)
-                return set_error(CHEM_EUNSUPPORTED, "split-BF16 path: multiplier slot layout");
-        // evaluation order: third-body multipliers first, then falloff
-        std::vector<uint32_t> ord_slot, ord_col;
-        for (int pass = 0; pass < 2; ++pass)
-            for (size_t f = 0; f < fslot.size(); ++f) {
-                const int kd = d->kind[order[fslot[f]]];
-                if ((pass == 0) == (kd == CHEM_RXN_THIRD_BODY)) {
-                    ord_slot.push_back(fslot[f]);
-                    ord_col.push_back(col_of(fslot[f]));
-                }
-            }
-        hmask.insert(hmask.end(), ord_slot.begin(), ord_slot.end());
-        hmask.insert(hmask.end(), ord_col.begin(), ord_col.end());
-    }
-    const int nfac = (int)fslot.size();
-    const int fac_chunk0 = nfac ? (int)(fslot[0] / RC) : nch;
-    if (tbsp.empty()) {
-        tbsp.push_back(0);
-        tbe.push_back(0.f);
-    }
-    if (fl.empty()) fl.push_back(FallBF{});
     std::vector<float> invW(ns);
     for (int k = 0; k < ns; ++k) invW[k] = (float)(1.0 / d->mol_weight[k]);
 
-    // B1 | B2 | coefficients | masks | falloff | third-body lists: contiguous, copied to
+    // B1 | B2 | E | coefficients | quarter masks | falloff | Gibbs: contiguous, copied to
     // shared memory by one bulk transfer (16-byte granules)
     auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
     auto a256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t ob1 = 0, ob2 = b1.size() * 2, ocf = ob2 + b2.size() * 2;
+    const size_t ob1 = 0, ob2 = b1.size() * 2, oe = ob2 + b2.size() * 2, ocf = oe + eb.size() * 2;
     const size_t ohm = a16(ocf + cf.size() * sizeof(CoefS));
-    const size_t ofl = a16(ohm + hmask.size() * 4);
-    const size_t otbe = a16(ofl + fl.size() * sizeof(FallBF));
-    const size_t otbs = a16(otbe + tbe.size() * 4);
-    const size_t ogb = a16(otbs + tbsp.size() * 2);
+    const size_t ofq = a16(ohm + hmask.size() * 4);
+    const size_t ogb = a16(ofq + fq.size() * sizeof(FallQ));
     const size_t blob = a16(ogb + gb.size() * sizeof(GibbsS));
     const size_t oiw = a256(blob), ost = a256(oiw + invW.size() * 4), total = a256(ost + 16);
     std::vector<unsigned char> h(total, 0);
     memcpy(h.data() + ob1, b1.data(), b1.size() * 2);
     memcpy(h.data() + ob2, b2.data(), b2.size() * 2);
+    memcpy(h.data() + oe, eb.data(), eb.size() * 2);
     memcpy(h.data() + ocf, cf.data(), cf.size() * sizeof(CoefS));
     memcpy(h.data() + ohm, hmask.data(), hmask.size() * 4);
-    memcpy(h.data() + ofl, fl.data(), fl.size() * sizeof(FallBF));
-    memcpy(h.data() + otbe, tbe.data(), tbe.size() * 4);
-    memcpy(h.data() + otbs, tbsp.data(), tbsp.size() * 2);
+    memcpy(h.data() + ofq, fq.data(), fq.size() * sizeof(FallQ));
     memcpy(h.data() + ogb, gb.data(), gb.size() * sizeof(GibbsS));
     memcpy(h.data() + oiw, invW.data(), invW.size() * 4);
     Bf16Tables *t = new (std::nothrow) Bf16Tables();
@@ -1007,19 +939,14 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
     t->nsp = nsp;
     t->fold = fold;
     t->nch = nch;
-    t->nfall = (int)fl.size();
-    t->ntb = (int)tbsp.size();
     t->b1_bytes = b1.size() * 2;
-    t->b2_bytes = b2.size() * 2;
-    t->tab_bytes = blob - ocf;
+    t->blob_bytes = blob;
+    t->o_b2 = (uint32_t)ob2;
+    t->o_e = (uint32_t)oe;
     t->o_coef = (uint32_t)ocf;
     t->o_hmask = (uint32_t)ohm;
-    t->o_fall = (uint32_t)ofl;
-    t->o_tbe = (uint32_t)otbe;
-    t->o_tbsp = (uint32_t)otbs;
+    t->o_fq = (uint32_t)ofq;
     t->o_gib = (uint32_t)ogb;
-    t->nfac = nfac;
-    t->fac_chunk0 = fac_chunk0;
     t->btab = (const uint16_t *)(base + ob1);
     t->invW = (const float *)(base + oiw);
     t->status = (int *)(base + ost);
@@ -1093,12 +1020,10 @@ chem_status launch_source_bf16(const chem_mech *m, int64_t n, const float *T, co
     prm.ldO = ldO;
     prm.ns = m->ns;
     prm.nch = t->nch;
-    prm.nfac = t->nfac;
     prm.bulk_out = (ldO == m->ns && (uintptr_t)om % 16 == 0) ? 1 : 0;
-    prm.fac_chunk0 = t->fac_chunk0;
     prm.ntiles = (int)((n + 127) / 128);
     prm.btab = t->btab;
-    prm.blob_bytes = (uint32_t)(t->b1_bytes + t->b2_bytes + t->tab_bytes);
+    prm.blob_bytes = (uint32_t)t->blob_bytes;
     prm.invW = t->invW;
     prm.t_mid = (float)m->t_mid;
     prm.lg2R = (float)log2(kR);
@@ -1106,17 +1031,15 @@ chem_status launch_source_bf16(const chem_mech *m, int64_t n, const float *T, co
     if ((int64_t)((n + 127) / 128) > 0x7fffffff) return set_error(CHEM_EINVAL, "n_cells too large");
     // shared memory layout
     auto al = [](size_t x, size_t a) { return (x + a - 1) & ~(a - 1); };
-    prm.o_b2 = (uint32_t)t->b1_bytes;
+    prm.o_b2 = t->o_b2;
+    prm.o_e = t->o_e;
     prm.o_coef = t->o_coef;
     prm.o_hmask = t->o_hmask;
-    prm.o_fall = t->o_fall;
-    prm.o_tbe = t->o_tbe;
-    prm.o_tbsp = t->o_tbsp;
+    prm.o_fq = t->o_fq;
     prm.o_gib = t->o_gib;
     size_t off = al(prm.blob_bytes, 128);
     const size_t ybytes = (size_t)128 * ldY * 4;
-    const size_t xw = (size_t)128 * m->ns * 4;
-    const size_t fixed = 2 * 512 + xw + al(m->ns * 4, 128) + 2048 + BAR_COUNT * 8 + 64 + 1024;
+    const size_t fixed = 2 * 512 + al(m->ns * 4, 128) + 2048 + BAR_COUNT * 8 + 64 + 1024;
     const bool aligned = ((uintptr_t)Y % 16 == 0) && ((uintptr_t)T % 16 == 0) && ((uintptr_t)P % 16 == 0);
     prm.stage_y = aligned && (off + ybytes + fixed <= 227 * 1024) ? 1 : 0;
     prm.o_y = (uint32_t)off;
@@ -1125,8 +1048,6 @@ chem_status launch_source_bf16(const chem_mech *m, int64_t n, const float *T, co
     off += 512;
     prm.o_p = (uint32_t)off;
     off += 512;
-    prm.o_xw = (uint32_t)off;
-    off = al(off + xw, 128);
     prm.o_iw = (uint32_t)off;
     off = al(off + m->ns * 4, 128);
     prm.o_psum = (uint32_t)off;
