@@ -31,8 +31,10 @@
 // Tiles overlap: the next tile's prologue runs as soon as every contraction 1 of the current
 // tile has completed (A1FREE), before the current tile's omega is read out of tensor memory
 // and stored, so that the next tile's contraction 1 starts meanwhile.
-// Warp roles (576 threads): warp 0 bulk-copies the T, P, Y tile into shared memory;
-// warp 1 owns tensor memory and issues every MMA from one thread; warps 2-17 form four
+// Warp roles (608 threads): warp 0 bulk-copies the T, P, Y tile into shared memory;
+// warp 1 owns tensor memory and issues contractions 0 and 1 from one thread, warp 18
+// contraction 2 (an MMA issue blocks while the tensor pipe is busy, so one issuer would sit
+// on contraction 2 of chunk c while chunk c + 1's S has been read out); warps 2-17 form four
 // epilogue warpgroups, warpgroup g taking reactions 16 g .. 16 g + 15 of every chunk (warp
 // w reaches tensor-memory lanes 32 (w % 4) .. 32 (w % 4) + 31).  Reactions with a third-body
 // or falloff factor sit in the first 8 slots of the last chunks' quarters (falloff ones in
@@ -56,7 +58,8 @@ constexpr int RH = RC / 4;             // reactions per warpgroup and chunk
 constexpr int NQ = RC / RH;            // warpgroups (chunk quarters)
 constexpr int kEpiWarp0 = 2;           // first epilogue warp
 constexpr int kEpiWarps = 16;
-constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);
+constexpr int kMma2Warp = kEpiWarp0 + kEpiWarps;   // issues contraction 2
+constexpr int kThreads = 32 * (kMma2Warp + 1);
 constexpr uint32_t kTmemCols = 512;
 constexpr float kLog2Floor = -1000.0f; // log2 X of an absent species: 2^x underflows to 0
 constexpr float kDead = -1.0e4f;       // log2 of a rate constant that is zero
@@ -267,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        const uint32_t cnt[BAR_COUNT] = {1, 1, 16, 16, 1, 16, 16, 1, 1, 16, 16, 1, 1, 16};
+        const uint32_t cnt[BAR_COUNT] = {1, 1, 16, 16, 1, 16, 16, 1, 1, 16, 16, 1, 2, 16};
         for (int i = 0; i < BAR_COUNT; ++i) tc::mbar_init(BAR(i), cnt[i]);
         tc::mbar_fence_init();
         ctl->abort = 0;
@@ -312,8 +315,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
             if (pending) wait_bar(BAR(BAR_YFULL), (it - 1) & 1, ctl, p.status, 1);
             wait_bar(BAR(BAR_BTAB), 0, ctl, p.status, 1);
         }
-    } else if (warp == 1) {
-        // ------------------------------------------------------------- MMA issuer
+    } else if (warp == 1 || warp == kMma2Warp) {
+        // ------------------------------------------------------------- MMA issuers
         if (lane == 0) {
             constexpr uint32_t id1 = tc::idesc_bf16_f32(128, 2 * RC);
             constexpr uint32_t id2 = tc::idesc_bf16_f32(128, NSP);
@@ -358,62 +361,51 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 if (c == p.nch - 1) tc::commit(BAR(BAR_D2FULL));
             };
             int it = 0;
-            for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x, ++it) {
-                if (!(ok = wait_bar(BAR(BAR_A1FULL), it & 1, ctl, p.status, 2))) break;
-                tc::fence_after();
-                // contraction 0: z (hi, lo) . (eff - 1) (hi, lo) as hi.hi + hi.lo + lo.hi into
-                // the multiplier columns; complete before chunk 0's D1FULL (issue order)
+            if (warp == 1) {
+                for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x, ++it) {
+                    if (!(ok = wait_bar(BAR(BAR_A1FULL), it & 1, ctl, p.status, 2))) break;
+                    tc::fence_after();
+                    // contraction 0: z (hi, lo) . (eff - 1) (hi, lo) as hi.hi + hi.lo + lo.hi
+                    // into the multiplier columns; complete before chunk 0's D1FULL (issue
+                    // order of this thread)
 #pragma unroll
-                for (int s = 0; s < 3; ++s)
+                    for (int s = 0; s < 3; ++s)
 #pragma unroll
-                    for (int kk = 0; kk < NSP / 16; ++kk)
-                        tc::mma_ts(tmem + CL::FC, tmem + CL::A2 + (s == 2 ? NSP / 2 : 0) + kk * 8,
-                                   tc::sdesc_noswz(be + (s == 1 ? kFacCols * NSP * 2 : 0) + kk * 256,
-                                                   128, (NSP / 8) * 128),
-                                   id0, (s | kk) != 0);
-                // Contraction 1 of the next chunk as soon as the epilogue has read the current
-                // one; contraction 2 strictly in chunk order (the omega accumulation order,
-                // hence the rounding, is fixed), first when both are ready.
-                int c1 = 0, c2 = 0;
-                bool d2_free = false, a1_freed = false;
-                long long t0 = clock64();
-                while (c2 < p.nch) {
-                    bool prog = false;
-                    if (!d2_free) d2_free = tc::mbar_test_wait(BAR(BAR_D2EMPTY), (it & 1) ^ 1);
-                    if (d2_free && c2 < c1 && tc::mbar_test_wait(BAR(BAR_A2FULL), u_a2 & 1)) {
+                        for (int kk = 0; kk < NSP / 16; ++kk)
+                            tc::mma_ts(tmem + CL::FC,
+                                       tmem + CL::A2 + (s == 2 ? NSP / 2 : 0) + kk * 8,
+                                       tc::sdesc_noswz(be + (s == 1 ? kFacCols * NSP * 2 : 0) +
+                                                           kk * 256,
+                                                       128, (NSP / 8) * 128),
+                                       id0, (s | kk) != 0);
+                    // contraction 1 of each chunk as soon as the previous S has been read out
+                    for (int c = 0; ok && c < p.nch; ++c) {
+                        if (!(ok = wait_bar(BAR(BAR_D1EMPTY), (u_d1 & 1) ^ 1, ctl, p.status, 2)))
+                            break;
                         tc::fence_after();
-                        mma2(c2);
-                        ++c2;
-                        prog = true;
+                        issue_mma1(c);
                     }
-                    if (c1 < p.nch && tc::mbar_test_wait(BAR(BAR_D1EMPTY), (u_d1 & 1) ^ 1)) {
+                    // completes when every contraction 1 of the tile has read its operands
+                    if (ok) tc::commit(BAR(BAR_A1FREE));
+                }
+            } else {
+                // contraction 2 in chunk order (the omega accumulation order, hence the
+                // rounding, is fixed), the first of a tile once omega of the tile before has
+                // been read out
+                for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x, ++it) {
+                    if (!(ok = wait_bar(BAR(BAR_D2EMPTY), (it & 1) ^ 1, ctl, p.status, 2))) break;
+                    for (int c = 0; ok && c < p.nch; ++c) {
+                        if (!(ok = wait_bar(BAR(BAR_A2FULL), u_a2 & 1, ctl, p.status, 2))) break;
                         tc::fence_after();
-                        issue_mma1(c1);
-                        ++c1;
-                        prog = true;
-                    }
-                    if (!a1_freed && c1 >= p.nch) {
-                        // completes when every contraction 1 of the tile has read its operands
-                        tc::commit(BAR(BAR_A1FREE));
-                        a1_freed = true;
-                    }
-                    if (prog) {
-                        t0 = clock64();
-                    } else if (clock64() - t0 < (1ll << 31) && !ctl->abort) {
-                        __nanosleep(32);                // back off: the epilogue warps share this SM
-                    } else if (ctl->abort || clock64() - t0 > (1ll << 31)) {
-                        ctl->abort = 1;
-                        atomicCAS(p.status, 0, 2);
-                        ok = false;
-                        break;
+                        mma2(c);
                     }
                 }
             }
-            // every MMA issued has completed before tensor memory is released
+            // every MMA issued (by both issuers) has completed before tensor memory is released
             tc::commit(BAR(BAR_DRAIN));
             wait_bar(BAR(BAR_DRAIN), 0, ctl, p.status, 2);
         }
-    } else {
+    } else if (warp < kMma2Warp) {
         // ------------------------------------------------------------- epilogue
         const int ew = warp - kEpiWarp0;             // 0..15
         const int g = ew >> 2;                        // warpgroup 0..3: quarter of each chunk
