@@ -126,6 +126,7 @@ enum {
 struct SmemCtl {
     uint32_t tmem_base;
     volatile int abort;
+    volatile int mma1_issued;   // contractions 1 issued so far (an ordering hint only)
 };
 
 // Bounded mbarrier wait: gives up after ~2^31 cycles (about a second), or as soon as
@@ -274,6 +275,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
         for (int i = 0; i < BAR_COUNT; ++i) tc::mbar_init(BAR(i), cnt[i]);
         tc::mbar_fence_init();
         ctl->abort = 0;
+        ctl->mma1_issued = 0;
     }
     for (int k = tid; k < p.ns; k += kThreads) iW[k] = p.invW[k];
     if (warp == 1) {
@@ -384,6 +386,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                             break;
                         tc::fence_after();
                         issue_mma1(c);
+                        ctl->mma1_issued = (int)u_d1;
                     }
                     // completes when every contraction 1 of the tile has read its operands
                     if (ok) tc::commit(BAR(BAR_A1FREE));
@@ -396,6 +399,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                     if (!(ok = wait_bar(BAR(BAR_D2EMPTY), (it & 1) ^ 1, ctl, p.status, 2))) break;
                     for (int c = 0; ok && c < p.nch; ++c) {
                         if (!(ok = wait_bar(BAR(BAR_A2FULL), u_a2 & 1, ctl, p.status, 2))) break;
+                        // Let contraction 1 of the next chunk go first: it gates the epilogue,
+                        // while this one fills the pipe during the next S read-out.  Only the
+                        // order on the tensor pipe depends on this (the two are independent),
+                        // so the wait is short and bounded and then proceeds regardless.
+                        if (c + 1 < p.nch)
+                            for (int spin = 0; spin < 4096 && ctl->mma1_issued < (int)u_a2 + 2; ++spin)
+                                __nanosleep(20);
                         tc::fence_after();
                         mma2(c);
                     }
