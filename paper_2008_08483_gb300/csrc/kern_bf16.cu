@@ -20,7 +20,8 @@
 //       q = 2^S' - 2^S'', q_net = q_f - q_r (Eq. 3), split into two BF16 terms written to
 //       tensor memory.
 //   contraction 2 (Eq. 2):  omega += q_net . nu^T          (M=128, N=NSP, K=RC)
-//   contraction 0 (Sec. 2.4), once per tile before chunk 0: the third-body sums
+//   contraction 0 (Sec. 2.4), once per tile, issued after chunk 0's contraction 1 (before
+//       it when chunk 0 itself reads multipliers): the third-body sums
 //       sum_k (eff_jk - 1) z_k of the reactions that need them (M=128, N=64, K=NSP), A = z as
 //       two BF16 terms in contraction 2's operand columns (free until chunk 0's q_net), B =
 //       eff - 1 as two BF16 terms (hi.hi + hi.lo + lo.hi), into the multiplier columns.
@@ -89,7 +90,7 @@ struct alignas(16) FallQ {
 };
 
 struct Bf16Tables {
-    int nsp, nch;
+    int nsp, nch, fac_chunk0;
     bool fold;                                   // Arrhenius layer folded into contraction 1
     size_t b1_bytes, blob_bytes;
     uint32_t o_b2, o_e, o_coef, o_hmask, o_fq, o_gib;   // offsets from the blob start
@@ -104,6 +105,7 @@ struct Bf16Params {
     float *om;
     int64_t n, ldY, ldO;
     int ns, nch, ntiles;
+    int fac_chunk0;            // chunk 0 holds third-body / falloff reactions
     int stage_y;               // T, P, Y tiles staged in shared memory (the Y buffer then also
                                // stages omega on its way out)
     int bulk_out;              // omega rows contiguous (ldO == ns) and 16-byte aligned
@@ -120,7 +122,7 @@ struct Bf16Params {
 
 enum {
     BAR_BTAB, BAR_YFULL, BAR_YEMPTY, BAR_A1FULL, BAR_D1FULL, BAR_D1EMPTY, BAR_A2FULL, BAR_A2EMPTY,
-    BAR_D2FULL, BAR_D2EMPTY, BAR_XREADY, BAR_A1FREE, BAR_DRAIN, BAR_WREADY, BAR_COUNT
+    BAR_D2FULL, BAR_D2EMPTY, BAR_XREADY, BAR_A1FREE, BAR_DRAIN, BAR_WREADY, BAR_ZFREE, BAR_COUNT
 };
 
 struct SmemCtl {
@@ -271,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        const uint32_t cnt[BAR_COUNT] = {1, 1, 16, 16, 1, 16, 16, 1, 1, 16, 16, 1, 2, 16};
+        const uint32_t cnt[BAR_COUNT] = {1, 1, 16, 16, 1, 16, 16, 1, 1, 16, 16, 1, 2, 16, 1};
         for (int i = 0; i < BAR_COUNT; ++i) tc::mbar_init(BAR(i), cnt[i]);
         tc::mbar_fence_init();
         ctl->abort = 0;
@@ -349,6 +351,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 tc::commit(BAR(BAR_D1FULL));
                 ++u_d1;
             };
+            // contraction 0: z (hi, lo) . (eff - 1) (hi, lo) as hi.hi + hi.lo + lo.hi into the
+            // multiplier columns.  Issued after chunk 0's contraction 1 (it then runs while
+            // chunk 0's S is read out) unless chunk 0 reads multipliers; either way a D1FULL
+            // commit of this thread covers it before the first chunk that reads them, and its
+            // operand columns are free for chunk 0's q_net at ZFREE.
+            auto issue_mma0 = [&]() {
+#pragma unroll
+                for (int s = 0; s < 3; ++s)
+#pragma unroll
+                    for (int kk = 0; kk < NSP / 16; ++kk)
+                        tc::mma_ts(tmem + CL::FC, tmem + CL::A2 + (s == 2 ? NSP / 2 : 0) + kk * 8,
+                                   tc::sdesc_noswz(be + (s == 1 ? kFacCols * NSP * 2 : 0) + kk * 256,
+                                                   128, (NSP / 8) * 128),
+                                   id0, (s | kk) != 0);
+                tc::commit(BAR(BAR_ZFREE));
+            };
             auto mma2 = [&](int c) {
                 const uint32_t bc = b2 + (uint32_t)c * (NSP * RC * 2);
 #pragma unroll
@@ -367,19 +385,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x, ++it) {
                     if (!(ok = wait_bar(BAR(BAR_A1FULL), it & 1, ctl, p.status, 2))) break;
                     tc::fence_after();
-                    // contraction 0: z (hi, lo) . (eff - 1) (hi, lo) as hi.hi + hi.lo + lo.hi
-                    // into the multiplier columns; complete before chunk 0's D1FULL (issue
-                    // order of this thread)
-#pragma unroll
-                    for (int s = 0; s < 3; ++s)
-#pragma unroll
-                        for (int kk = 0; kk < NSP / 16; ++kk)
-                            tc::mma_ts(tmem + CL::FC,
-                                       tmem + CL::A2 + (s == 2 ? NSP / 2 : 0) + kk * 8,
-                                       tc::sdesc_noswz(be + (s == 1 ? kFacCols * NSP * 2 : 0) +
-                                                           kk * 256,
-                                                       128, (NSP / 8) * 128),
-                                       id0, (s | kk) != 0);
+                    // chunk 0 reads multipliers: contraction 0 first (its D1FULL covers it)
+                    if (p.fac_chunk0) issue_mma0();
                     // contraction 1 of each chunk as soon as the previous S has been read out
                     for (int c = 0; ok && c < p.nch; ++c) {
                         if (!(ok = wait_bar(BAR(BAR_D1EMPTY), (u_d1 & 1) ^ 1, ctl, p.status, 2)))
@@ -387,6 +394,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                         tc::fence_after();
                         issue_mma1(c);
                         ctl->mma1_issued = (int)u_d1;
+                        if (c == 0 && !p.fac_chunk0) issue_mma0();
                     }
                     // completes when every contraction 1 of the tile has read its operands
                     if (ok) tc::commit(BAR(BAR_A1FREE));
@@ -620,6 +628,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                     lw[r / 2] = tc::pack_bf16x2(r0, r1);
                 }
                 if (!(ok = wait_bar(BAR(BAR_A2EMPTY), (u & 1) ^ 1, ctl, p.status, 3))) break;
+                // chunk 0: contraction 0 has read z from these columns
+                if (c == 0 && !(ok = wait_bar(BAR(BAR_ZFREE), it & 1, ctl, p.status, 3))) break;
                 tc::fence_after();
                 const uint32_t a2 = tmem + lane_off + CL::A2 + g * (RH / 2);
                 tc::tmem_st8(a2, hw);
@@ -940,6 +950,8 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
     unsigned char *base = (unsigned char *)t->d_blob;
     t->nsp = nsp;
     t->fold = fold;
+    t->fac_chunk0 = 0;
+    for (int q = 0; q < NQ; ++q) t->fac_chunk0 |= hmask[q] ? 1 : 0;
     t->nch = nch;
     t->b1_bytes = b1.size() * 2;
     t->blob_bytes = blob;
@@ -1022,6 +1034,7 @@ chem_status launch_source_bf16(const chem_mech *m, int64_t n, const float *T, co
     prm.ldO = ldO;
     prm.ns = m->ns;
     prm.nch = t->nch;
+    prm.fac_chunk0 = t->fac_chunk0;
     prm.bulk_out = (ldO == m->ns && (uintptr_t)om % 16 == 0) ? 1 : 0;
     prm.ntiles = (int)((n + 127) / 128);
     prm.btab = t->btab;
