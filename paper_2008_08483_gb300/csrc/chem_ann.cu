@@ -67,9 +67,17 @@ extern "C" chem_status chem_kc_ann_load(const chem_mech *m, const chem_kc_ann_de
     };
     put(d->w_in, n_in);
     put(d->b_in, n_in);
-    put(d->w_hid, n_hid);
+    // hidden weights stored input-major per layer ([n_layers - 1][input][output]): lane o of
+    // the FP32 kernel computes output unit o, so one input's weights are read together
+    for (int l = 0; l + 1 < nl; ++l)
+        for (int i = 0; i < nh; ++i)
+            for (int o = 0; o < nh; ++o)
+                h.push_back(d->w_hid[((size_t)l * nh + o) * nh + i]);
     put(d->b_hid, n_bh);
-    put(d->w_out, n_out);
+    // output weights stored hidden-unit-major ([n_hidden][n_reactions]): the FP32 kernel's
+    // lanes take consecutive reactions and read one hidden unit's weights together
+    for (int u = 0; u < nh; ++u)
+        for (int j = 0; j < nr; ++j) h.push_back(d->w_out[(size_t)j * nh + u]);
     put(d->b_out, nr);
     put(d->y_mean, nr);
     put(d->y_std, nr);

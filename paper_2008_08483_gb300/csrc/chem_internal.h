@@ -100,8 +100,8 @@ struct KcAnnView {
     int nl, nh, act;             // act: 0 ReLU, 1 ELU
     float x_mean, x_inv_std;
     const float *w_in, *b_in;    // [nh], [nh]
-    const float *w_hid, *b_hid;  // [nl-1][nh][nh] (row = output unit), [nl-1][nh]
-    const float *w_out, *b_out;  // [nr][nh], [nr]
+    const float *w_hid, *b_hid;  // [nl-1][nh][nh] (input-major: [input][output]), [nl-1][nh]
+    const float *w_out, *b_out;  // [nh][nr] (hidden-unit-major), [nr]
     const float *y_mean, *y_std; // [nr]
 };
 
@@ -113,6 +113,21 @@ struct MechViewF32 {
     const float *tb_e;
     float t_mid;
     float2 lg2_pref_R;           // log2(p_ref / R), double-float
+    // species-major net stoichiometry (Eq. 2 as a gather): the reactions that change species
+    // k are entries col_ptr[k] .. col_ptr[k + 1] of (col_rxn, col_nu = nu''_kj - nu'_kj),
+    // in reaction order
+    const int32_t *col_ptr;
+    const int32_t *col_rxn;
+    const float *col_nu;
+    // the gather's species per lane, balanced by entry count: lane l takes species
+    // lane_sp[lane_ptr[l]] .. lane_sp[lane_ptr[l + 1] - 1]
+    const int32_t *lane_ptr;
+    const int32_t *lane_sp;
+    // the reaction records as 32-bit words, slot-major ([word][slot], slots in the kind-
+    // grouped processing order, empty slots zero), so that 32 lanes reading one field of 32
+    // consecutive slots make one coalesced load
+    const uint32_t *rxn_t;
+    int32_t n_slots;
 };
 
 }  // namespace chem

@@ -14,6 +14,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "chem_internal.h"
@@ -330,11 +331,64 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
         gptr[g * (ns + 1) + ns] = (int32_t)gslot.size();
     }
     const size_t nge = gslot.size() ? gslot.size() : 1;
+    // species-major net stoichiometry for the FP32 gather
+    std::vector<int32_t> cptr(ns + 1, 0), crxn;
+    std::vector<float> cnu;
+    for (int k = 0; k < ns; ++k) {
+        cptr[k] = (int32_t)crxn.size();
+        for (int j = 0; j < nr; ++j) {
+            const int nu = d->nu_r[(size_t)j * ns + k] - d->nu_f[(size_t)j * ns + k];
+            if (nu) {
+                crxn.push_back(j);
+                cnu.push_back((float)nu);
+            }
+        }
+    }
+    cptr[ns] = (int32_t)crxn.size();
+    const size_t nce = crxn.size() ? crxn.size() : 1;
+    // species -> lanes for the gather: longest lists first, each to the least loaded lane
+    std::vector<int32_t> lptr(33, 0), lsp;
+    {
+        std::vector<int> by(ns);
+        for (int k = 0; k < ns; ++k) by[k] = k;
+        std::stable_sort(by.begin(), by.end(), [&](int a, int b) {
+            return cptr[a + 1] - cptr[a] > cptr[b + 1] - cptr[b];
+        });
+        std::vector<std::vector<int32_t>> lanes(32);
+        std::vector<long> load(32, 0);
+        for (int k : by) {
+            int l = 0;
+            for (int x = 1; x < 32; ++x)
+                if (load[x] < load[l]) l = x;
+            lanes[l].push_back(k);
+            load[l] += 1 + (cptr[k + 1] - cptr[k]);
+        }
+        for (int l = 0; l < 32; ++l) {
+            lptr[l] = (int32_t)lsp.size();
+            lsp.insert(lsp.end(), lanes[l].begin(), lanes[l].end());
+        }
+        lptr[32] = (int32_t)lsp.size();
+    }
+    // reaction records, slot-major words
+    constexpr size_t kW32 = sizeof(RxnF32) / 4;
+    std::vector<uint32_t> rt(kW32 * order.size(), 0);
+    for (size_t sl = 0; sl < order.size(); ++sl) {
+        if (order[sl] < 0) continue;
+        uint32_t w[kW32];
+        memcpy(w, &r32[order[sl]], sizeof(RxnF32));
+        for (size_t q = 0; q < kW32; ++q) rt[q * order.size() + sl] = w[q];
+    }
     size_t o_ord = align(o_w + sizeof(double) * ns);
     size_t o_gptr = align(o_ord + sizeof(int32_t) * order.size());
     size_t o_gslot = align(o_gptr + sizeof(int32_t) * gptr.size());
     size_t o_gnu = align(o_gslot + sizeof(int32_t) * nge);
-    size_t total = align(o_gnu + sizeof(double) * nge);
+    size_t o_cptr = align(o_gnu + sizeof(double) * nge);
+    size_t o_crxn = align(o_cptr + sizeof(int32_t) * cptr.size());
+    size_t o_cnu = align(o_crxn + sizeof(int32_t) * nce);
+    size_t o_lptr = align(o_cnu + sizeof(float) * nce);
+    size_t o_lsp = align(o_lptr + sizeof(int32_t) * lptr.size());
+    size_t o_rt = align(o_lsp + sizeof(int32_t) * (lsp.size() ? lsp.size() : 1));
+    size_t total = align(o_rt + sizeof(uint32_t) * rt.size());
     std::vector<unsigned char> h(total, 0);
     memcpy(h.data() + o_r64, r64.data(), sizeof(RxnF64) * nr);
     memcpy(h.data() + o_r32, r32.data(), sizeof(RxnF32) * nr);
@@ -353,6 +407,14 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
     if (!gslot.empty()) {
         memcpy(h.data() + o_gslot, gslot.data(), sizeof(int32_t) * gslot.size());
         memcpy(h.data() + o_gnu, gnu.data(), sizeof(double) * gnu.size());
+    }
+    memcpy(h.data() + o_cptr, cptr.data(), sizeof(int32_t) * cptr.size());
+    memcpy(h.data() + o_lptr, lptr.data(), sizeof(int32_t) * lptr.size());
+    if (!lsp.empty()) memcpy(h.data() + o_lsp, lsp.data(), sizeof(int32_t) * lsp.size());
+    memcpy(h.data() + o_rt, rt.data(), sizeof(uint32_t) * rt.size());
+    if (!crxn.empty()) {
+        memcpy(h.data() + o_crxn, crxn.data(), sizeof(int32_t) * crxn.size());
+        memcpy(h.data() + o_cnu, cnu.data(), sizeof(float) * cnu.size());
     }
 
     chem_mech *m = new (std::nothrow) chem_mech();
@@ -395,6 +457,13 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
     m->v32.tb_e = (const float *)(base + o_tbe32);
     m->v32.t_mid = (float)d->t_mid;
     m->v32.lg2_pref_R = dsplit(log2(d->p_ref / kR));
+    m->v32.col_ptr = (const int32_t *)(base + o_cptr);
+    m->v32.col_rxn = (const int32_t *)(base + o_crxn);
+    m->v32.col_nu = (const float *)(base + o_cnu);
+    m->v32.lane_ptr = (const int32_t *)(base + o_lptr);
+    m->v32.lane_sp = (const int32_t *)(base + o_lsp);
+    m->v32.rxn_t = (const uint32_t *)(base + o_rt);
+    m->v32.n_slots = (int32_t)order.size();
     m->vint.rxn = (const RxnInt *)(base + o_rint);
     m->vint.nasa = (const double *)(base + o_nasa);
     m->vint.W = (const double *)(base + o_w);

@@ -1,15 +1,17 @@
 // kern_simt.cu -- SIMT source-term kernels: FP64 and FP32 (double-float exponents).
 //
-// One thread per cell; all threads of a warp walk the reactions in the same order,
+// FP64: one thread per cell; all threads of a warp walk the reactions in the same order,
 // so every per-reaction table load is a broadcast and every branch on the reaction
 // kind is warp-uniform.  Per-cell species arrays live in shared memory laid out
-// [species][thread] (conflict-free, each thread owns one column).
+// [species][thread] (conflict-free, each thread owns one column).  FP32: one warp per cell
+// (see k_source_f32).
 //
 // Per reaction j (Eq. 4 in log space, Eqs. 5-11, Sec. 2.4):
 //   ln q_f = sum_k nu'_kj ln C_k + ln k_inf,j + ln(third-body or falloff factor)
 //   ln q_r = sum_k nu''_kj ln C_k + ln k_inf,j - ln K_c,j + (same factor)   [reversible]
 //   omega_k += (nu''_kj - nu'_kj) (exp(ln q_f) - exp(ln q_r))
 #include <math.h>
+#include <stddef.h>
 #include <string.h>
 
 #include "chem_internal.h"
@@ -166,202 +168,270 @@ __device__ __forceinline__ float ann_act(float x, int act)
     return act ? (x > 0.0f ? x : expm1f(x)) : fmaxf(x, 0.0f);
 }
 
-// With ANN, ln K_c of every reversible reaction comes from the approximate network
-// (Sec. 2.3, Eqs. 12-14) evaluated once per cell, instead of the Gibbs layer.
-template <int BLK, bool ANN>
-__global__ void __launch_bounds__(BLK)
-k_source_f32(MechViewF32 mv, KcAnnView av, int64_t n, const float *__restrict__ T,
+// One warp per cell, 32 cells per warp.  A first pass with one lane per cell computes the
+// per-cell features (FP64, converted to double-float pairs) of the warp's 32 cells; then for
+// each cell the lanes take its species (z_k = Y_k / W_k from one coalesced row, log2 z_k as
+// an exact exponent and the log2 of the mantissa, the Gibbs layer, sum_k z_k by a warp
+// reduction), then its reactions (lane = reaction slot, slots grouped by kind so that the
+// kind branches are warp-uniform), then omega by species (a gather over the species-major
+// net stoichiometry, compensated, one coalesced row store).  With ANN, ln K_c of every
+// reversible reaction comes from the approximate network (Sec. 2.3, Eqs. 12-14), whose hidden
+// units the lanes evaluate once per cell, instead of the Gibbs layer.
+constexpr int kF32Warps = 8;                   // warps per block
+constexpr int kCellScalars = 16;               // per-cell scalars kept in shared memory
+
+__device__ __forceinline__ df df_warp_sum(df v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const df o = mkdf(__shfl_xor_sync(0xffffffffu, v.h, off),
+                          __shfl_xor_sync(0xffffffffu, v.l, off));
+        v = df_add(v, o);
+    }
+    return v;
+}
+
+// log2 of a positive double-float: exact exponent + log2 of the mantissa + the low part
+__device__ __forceinline__ df df_log2(df x)
+{
+    int ex;
+    const float m = frexpf(x.h, &ex);          // x.h = m 2^ex, m in [0.5, 1)
+    return df_add_f(two_sum((float)ex, log2f(m)), x.l / x.h * 1.4426950408889634f);
+}
+
+// One reaction record read from the slot-major word table: 32 lanes loading one field of 32
+// consecutive slots make one coalesced load.
+struct RxnW {
+    const uint32_t *p;                         // word 0 of this slot
+    int stride;                                // slots per word row
+    __device__ __forceinline__ uint32_t word(size_t b) const { return __ldg(p + (b / 4) * (size_t)stride); }
+    __device__ __forceinline__ float f(size_t b) const { return __uint_as_float(word(b)); }
+    __device__ __forceinline__ int i(size_t b) const { return (int)word(b); }
+    __device__ __forceinline__ df d2(size_t b) const { return mkdf(f(b), f(b + 4)); }
+    __device__ __forceinline__ int u16(size_t b) const
+    {
+        const uint32_t x = word(b);
+        return (b & 2) ? (int)(x >> 16) : (int)(x & 0xFFFFu);
+    }
+    __device__ __forceinline__ int u8(size_t b) const
+    {
+        return (int)((word(b) >> (8 * (b & 3))) & 0xFFu);
+    }
+};
+#define RXO(field) offsetof(RxnF32, field)
+
+template <bool ANN>
+__global__ void __launch_bounds__(32 * kF32Warps)
+k_source_f32(MechViewF32 mv, IntView iv, KcAnnView av, int64_t n, const float *__restrict__ T,
              const float *__restrict__ P, const float *__restrict__ Y, int64_t ldY,
              float *__restrict__ om, int64_t ldO)
 {
     extern __shared__ float smem32[];
-    const int ns = mv.ns, tid = threadIdx.x;
-    const int64_t i = (int64_t)blockIdx.x * BLK + tid;
-    if (i >= n) return;
-    float *sE = smem32 + tid;                  // integer part of log2 X_k (exact)
-    float *sF = smem32 + ns * BLK + tid;       // log2 of the mantissa of X_k, in [-1, 0)
-    float *sGh = smem32 + 2 * ns * BLK + tid;  // -g_k/(RT) in log2 units, double-float
-    float *sGl = smem32 + 3 * ns * BLK + tid;
-    float *sWs = smem32 + 4 * ns * BLK + tid;  // omega_k, compensated sum
-    float *sWc = smem32 + 5 * ns * BLK + tid;
-    float *sH = smem32 + 6 * ns * BLK + tid;   // ANN: two layers of hidden units
-    const float Tf = T[i], Pf = P[i];
-    const float *Yi = Y + i * ldY;
-    double sum = 0.0;
-    for (int k = 0; k < ns; ++k) {
-        float y = Yi[k];
-        y = (y > 0.0f ? y : 0.0f) * mv.spec[k].invW;
-        sF[k * BLK] = y;
-        sum += (double)y;
-    }
-    const double inv_sum = sum > 0.0 ? 1.0 / sum : 0.0;
-    // per-cell features in double precision, kept as double-float pairs
-    const double Td = (double)Tf;
-    const double lg2Td = log2(Td);
-    const df lg2T = df_from_double(lg2Td);
-    const df invT = df_from_double(1.0 / Td);
-    const double taud = Td * 1e-3;
-    df phi[7];                                 // [1, log2 T, tau, tau^2, tau^3, tau^4, 1/T]
-    phi[0] = mkdf(1.0f, 0.0f);
-    phi[1] = lg2T;
-    phi[2] = df_from_double(taud);
-    phi[3] = df_from_double(taud * taud);
-    phi[4] = df_from_double(taud * taud * taud);
-    phi[5] = df_from_double(taud * taud * taud * taud);
-    phi[6] = invT;
-    const df lgct = df_from_double(log2((double)Pf) - log2(kR) - lg2Td);    // log2 c_tot
-    const df lgpRT = df_add(mkdf(mv.lg2_pref_R), mkdf(-lg2T.h, -lg2T.l));  // log2(p_ref/RT)
-    const int rg = Tf >= mv.t_mid ? 1 : 0;
-    for (int k = 0; k < ns; ++k) {
-        const double X = (double)sF[k * BLK] * inv_sum;
-        float e, f;
-        if (X > 0x1p-150) {
-            int ex;
-            const double m = frexp(X, &ex);    // X = m 2^ex, m in [0.5, 1)
-            e = (float)ex;
-            f = log2f((float)m);
-        } else {
-            e = kLg2Floor;
-            f = 0.0f;
-        }
-        sE[k * BLK] = e;
-        sF[k * BLK] = f;
-        if (!ANN) {
-            const float2 *c = mv.spec[k].gl[rg];
-            df g = mkdf(c[0]);
-            for (int m = 1; m < 7; ++m) g = df_add(g, df_mul(mkdf(c[m]), phi[m]));
-            sGh[k * BLK] = g.h;
-            sGl[k * BLK] = g.l;
-        }
-        sWs[k * BLK] = 0.0f;
-        sWc[k * BLK] = 0.0f;
-    }
-    int cur = 0;                               // ANN: layer buffer holding the last layer
-    if (ANN) {
-        const float x = (logf(Tf) - av.x_mean) * av.x_inv_std;
-        for (int h = 0; h < av.nh; ++h) sH[h * BLK] = ann_act(fmaf(av.w_in[h], x, av.b_in[h]), av.act);
-        for (int l = 0; l + 1 < av.nl; ++l) {
-            const float *W = av.w_hid + (size_t)l * av.nh * av.nh;
-            for (int o = 0; o < av.nh; ++o) {
-                float a = av.b_hid[l * av.nh + o];
-                for (int h = 0; h < av.nh; ++h)
-                    a = fmaf(W[o * av.nh + h], sH[(cur * kAnnMaxHidden + h) * BLK], a);
-                sH[((cur ^ 1) * kAnnMaxHidden + o) * BLK] = ann_act(a, av.act);
-            }
-            cur ^= 1;
+    const int ns = mv.ns, nr = mv.nr, lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    const int per_warp = 32 * kCellScalars + 5 * ns + nr + (ANN ? 2 * kAnnMaxHidden : 0);
+    float *cs = smem32 + (size_t)wb * per_warp;    // [32 cells][kCellScalars]
+    float *sE = cs + 32 * kCellScalars;            // integer part of log2 z_k (exact)
+    float *sF = sE + ns;                           // log2 of the mantissa of z_k, in [-1, 0)
+    float *sX = sF + ns;                           // X_k (third-body sums)
+    float *sGh = sX + ns;                          // -g_k/(RT) in log2 units, double-float
+    float *sGl = sGh + ns;
+    float *sQ = sGl + ns;                          // q_net per reaction
+    float *sH = sQ + nr;                           // ANN: two layers of hidden units
+    const int64_t i0 = ((int64_t)blockIdx.x * kF32Warps + wb) * 32;
+    if (i0 >= n) return;
+
+    // ---- per-cell features of the warp's 32 cells, one lane per cell (FP64 -> double-float)
+    {
+        const int64_t i = i0 + lane;
+        float *c = cs + lane * kCellScalars;
+        if (i < n) {
+            const float Tf = T[i], Pf = P[i];
+            const double Td = (double)Tf, lg2Td = log2(Td), taud = Td * 1e-3;
+            const df lg2T = df_from_double(lg2Td), invT = df_from_double(1.0 / Td);
+            const df p2 = df_from_double(taud), p3 = df_from_double(taud * taud);
+            const df p4 = df_from_double(taud * taud * taud);
+            const df p5 = df_from_double(taud * taud * taud * taud);
+            const df lgct = df_from_double(log2((double)Pf) - log2(kR) - lg2Td);  // log2 c_tot
+            const float v[kCellScalars] = {lg2T.h, lg2T.l, invT.h, invT.l, p2.h, p2.l, p3.h, p3.l,
+                                           p4.h,   p4.l,   p5.h,   p5.l,   lgct.h, lgct.l, Tf,
+                                           Tf >= mv.t_mid ? 1.0f : 0.0f};
+#pragma unroll
+            for (int q = 0; q < kCellScalars; ++q) c[q] = v[q];
         }
     }
-    for (int j = 0; j < mv.nr; ++j) {
-        const RxnF32 *R = mv.rxn + j;
-        // Arrhenius layer, log2 k_inf (Eq. 6)
-        df tf = df_add(df_add(mkdf(R->kf[0]), df_mul(mkdf(R->kf[1]), lg2T)),
-                       df_mul(mkdf(R->kf[2]), invT));
-        // third-body / falloff factor, log2 (Sec. 2.4)
-        df fac = mkdf(0.0f, 0.0f);
-        bool dead = false;
-        const int kind = R->kind;
-        if (kind != 0) {
-            float s = 1.0f;                    // M / c_tot = 1 + sum_k (eff_k - 1) X_k
-            for (int t = R->tb_begin; t < R->tb_end; ++t) {
-                const int k = mv.tb_sp[t];
-                s = fmaf(mv.tb_e[t], ldexpf(exp2f(sF[k * BLK]), (int)sE[k * BLK]), s);
-            }
-            if (!(s > 0.0f)) {
-                dead = true;
+    __syncwarp();
+
+    for (int cc = 0; cc < 32 && i0 + cc < n; ++cc) {
+        const int64_t i = i0 + cc;
+        const float *c = cs + cc * kCellScalars;
+        const df lg2T = mkdf(c[0], c[1]), invT = mkdf(c[2], c[3]);
+        const df lgct = mkdf(c[12], c[13]);
+        const float Tf = c[14];
+        const int rg = c[15] != 0.0f ? 1 : 0;
+        // ---- species: z_k, log2 z_k, Gibbs layer (Eq. 10), sum_k z_k
+        df zsum = mkdf(0.0f, 0.0f);
+        for (int k = lane; k < ns; k += 32) {
+            float y = Y[i * ldY + k];
+            const float z = (y > 0.0f ? y : 0.0f) * mv.spec[k].invW;
+            zsum = df_add_f(zsum, z);
+            sX[k] = z;
+            if (z > 0.0f) {
+                int ex;
+                const float m = frexpf(z, &ex);     // z = m 2^ex, m in [0.5, 1)
+                sE[k] = (float)ex;
+                sF[k] = log2f(m);
             } else {
-                const df lgM = df_add_f(lgct, log2f(s));
-                if (kind == 1) {
-                    fac = lgM;
-                } else {
-                    df t0 = df_add(df_add(mkdf(R->k0[0]), df_mul(mkdf(R->k0[1]), lg2T)),
-                                   df_mul(mkdf(R->k0[2]), invT));
-                    df lPr = df_add(df_add(t0, mkdf(-tf.h, -tf.l)), lgM);   // log2 Pr
-                    // log2(Pr / (1 + Pr)) without cancellation on either side of Pr = 1
-                    if (lPr.h < 0.0f)
-                        fac = df_add_f(lPr, -log2f(1.0f + exp2f(lPr.h)));
-                    else
-                        fac = mkdf(-log2f(1.0f + exp2f(-lPr.h)), 0.0f);
-                    if (kind == 3) {
-                        const float Tn = Tf;
-                        float Fc = R->troe[0] * expf(-Tn * R->troe[2]) +
-                                   R->troe[1] * expf(-Tn * R->troe[3]);
-                        if (R->troe[4] > 0.0f) Fc += expf(-R->troe[4] / Tn);
-                        const float lFc = log10f(Fc);
-                        const float c = -0.4f - 0.67f * lFc, nn = 0.75f - 1.27f * lFc;
-                        const float x = (lPr.h + lPr.l) * 0.30102999566398120f + c;
-                        const float f1 = x / (nn - 0.14f * x);
-                        fac = df_add_f(fac, lFc / (1.0f + f1 * f1) * 3.3219280948873623f);
-                    }
-                }
+                sE[k] = kLg2Floor;
+                sF[k] = 0.0f;
+            }
+            if (!ANN) {
+                const df phi[7] = {mkdf(1.0f, 0.0f), lg2T,           mkdf(c[4], c[5]),
+                                   mkdf(c[6], c[7]),  mkdf(c[8], c[9]), mkdf(c[10], c[11]), invT};
+                const float2 *g = mv.spec[k].gl[rg];
+                df G = mkdf(g[0]);
+                for (int m = 1; m < 7; ++m) G = df_add(G, df_mul(mkdf(g[m]), phi[m]));
+                sGh[k] = G.h;
+                sGl[k] = G.l;
             }
         }
-        float qn = 0.0f;
-        if (!dead) {
-            // forward: tf + ord' log2 c_tot + sum nu' log2 X + factor
-            float ei = 0.0f, fs = 0.0f;
-            for (int t = 0; t < R->nf; ++t) {
-                const int k = R->spf[t];
-                const float nu = (float)R->nuf[t];
-                ei = fmaf(nu, sE[k * BLK], ei);
-                fs = fmaf(nu, sF[k * BLK], fs);
-            }
-            df xf = df_add(df_add(tf, df_mul_f(lgct, (float)R->ordf)), fac);
-            xf = df_add_f(df_add_f(xf, ei), fs);
-            qn = df_exp2(xf);
-            if (R->rev) {
-                df lkc;
-                float er = 0.0f, fr = 0.0f;
-                if (ANN) {
-                    // ln K_c = y_mean + y_std (b + sum_h w_h a_h) (Eq. 14), in log2 units
-                    const float *w = av.w_out + (size_t)j * av.nh;
-                    float a = av.b_out[j];
+        zsum = df_warp_sum(zsum);
+        const bool any = zsum.h > 0.0f;
+        const float inv_sum = any ? 1.0f / zsum.h : 0.0f;
+        for (int k = lane; k < ns; k += 32) sX[k] *= inv_sum;    // X_k = z_k / sum_k z_k
+        // log2 X_k = log2 z_k - log2 sum_k z_k: the second term enters every reaction through
+        // its order, together with log2 c_tot
+        const df ls = any ? df_log2(zsum) : mkdf(0.0f, 0.0f);
+        const df lgcn = df_add(lgct, mkdf(-ls.h, -ls.l));
+        const df lgpRT = df_add(mkdf(mv.lg2_pref_R), mkdf(-lg2T.h, -lg2T.l));   // log2(p_ref/RT)
+        int cur = 0;
+        if (ANN) {
+            const float x = (logf(Tf) - av.x_mean) * av.x_inv_std;
+            if (lane < av.nh) sH[lane] = ann_act(fmaf(av.w_in[lane], x, av.b_in[lane]), av.act);
+            for (int l = 0; l + 1 < av.nl; ++l) {
+                __syncwarp();
+                const float *W = av.w_hid + (size_t)l * av.nh * av.nh;
+                if (lane < av.nh) {
+                    float a = av.b_hid[l * av.nh + lane];
                     for (int h = 0; h < av.nh; ++h)
-                        a = fmaf(w[h], sH[(cur * kAnnMaxHidden + h) * BLK], a);
-                    lkc = mkdf(fmaf(av.y_std[j], a, av.y_mean[j]) * 1.4426950408889634f, 0.0f);
-                    for (int t = 0; t < R->nr; ++t) {
-                        const int k = R->spr[t];
-                        const float nu = (float)R->nur[t];
-                        er = fmaf(nu, sE[k * BLK], er);
-                        fr = fmaf(nu, sF[k * BLK], fr);
-                    }
-                } else {
-                    // log2 K_c = sum_k nu_kj (-g_k/RT) + dnu log2(p_ref/RT) (Eqs. 8-9)
-                    lkc = df_mul_f(lgpRT, (float)R->dnu);
-                    for (int t = 0; t < R->nr; ++t) {
-                        const int k = R->spr[t];
-                        const float nu = (float)R->nur[t];
-                        lkc = df_add(lkc, df_mul_f(mkdf(sGh[k * BLK], sGl[k * BLK]), nu));
-                        er = fmaf(nu, sE[k * BLK], er);
-                        fr = fmaf(nu, sF[k * BLK], fr);
-                    }
-                    for (int t = 0; t < R->nf; ++t) {
-                        const int k = R->spf[t];
-                        lkc = df_add(lkc, df_mul_f(mkdf(sGh[k * BLK], sGl[k * BLK]),
-                                                   -(float)R->nuf[t]));
-                    }
+                        a = fmaf(W[h * av.nh + lane], sH[cur * kAnnMaxHidden + h], a);
+                    sH[(cur ^ 1) * kAnnMaxHidden + lane] = ann_act(a, av.act);
                 }
-                df xr = df_add(df_add(tf, df_mul_f(lgct, (float)R->ordr)), fac);
-                xr = df_add(xr, mkdf(-lkc.h, -lkc.l));
-                xr = df_add_f(df_add_f(xr, er), fr);
-                qn -= df_exp2(xr);
+                cur ^= 1;
             }
         }
-        // omega_k += nu_kj q_net (Eq. 2), compensated accumulation
-        for (int t = 0; t < R->nf; ++t) {
-            const int k = R->spf[t];
-            const df s = two_sum(sWs[k * BLK], -(float)R->nuf[t] * qn);
-            sWs[k * BLK] = s.h;
-            sWc[k * BLK] += s.l;
+        __syncwarp();
+        // ---- reactions, one slot per lane
+        for (int sl = lane; sl < iv.n_slots; sl += 32) {
+            const int j = iv.order[sl];
+            if (j < 0) continue;
+            const RxnW R{mv.rxn_t + sl, mv.n_slots};
+            // Arrhenius layer, log2 k_inf (Eq. 6)
+            const df tf = df_add(df_add(R.d2(RXO(kf)), df_mul(R.d2(RXO(kf) + 8), lg2T)),
+                                 df_mul(R.d2(RXO(kf) + 16), invT));
+            // third-body / falloff factor, log2 (Sec. 2.4)
+            df fac = mkdf(0.0f, 0.0f);
+            bool dead = false;
+            const int kind = R.i(RXO(kind));
+            if (kind != 0) {
+                float s = 1.0f;                    // M / c_tot = 1 + sum_k (eff_k - 1) X_k
+                const int tb1 = R.i(RXO(tb_end));
+                for (int t = R.i(RXO(tb_begin)); t < tb1; ++t) s = fmaf(mv.tb_e[t], sX[mv.tb_sp[t]], s);
+                if (!(s > 0.0f)) {
+                    dead = true;
+                } else {
+                    const df lgM = df_add_f(lgct, log2f(s));
+                    if (kind == 1) {
+                        fac = lgM;
+                    } else {
+                        df t0 = df_add(df_add(R.d2(RXO(k0)), df_mul(R.d2(RXO(k0) + 8), lg2T)),
+                                       df_mul(R.d2(RXO(k0) + 16), invT));
+                        df lPr = df_add(df_add(t0, mkdf(-tf.h, -tf.l)), lgM);   // log2 Pr
+                        // log2(Pr / (1 + Pr)) without cancellation on either side of Pr = 1
+                        if (lPr.h < 0.0f)
+                            fac = df_add_f(lPr, -log2f(1.0f + exp2f(lPr.h)));
+                        else
+                            fac = mkdf(-log2f(1.0f + exp2f(-lPr.h)), 0.0f);
+                        if (kind == 3) {
+                            const float tr4 = R.f(RXO(troe) + 16);
+                            float Fc = R.f(RXO(troe)) * expf(-Tf * R.f(RXO(troe) + 8)) +
+                                       R.f(RXO(troe) + 4) * expf(-Tf * R.f(RXO(troe) + 12));
+                            if (tr4 > 0.0f) Fc += expf(-tr4 / Tf);
+                            const float lFc = log10f(Fc);
+                            const float c1 = -0.4f - 0.67f * lFc, nn = 0.75f - 1.27f * lFc;
+                            const float x = (lPr.h + lPr.l) * 0.30102999566398120f + c1;
+                            const float f1 = x / (nn - 0.14f * x);
+                            fac = df_add_f(fac, lFc / (1.0f + f1 * f1) * 3.3219280948873623f);
+                        }
+                    }
+                }
+            }
+            float qn = 0.0f;
+            if (!dead) {
+                // forward: tf + ord' log2(c_tot / sum z) + sum nu' log2 z + factor
+                float ei = 0.0f, fs = 0.0f;
+                const int nf = R.i(RXO(nf)), nrr = R.i(RXO(nr));
+                for (int t = 0; t < nf; ++t) {
+                    const int k = R.u16(RXO(spf) + 2 * t);
+                    const float nu = (float)R.u8(RXO(nuf) + t);
+                    ei = fmaf(nu, sE[k], ei);
+                    fs = fmaf(nu, sF[k], fs);
+                }
+                df xf = df_add(df_add(tf, df_mul_f(lgcn, (float)R.i(RXO(ordf)))), fac);
+                xf = df_add_f(df_add_f(xf, ei), fs);
+                qn = df_exp2(xf);
+                if (R.i(RXO(rev))) {
+                    df lkc;
+                    float er = 0.0f, fr = 0.0f;
+                    if (ANN) {
+                        // ln K_c = y_mean + y_std (b + sum_h w_h a_h) (Eq. 14), in log2 units
+                        float a = av.b_out[j];
+                        for (int h = 0; h < av.nh; ++h)
+                            a = fmaf(av.w_out[(size_t)h * nr + j], sH[cur * kAnnMaxHidden + h], a);
+                        lkc = mkdf(fmaf(av.y_std[j], a, av.y_mean[j]) * 1.4426950408889634f, 0.0f);
+                        for (int t = 0; t < nrr; ++t) {
+                            const int k = R.u16(RXO(spr) + 2 * t);
+                            const float nu = (float)R.u8(RXO(nur) + t);
+                            er = fmaf(nu, sE[k], er);
+                            fr = fmaf(nu, sF[k], fr);
+                        }
+                    } else {
+                        // log2 K_c = sum_k nu_kj (-g_k/RT) + dnu log2(p_ref/RT) (Eqs. 8-9)
+                        lkc = df_mul_f(lgpRT, (float)R.i(RXO(dnu)));
+                        for (int t = 0; t < nrr; ++t) {
+                            const int k = R.u16(RXO(spr) + 2 * t);
+                            const float nu = (float)R.u8(RXO(nur) + t);
+                            lkc = df_add(lkc, df_mul_f(mkdf(sGh[k], sGl[k]), nu));
+                            er = fmaf(nu, sE[k], er);
+                            fr = fmaf(nu, sF[k], fr);
+                        }
+                        for (int t = 0; t < nf; ++t) {
+                            const int k = R.u16(RXO(spf) + 2 * t);
+                            lkc = df_add(lkc, df_mul_f(mkdf(sGh[k], sGl[k]),
+                                                       -(float)R.u8(RXO(nuf) + t)));
+                        }
+                    }
+                    df xr = df_add(df_add(tf, df_mul_f(lgcn, (float)R.i(RXO(ordr)))), fac);
+                    xr = df_add(xr, mkdf(-lkc.h, -lkc.l));
+                    xr = df_add_f(df_add_f(xr, er), fr);
+                    qn -= df_exp2(xr);
+                }
+            }
+            sQ[j] = qn;
         }
-        for (int t = 0; t < R->nr; ++t) {
-            const int k = R->spr[t];
-            const df s = two_sum(sWs[k * BLK], (float)R->nur[t] * qn);
-            sWs[k * BLK] = s.h;
-            sWc[k * BLK] += s.l;
+        __syncwarp();
+        // ---- omega_k = sum_j (nu''_kj - nu'_kj) q_net,j (Eq. 2), compensated, reaction order;
+        // the species are spread over the lanes by entry count
+        for (int a = mv.lane_ptr[lane]; a < mv.lane_ptr[lane + 1]; ++a) {
+            const int k = mv.lane_sp[a];
+            float ws = 0.0f, wc = 0.0f;
+            for (int e = mv.col_ptr[k]; e < mv.col_ptr[k + 1]; ++e) {
+                const df t = two_sum(ws, mv.col_nu[e] * sQ[mv.col_rxn[e]]);
+                ws = t.h;
+                wc += t.l;
+            }
+            om[i * ldO + k] = ws + wc;
         }
     }
-    float *oi = om + i * ldO;
-    for (int k = 0; k < ns; ++k) oi[k] = sWs[k * BLK] + sWc[k * BLK];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -413,36 +483,38 @@ chem_status launch_source_fp64(const chem_mech *m, int64_t n, const double *T, c
     return set_error(CHEM_EUNSUPPORTED, "fp64: %d species exceed the SIMT kernel", m->ns);
 }
 
+static size_t f32_warp_floats(const chem_mech *m, bool ann)
+{
+    return 32 * (size_t)kCellScalars + 5 * (size_t)m->ns + (size_t)m->nr +
+           (ann ? 2 * (size_t)kAnnMaxHidden : 0);
+}
+
 chem_status launch_source_fp32(const chem_mech *m, int64_t n, const float *T, const float *P,
                                const float *Y, int64_t ldY, float *om, int64_t ldO,
                                cudaStream_t s)
 {
-    static std::atomic<uint32_t> m64{0}, m32{0};
-    const size_t per = 6 * sizeof(float) * (size_t)m->ns;
+    static std::atomic<uint32_t> mask{0};
+    const size_t smem = sizeof(float) * kF32Warps * f32_warp_floats(m, false);
+    if (smem > kMaxDynSmem)
+        return set_error(CHEM_EUNSUPPORTED, "fp32: %d species / %d reactions exceed the SIMT kernel",
+                         m->ns, m->nr);
     KcAnnView none;
     memset(&none, 0, sizeof none);
-    if (per * 64 <= 200 * 1024)
-        return launch_rows<64>(k_source_f32<64, false>, m64, per * 64, n, s, "fp32", m->v32,
-                               none, n, T, P, Y, ldY, om, ldO);
-    if (per * 32 <= kMaxDynSmem)
-        return launch_rows<32>(k_source_f32<32, false>, m32, per * 32, n, s, "fp32", m->v32,
-                               none, n, T, P, Y, ldY, om, ldO);
-    return set_error(CHEM_EUNSUPPORTED, "fp32: %d species exceed the SIMT kernel", m->ns);
+    return launch_rows<32 * kF32Warps>(k_source_f32<false>, mask, smem, n, s, "fp32", m->v32,
+                                       m->vint, none, n, T, P, Y, ldY, om, ldO);
 }
 
 chem_status launch_source_fp32_ann(const chem_mech *m, const KcAnnView &av, int64_t n,
                                    const float *T, const float *P, const float *Y, int64_t ldY,
                                    float *om, int64_t ldO, cudaStream_t s)
 {
-    static std::atomic<uint32_t> m64{0}, m32{0};
-    const size_t per = sizeof(float) * (6 * (size_t)m->ns + 2 * kAnnMaxHidden);
-    if (per * 64 <= 200 * 1024)
-        return launch_rows<64>(k_source_f32<64, true>, m64, per * 64, n, s, "fp32 ann", m->v32,
-                               av, n, T, P, Y, ldY, om, ldO);
-    if (per * 32 <= kMaxDynSmem)
-        return launch_rows<32>(k_source_f32<32, true>, m32, per * 32, n, s, "fp32 ann", m->v32,
-                               av, n, T, P, Y, ldY, om, ldO);
-    return set_error(CHEM_EUNSUPPORTED, "fp32 ann: %d species exceed the SIMT kernel", m->ns);
+    static std::atomic<uint32_t> mask{0};
+    const size_t smem = sizeof(float) * kF32Warps * f32_warp_floats(m, true);
+    if (smem > kMaxDynSmem)
+        return set_error(CHEM_EUNSUPPORTED,
+                         "fp32 ann: %d species / %d reactions exceed the SIMT kernel", m->ns, m->nr);
+    return launch_rows<32 * kF32Warps>(k_source_f32<true>, mask, smem, n, s, "fp32 ann", m->v32,
+                                       m->vint, av, n, T, P, Y, ldY, om, ldO);
 }
 
 // Exact ln K_c of every reaction (Eqs. 8-11, the FP64 folded Gibbs layer), one thread per
