@@ -338,6 +338,7 @@ def main():
 
     if rank == 0 and not args.no_extras:
         extras(line, h, mech, T, P, Y, dev, dev32, out32, ns, prec_name, stream, args)
+        extras_sweep(line, h, T, P, Y, dev, stream)
         extras_integrator(line, mech, dev, stream)
         extras_heavy(line, dev, stream)
         extras_kc_ann(line, dev, stream)
@@ -419,6 +420,57 @@ def extras(line, h, mech, T, P, Y, dev, dev32, out32, ns, prec_name, stream, arg
     if "fp64" in paths and "cells_per_s" in paths.get(prec_name, {}):
         paths["speedup_vs_fp64"] = paths[prec_name]["cells_per_s"] / paths["fp64"]["cells_per_s"]
     line["paths"] = paths
+
+
+def extras_sweep(line, h, T, P, Y, dev, stream):
+    """Launch latency and the cell-count sweep.  The 9/21 mechanism at 1024 cells (states as
+    the parity tests draw them) gives microseconds per call for each path; the 53/325
+    mechanism from 2^6 to 2^22 cells (the workload's states, repeated past 2^20) gives ms per
+    call and cells/s, flat below the count that fills the GPU and then linear in it."""
+    import torch
+    from paper_2008_08483_gb300 import chem, synth
+    res = {}
+    m9 = synth.make_mechanism("h2air_9_21", seed=1)
+    h9 = chem.Mechanism(m9)
+    T9, P9, Y9 = synth.make_states(m9, 1024, seed=STATE_SEED, kind="dirichlet",
+                                   T_range=(1000.0, 2500.0), P_atm=(1.0, 1.0))
+    lat = {}
+    for name in ("fp64", "fp32", "split_bf16"):
+        p = chem.PRECISIONS[name]
+        dt = torch.float64 if p == chem.FP64 else torch.float32
+        din = [torch.as_tensor(a, dtype=dt).to(dev) for a in (T9, P9, Y9)]
+        o = torch.empty((1024, m9.n_species), dtype=dt, device=dev)
+        ms = time_device(lambda: chem.source_term(h9, *din, p, out=o, stream=stream), 200, 20,
+                         stream, 1, dev)
+        lat[name] = ms * 1e3
+    res["h2air_9_21_1024_cells_us_per_call"] = lat
+    h9.close()
+    sweep = {}
+    ns = Y.shape[1]
+    for name, top in (("split_bf16", 22), ("fp32", 22), ("fp64", 20)):
+        p = chem.PRECISIONS[name]
+        dt = torch.float64 if p == chem.FP64 else torch.float32
+        n_top = 1 << top
+        rep = (n_top + len(T) - 1) // len(T)
+        Tt = torch.as_tensor(np.tile(T, rep)[:n_top], dtype=dt).to(dev)
+        Pt = torch.as_tensor(np.tile(P, rep)[:n_top], dtype=dt).to(dev)
+        Yt = torch.as_tensor(np.tile(Y, (rep, 1))[:n_top], dtype=dt).to(dev)
+        o = torch.empty((n_top, ns), dtype=dt, device=dev)
+        pts = []
+        for lg in range(6, top + 1, 2):
+            n = 1 << lg
+            steps = 200 if lg <= 14 else (50 if lg <= 18 else 5)
+            ms = time_device(lambda n=n: chem.source_term(h, Tt[:n], Pt[:n], Yt[:n], p, out=o[:n],
+                                                          stream=stream),
+                             steps, 3, stream, 1, dev)
+            pts.append({"n_cells": n, "ms": ms, "cells_per_s": n / (ms * 1e-3)})
+        best = max(q["cells_per_s"] for q in pts)
+        sweep[name] = {"points": pts,
+                       "saturation_cells": min(q["n_cells"] for q in pts
+                                               if q["cells_per_s"] >= 0.9 * best)}
+        del Tt, Pt, Yt, o
+    res["gri_53_325_sweep"] = sweep
+    line["latency_and_sweep"] = res
 
 
 def extras_integrator(line, mech, dev, stream, n=4096, t_end=1e-2, rtol=1e-6, atol=1e-12):
