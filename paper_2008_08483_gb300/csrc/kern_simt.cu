@@ -168,8 +168,10 @@ __device__ __forceinline__ float ann_act(float x, int act)
     return act ? (x > 0.0f ? x : expm1f(x)) : fmaxf(x, 0.0f);
 }
 
-// One warp per cell, 32 cells per warp.  A first pass with one lane per cell computes the
-// per-cell features (FP64, converted to double-float pairs) of the warp's 32 cells; then for
+// One warp per cell, cpw (1..32) consecutive cells per warp: 32 once the batch fills the GPU,
+// fewer for small batches so that every resident warp gets work.  A first pass with one lane
+// per cell computes the per-cell features (FP64, converted to double-float pairs) of the
+// warp's cells; then for
 // each cell the lanes take its species (z_k = Y_k / W_k from one coalesced row, log2 z_k as
 // an exact exponent and the log2 of the mantissa, the Gibbs layer, sum_k z_k by a warp
 // reduction), then its reactions (lane = reaction slot, slots grouped by kind so that the
@@ -222,9 +224,9 @@ struct RxnW {
 
 template <bool ANN>
 __global__ void __launch_bounds__(32 * kF32Warps)
-k_source_f32(MechViewF32 mv, IntView iv, KcAnnView av, int64_t n, const float *__restrict__ T,
-             const float *__restrict__ P, const float *__restrict__ Y, int64_t ldY,
-             float *__restrict__ om, int64_t ldO)
+k_source_f32(MechViewF32 mv, IntView iv, KcAnnView av, int64_t n, int cpw,
+             const float *__restrict__ T, const float *__restrict__ P,
+             const float *__restrict__ Y, int64_t ldY, float *__restrict__ om, int64_t ldO)
 {
     extern __shared__ float smem32[];
     const int ns = mv.ns, nr = mv.nr, lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
@@ -237,14 +239,14 @@ k_source_f32(MechViewF32 mv, IntView iv, KcAnnView av, int64_t n, const float *_
     float *sGl = sGh + ns;
     float *sQ = sGl + ns;                          // q_net per reaction
     float *sH = sQ + nr;                           // ANN: two layers of hidden units
-    const int64_t i0 = ((int64_t)blockIdx.x * kF32Warps + wb) * 32;
+    const int64_t i0 = ((int64_t)blockIdx.x * kF32Warps + wb) * cpw;
     if (i0 >= n) return;
 
-    // ---- per-cell features of the warp's 32 cells, one lane per cell (FP64 -> double-float)
+    // ---- per-cell features of the warp's cells, one lane per cell (FP64 -> double-float)
     {
         const int64_t i = i0 + lane;
         float *c = cs + lane * kCellScalars;
-        if (i < n) {
+        if (lane < cpw && i < n) {
             const float Tf = T[i], Pf = P[i];
             const double Td = (double)Tf, lg2Td = log2(Td), taud = Td * 1e-3;
             const df lg2T = df_from_double(lg2Td), invT = df_from_double(1.0 / Td);
@@ -261,7 +263,7 @@ k_source_f32(MechViewF32 mv, IntView iv, KcAnnView av, int64_t n, const float *_
     }
     __syncwarp();
 
-    for (int cc = 0; cc < 32 && i0 + cc < n; ++cc) {
+    for (int cc = 0; cc < cpw && i0 + cc < n; ++cc) {
         const int64_t i = i0 + cc;
         const float *c = cs + cc * kCellScalars;
         const df lg2T = mkdf(c[0], c[1]), invT = mkdf(c[2], c[3]);
@@ -489,32 +491,57 @@ static size_t f32_warp_floats(const chem_mech *m, bool ann)
            (ann ? 2 * (size_t)kAnnMaxHidden : 0);
 }
 
+// Cells per warp: 32 when the batch fills every resident warp 32 times over, else just
+// enough to cover the batch with the resident warps.
+template <typename K>
+static int f32_cells_per_warp(K kern, size_t smem, int64_t n)
+{
+    int dev = 0, nsm = 0, blocks = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, 32 * kF32Warps, smem);
+    const int64_t warps = (int64_t)(nsm > 0 ? nsm : 1) * (blocks > 0 ? blocks : 1) * kF32Warps;
+    const int64_t cpw = (n + warps - 1) / warps;
+    return (int)(cpw < 1 ? 1 : cpw > 32 ? 32 : cpw);
+}
+
+template <bool ANN>
+static chem_status launch_f32(const chem_mech *m, const KcAnnView &av, int64_t n, const float *T,
+                              const float *P, const float *Y, int64_t ldY, float *om,
+                              int64_t ldO, cudaStream_t s, const char *name)
+{
+    static std::atomic<uint32_t> mask{0};
+    if (n <= 0) return CHEM_OK;
+    const size_t smem = sizeof(float) * kF32Warps * f32_warp_floats(m, ANN);
+    if (smem > kMaxDynSmem)
+        return set_error(CHEM_EUNSUPPORTED, "%s: %d species / %d reactions exceed the SIMT kernel",
+                         name, m->ns, m->nr);
+    chem_status st = smem_opt_in(k_source_f32<ANN>, mask, name);
+    if (st != CHEM_OK) return st;
+    const int cpw = f32_cells_per_warp(k_source_f32<ANN>, smem, n);
+    const int64_t per_block = (int64_t)cpw * kF32Warps;
+    k_source_f32<ANN><<<(unsigned)((n + per_block - 1) / per_block), 32 * kF32Warps, smem, s>>>(
+        m->v32, m->vint, av, n, cpw, T, P, Y, ldY, om, ldO);
+    g_launches.fetch_add(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(CHEM_ECUDA, "%s launch: %s", name, cudaGetErrorString(e));
+    return CHEM_OK;
+}
+
 chem_status launch_source_fp32(const chem_mech *m, int64_t n, const float *T, const float *P,
                                const float *Y, int64_t ldY, float *om, int64_t ldO,
                                cudaStream_t s)
 {
-    static std::atomic<uint32_t> mask{0};
-    const size_t smem = sizeof(float) * kF32Warps * f32_warp_floats(m, false);
-    if (smem > kMaxDynSmem)
-        return set_error(CHEM_EUNSUPPORTED, "fp32: %d species / %d reactions exceed the SIMT kernel",
-                         m->ns, m->nr);
     KcAnnView none;
     memset(&none, 0, sizeof none);
-    return launch_rows<32 * kF32Warps>(k_source_f32<false>, mask, smem, n, s, "fp32", m->v32,
-                                       m->vint, none, n, T, P, Y, ldY, om, ldO);
+    return launch_f32<false>(m, none, n, T, P, Y, ldY, om, ldO, s, "fp32");
 }
 
 chem_status launch_source_fp32_ann(const chem_mech *m, const KcAnnView &av, int64_t n,
                                    const float *T, const float *P, const float *Y, int64_t ldY,
                                    float *om, int64_t ldO, cudaStream_t s)
 {
-    static std::atomic<uint32_t> mask{0};
-    const size_t smem = sizeof(float) * kF32Warps * f32_warp_floats(m, true);
-    if (smem > kMaxDynSmem)
-        return set_error(CHEM_EUNSUPPORTED,
-                         "fp32 ann: %d species / %d reactions exceed the SIMT kernel", m->ns, m->nr);
-    return launch_rows<32 * kF32Warps>(k_source_f32<true>, mask, smem, n, s, "fp32 ann", m->v32,
-                                       m->vint, av, n, T, P, Y, ldY, om, ldO);
+    return launch_f32<true>(m, av, n, T, P, Y, ldY, om, ldO, s, "fp32 ann");
 }
 
 // Exact ln K_c of every reaction (Eqs. 8-11, the FP64 folded Gibbs layer), one thread per
