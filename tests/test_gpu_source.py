@@ -204,3 +204,16 @@ def test_bf16_without_folded_arrhenius_rows(dev, size, extra):
     w, _ = run(h, T, P, Y, chem.SPLIT_BF16, dev)
     assert np.all(w[:, base.n_species:] == 0.0)
     assert cell_err(w, ref).max() <= TOL[chem.SPLIT_BF16]
+
+
+@pytest.mark.parametrize("n", [3 * 4864 + 17, 70001])
+def test_fp32_intermediate_cells_per_warp(dev, n):
+    """Batch sizes for which the FP32 kernel gives each warp between 2 and 31 cells, with a
+    ragged last warp: sampled cells and the tail against the oracle."""
+    m, h, om = loaded("gri_53_325")
+    T, P, Y = states(m, "gri_53_325", n, seed=31)
+    T, P, Y = (as_prec(x, chem.FP32) for x in (T, P, Y))
+    w, _ = run(h, T, P, Y, chem.FP32, dev)
+    idx = np.concatenate([synth.subset_indices(n, 512), np.arange(n - 40, n)])
+    ref = O.source_term(om, T[idx], P[idx], Y[idx])
+    assert cell_err(w[idx], ref).max() <= TOL[chem.FP32]
