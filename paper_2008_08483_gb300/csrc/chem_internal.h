@@ -91,6 +91,13 @@ struct MechViewF64 {
     const double *tb_e;          // efficiency - 1 for listed species
     const double *invW;          // [ns] 1 / W_k
     double t_mid;
+    // as in MechViewF32: the records as slot-major 32-bit words (kind-grouped slots) and the
+    // species-major net stoichiometry with its species-to-lane schedule (shared arrays)
+    const uint32_t *rxn_t;
+    int32_t n_slots;
+    const int32_t *col_ptr, *col_rxn;
+    const float *col_nu;
+    const int32_t *lane_ptr, *lane_sp;
 };
 
 // Approximate-ANN ln K_c (Sec. 2.3, Eqs. 12-14): standardised ln T -> N_L hidden layers of

@@ -378,6 +378,14 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
         memcpy(w, &r32[order[sl]], sizeof(RxnF32));
         for (size_t q = 0; q < kW32; ++q) rt[q * order.size() + sl] = w[q];
     }
+    constexpr size_t kW64 = sizeof(RxnF64) / 4;
+    std::vector<uint32_t> rt64(kW64 * order.size(), 0);
+    for (size_t sl = 0; sl < order.size(); ++sl) {
+        if (order[sl] < 0) continue;
+        uint32_t w[kW64];
+        memcpy(w, &r64[order[sl]], sizeof(RxnF64));
+        for (size_t q = 0; q < kW64; ++q) rt64[q * order.size() + sl] = w[q];
+    }
     size_t o_ord = align(o_w + sizeof(double) * ns);
     size_t o_gptr = align(o_ord + sizeof(int32_t) * order.size());
     size_t o_gslot = align(o_gptr + sizeof(int32_t) * gptr.size());
@@ -388,7 +396,8 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
     size_t o_lptr = align(o_cnu + sizeof(float) * nce);
     size_t o_lsp = align(o_lptr + sizeof(int32_t) * lptr.size());
     size_t o_rt = align(o_lsp + sizeof(int32_t) * (lsp.size() ? lsp.size() : 1));
-    size_t total = align(o_rt + sizeof(uint32_t) * rt.size());
+    size_t o_rt64 = align(o_rt + sizeof(uint32_t) * rt.size());
+    size_t total = align(o_rt64 + sizeof(uint32_t) * rt64.size());
     std::vector<unsigned char> h(total, 0);
     memcpy(h.data() + o_r64, r64.data(), sizeof(RxnF64) * nr);
     memcpy(h.data() + o_r32, r32.data(), sizeof(RxnF32) * nr);
@@ -412,6 +421,7 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
     memcpy(h.data() + o_lptr, lptr.data(), sizeof(int32_t) * lptr.size());
     if (!lsp.empty()) memcpy(h.data() + o_lsp, lsp.data(), sizeof(int32_t) * lsp.size());
     memcpy(h.data() + o_rt, rt.data(), sizeof(uint32_t) * rt.size());
+    memcpy(h.data() + o_rt64, rt64.data(), sizeof(uint32_t) * rt64.size());
     if (!crxn.empty()) {
         memcpy(h.data() + o_crxn, crxn.data(), sizeof(int32_t) * crxn.size());
         memcpy(h.data() + o_cnu, cnu.data(), sizeof(float) * cnu.size());
@@ -464,6 +474,13 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
     m->v32.lane_sp = (const int32_t *)(base + o_lsp);
     m->v32.rxn_t = (const uint32_t *)(base + o_rt);
     m->v32.n_slots = (int32_t)order.size();
+    m->v64.rxn_t = (const uint32_t *)(base + o_rt64);
+    m->v64.n_slots = m->v32.n_slots;
+    m->v64.col_ptr = m->v32.col_ptr;
+    m->v64.col_rxn = m->v32.col_rxn;
+    m->v64.col_nu = m->v32.col_nu;
+    m->v64.lane_ptr = m->v32.lane_ptr;
+    m->v64.lane_sp = m->v32.lane_sp;
     m->vint.rxn = (const RxnInt *)(base + o_rint);
     m->vint.nasa = (const double *)(base + o_nasa);
     m->vint.W = (const double *)(base + o_w);

@@ -1,10 +1,10 @@
 // kern_simt.cu -- SIMT source-term kernels: FP64 and FP32 (double-float exponents).
 //
-// FP64: one thread per cell; all threads of a warp walk the reactions in the same order,
-// so every per-reaction table load is a broadcast and every branch on the reaction
-// kind is warp-uniform.  Per-cell species arrays live in shared memory laid out
-// [species][thread] (conflict-free, each thread owns one column).  FP32: one warp per cell
-// (see k_source_f32).
+// Both take one warp per cell (several consecutive cells per warp for large batches): the
+// lanes take the cell's species, then its reactions (one slot of the kind-grouped order per
+// lane, so kind branches are warp-uniform and record fields load coalesced from slot-major
+// word tables), then omega by species (a gather over the species-major net stoichiometry,
+// so results do not depend on an atomic order).
 //
 // Per reaction j (Eq. 4 in log space, Eqs. 5-11, Sec. 2.4):
 //   ln q_f = sum_k nu'_kj ln C_k + ln k_inf,j + ln(third-body or falloff factor)
@@ -17,89 +17,6 @@
 #include "chem_internal.h"
 
 namespace chem {
-
-// ---------------------------------------------------------------------------------------
-// FP64
-// ---------------------------------------------------------------------------------------
-
-template <int BLK>
-__global__ void __launch_bounds__(BLK)
-k_source_f64(MechViewF64 mv, int64_t n, const double *__restrict__ T,
-             const double *__restrict__ P, const double *__restrict__ Y, int64_t ldY,
-             double *__restrict__ om, int64_t ldO)
-{
-    extern __shared__ double smem64[];
-    const int ns = mv.ns, tid = threadIdx.x;
-    const int64_t i = (int64_t)blockIdx.x * BLK + tid;
-    if (i >= n) return;
-    double *sC = smem64 + tid;                 // C_k        [k * BLK]
-    double *sL = smem64 + ns * BLK + tid;      // ln C_k
-    double *sW = smem64 + 2 * ns * BLK + tid;  // omega_k
-    const double Ti = T[i], Pi = P[i];
-    const double *Yi = Y + i * ldY;
-    double sum = 0.0;
-    for (int k = 0; k < ns; ++k) {
-        double y = Yi[k];
-        y = (y > 0.0 ? y : 0.0) * mv.invW[k];
-        sC[k * BLK] = y;
-        sum += y;
-    }
-    const double ctot = Pi / (kR * Ti);
-    const double scale = sum > 0.0 ? ctot / sum : 0.0;
-    for (int k = 0; k < ns; ++k) {
-        double c = sC[k * BLK] * scale;
-        sC[k * BLK] = c;
-        sL[k * BLK] = log(c);                  // -inf for an absent species
-        sW[k * BLK] = 0.0;
-    }
-    const double lnT = log(Ti), invT = 1.0 / Ti, tau = Ti * 1e-3;
-    const int rg = Ti >= mv.t_mid ? 1 : 0;
-    for (int j = 0; j < mv.nr; ++j) {
-        const RxnF64 *R = mv.rxn + j;
-        const double lkinf = R->lnA + R->b * lnT - R->EoR * invT;
-        double lfac = 0.0;
-        const int kind = R->kind;
-        if (kind != 0) {
-            double M = ctot;                   // sum_k eff_k C_k = c_tot + sum_k (eff_k - 1) C_k
-            for (int t = R->tb_begin; t < R->tb_end; ++t) M += mv.tb_e[t] * sC[mv.tb_sp[t] * BLK];
-            if (kind == 1) {
-                lfac = log(M);
-            } else {
-                const double lk0 = R->low[0] + R->low[1] * lnT - R->low[2] * invT;
-                const double Pr = exp(lk0 - lkinf) * M;
-                if (Pr > 0.0) {
-                    lfac = log(Pr / (1.0 + Pr));
-                    if (kind == 3) {
-                        double Fc = R->troe[0] * exp(-Ti * R->troe[2]) +
-                                    R->troe[1] * exp(-Ti * R->troe[3]);
-                        if (R->troe[4] > 0.0) Fc += exp(-R->troe[4] * invT);
-                        const double lFc = log10(Fc);
-                        const double c = -0.4 - 0.67 * lFc, nn = 0.75 - 1.27 * lFc;
-                        const double x = log10(Pr) + c;
-                        const double f1 = x / (nn - 0.14 * x);
-                        lfac += lFc / (1.0 + f1 * f1) * 2.302585092994045684;
-                    }
-                } else {
-                    lfac = -INFINITY;
-                }
-            }
-        }
-        const double *kc = R->kc[rg];
-        const double lKc = kc[0] + kc[1] * lnT +
-                           tau * (kc[2] + tau * (kc[3] + tau * (kc[4] + tau * kc[5]))) +
-                           kc[6] * invT;
-        double sf = lkinf + lfac, sr = lkinf + lfac - lKc;
-        for (int t = 0; t < R->nf; ++t) sf += R->nuf[t] * sL[R->spf[t] * BLK];
-        for (int t = 0; t < R->nr; ++t) sr += R->nur[t] * sL[R->spr[t] * BLK];
-        const double qf = exp(sf);
-        const double qr = R->rev ? exp(sr) : 0.0;
-        const double qn = qf - qr;
-        for (int t = 0; t < R->nf; ++t) sW[R->spf[t] * BLK] -= R->nuf[t] * qn;
-        for (int t = 0; t < R->nr; ++t) sW[R->spr[t] * BLK] += R->nur[t] * qn;
-    }
-    double *oi = om + i * ldO;
-    for (int k = 0; k < ns; ++k) oi[k] = sW[k * BLK];
-}
 
 // ---------------------------------------------------------------------------------------
 // FP32 with double-float exponent assembly
@@ -210,6 +127,10 @@ struct RxnW {
     __device__ __forceinline__ float f(size_t b) const { return __uint_as_float(word(b)); }
     __device__ __forceinline__ int i(size_t b) const { return (int)word(b); }
     __device__ __forceinline__ df d2(size_t b) const { return mkdf(f(b), f(b + 4)); }
+    __device__ __forceinline__ double dbl(size_t b) const
+    {
+        return __hiloint2double((int)word(b + 4), (int)word(b));
+    }
     __device__ __forceinline__ int u16(size_t b) const
     {
         const uint32_t x = word(b);
@@ -437,6 +358,132 @@ k_source_f32(MechViewF32 mv, IntView iv, KcAnnView av, int64_t n, int cpw,
 }
 
 // ---------------------------------------------------------------------------------------
+// FP64
+// ---------------------------------------------------------------------------------------
+
+// One warp per cell, cpw cells per warp, as k_source_f32, in plain FP64 and natural-log
+// units: the lane-per-cell pass computes ln T, 1/T, tau, c_tot; per cell the lanes take the
+// species (C_k = c_tot z_k / sum z, ln C_k; -inf for an absent species), the reactions
+// (Arrhenius layer, third-body / falloff factor, the FP64 folded Gibbs polynomial of the
+// reaction's T range, exp of both sides) and omega by the species-major gather.
+constexpr int kF64Warps = 8;                   // warps per block
+constexpr int kCell64 = 6;                     // per-cell scalars kept in shared memory
+#define RXO64(field) offsetof(RxnF64, field)
+
+__global__ void __launch_bounds__(32 * kF64Warps)
+k_source_f64(MechViewF64 mv, IntView iv, int64_t n, int cpw, const double *__restrict__ T,
+             const double *__restrict__ P, const double *__restrict__ Y, int64_t ldY,
+             double *__restrict__ om, int64_t ldO)
+{
+    extern __shared__ double smem64[];
+    const int ns = mv.ns, nr = mv.nr, lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    const int per_warp = 32 * kCell64 + 2 * ns + nr;
+    double *cs = smem64 + (size_t)wb * per_warp;   // [cells][kCell64]
+    double *sC = cs + 32 * kCell64;                // C_k
+    double *sL = sC + ns;                          // ln C_k
+    double *sQ = sL + ns;                          // q_net per reaction
+    const int64_t i0 = ((int64_t)blockIdx.x * kF64Warps + wb) * cpw;
+    if (i0 >= n) return;
+    {
+        const int64_t i = i0 + lane;
+        if (lane < cpw && i < n) {
+            const double Ti = T[i], Pi = P[i];
+            double *c = cs + lane * kCell64;
+            c[0] = log(Ti);
+            c[1] = 1.0 / Ti;
+            c[2] = Ti * 1e-3;
+            c[3] = Pi / (kR * Ti);                 // c_tot
+            c[4] = Ti;
+            c[5] = Ti >= mv.t_mid ? 1.0 : 0.0;
+        }
+    }
+    __syncwarp();
+    for (int cc = 0; cc < cpw && i0 + cc < n; ++cc) {
+        const int64_t i = i0 + cc;
+        const double *c = cs + cc * kCell64;
+        const double lnT = c[0], invT = c[1], tau = c[2], ctot = c[3], Ti = c[4];
+        const int rg = c[5] != 0.0 ? 1 : 0;
+        // ---- species: C_k = c_tot z_k / sum_k z_k, ln C_k
+        double zs = 0.0;
+        for (int k = lane; k < ns; k += 32) {
+            const double y = Y[i * ldY + k];
+            const double z = (y > 0.0 ? y : 0.0) * mv.invW[k];
+            sC[k] = z;
+            zs += z;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) zs += __shfl_xor_sync(0xffffffffu, zs, off);
+        const double scale = zs > 0.0 ? ctot / zs : 0.0;
+        for (int k = lane; k < ns; k += 32) {
+            const double cv = sC[k] * scale;
+            sC[k] = cv;
+            sL[k] = log(cv);                       // -inf for an absent species
+        }
+        __syncwarp();
+        // ---- reactions, one slot per lane
+        for (int sl = lane; sl < mv.n_slots; sl += 32) {
+            const int j = iv.order[sl];
+            if (j < 0) continue;
+            const RxnW R{mv.rxn_t + sl, mv.n_slots};
+            const double lkinf = R.dbl(RXO64(lnA)) + R.dbl(RXO64(b)) * lnT -
+                                 R.dbl(RXO64(EoR)) * invT;          // Eq. 6
+            double lfac = 0.0;                     // Sec. 2.4
+            const int kind = R.i(RXO64(kind));
+            if (kind != 0) {
+                double M = ctot;                   // sum_k eff_k C_k = c_tot + sum_k (eff_k - 1) C_k
+                const int tb1 = R.i(RXO64(tb_end));
+                for (int t = R.i(RXO64(tb_begin)); t < tb1; ++t) M += mv.tb_e[t] * sC[mv.tb_sp[t]];
+                if (kind == 1) {
+                    lfac = log(M);
+                } else {
+                    const double lk0 = R.dbl(RXO64(low)) + R.dbl(RXO64(low) + 8) * lnT -
+                                       R.dbl(RXO64(low) + 16) * invT;
+                    const double Pr = exp(lk0 - lkinf) * M;
+                    if (Pr > 0.0) {
+                        lfac = log(Pr / (1.0 + Pr));
+                        if (kind == 3) {
+                            const size_t ot = RXO64(troe);
+                            const double t4 = R.dbl(ot + 32);
+                            double Fc = R.dbl(ot) * exp(-Ti * R.dbl(ot + 16)) +
+                                        R.dbl(ot + 8) * exp(-Ti * R.dbl(ot + 24));
+                            if (t4 > 0.0) Fc += exp(-t4 * invT);
+                            const double lFc = log10(Fc);
+                            const double c1 = -0.4 - 0.67 * lFc, nn = 0.75 - 1.27 * lFc;
+                            const double x = log10(Pr) + c1;
+                            const double f1 = x / (nn - 0.14 * x);
+                            lfac += lFc / (1.0 + f1 * f1) * 2.302585092994045684;
+                        }
+                    } else {
+                        lfac = -INFINITY;
+                    }
+                }
+            }
+            const size_t ok = RXO64(kc) + (size_t)rg * 56;     // Eqs. 9-11, folded
+            const double lKc = R.dbl(ok) + R.dbl(ok + 8) * lnT +
+                               tau * (R.dbl(ok + 16) +
+                                      tau * (R.dbl(ok + 24) + tau * (R.dbl(ok + 32) + tau * R.dbl(ok + 40)))) +
+                               R.dbl(ok + 48) * invT;
+            double sf = lkinf + lfac, sr = lkinf + lfac - lKc;
+            const int nf = R.i(RXO64(nf)), nrr = R.i(RXO64(nr));
+            for (int t = 0; t < nf; ++t) sf += R.u8(RXO64(nuf) + t) * sL[R.u16(RXO64(spf) + 2 * t)];
+            for (int t = 0; t < nrr; ++t) sr += R.u8(RXO64(nur) + t) * sL[R.u16(RXO64(spr) + 2 * t)];
+            const double qf = exp(sf);
+            const double qr = R.i(RXO64(rev)) ? exp(sr) : 0.0;
+            sQ[j] = qf - qr;
+        }
+        __syncwarp();
+        // ---- omega_k = sum_j (nu''_kj - nu'_kj) q_net,j (Eq. 2), reaction order
+        for (int a = mv.lane_ptr[lane]; a < mv.lane_ptr[lane + 1]; ++a) {
+            const int k = mv.lane_sp[a];
+            double w = 0.0;
+            for (int e = mv.col_ptr[k]; e < mv.col_ptr[k + 1]; ++e)
+                w += (double)mv.col_nu[e] * sQ[mv.col_rxn[e]];
+            om[i * ldO + k] = w;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------------
 
@@ -457,32 +504,34 @@ static chem_status smem_opt_in(K kern, std::atomic<uint32_t> &done_mask, const c
     return CHEM_OK;
 }
 
-template <int BLK, typename K, typename... A>
-static chem_status launch_rows(K kern, std::atomic<uint32_t> &mask, size_t smem, int64_t n,
-                               cudaStream_t s, const char *name, A... args)
-{
-    chem_status st = smem_opt_in(kern, mask, name);
-    if (st != CHEM_OK) return st;
-    kern<<<(unsigned)((n + BLK - 1) / BLK), BLK, smem, s>>>(args...);
-    g_launches.fetch_add(1);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return set_error(CHEM_ECUDA, "%s launch: %s", name, cudaGetErrorString(e));
-    return CHEM_OK;
-}
 
 chem_status launch_source_fp64(const chem_mech *m, int64_t n, const double *T, const double *P,
                                const double *Y, int64_t ldY, double *om, int64_t ldO,
                                cudaStream_t s)
 {
-    static std::atomic<uint32_t> m64{0}, m32{0};
-    const size_t per = 3 * sizeof(double) * (size_t)m->ns;
-    if (per * 64 <= 200 * 1024)
-        return launch_rows<64>(k_source_f64<64>, m64, per * 64, n, s, "fp64", m->v64, n, T, P,
-                               Y, ldY, om, ldO);
-    if (per * 32 <= kMaxDynSmem)
-        return launch_rows<32>(k_source_f64<32>, m32, per * 32, n, s, "fp64", m->v64, n, T, P,
-                               Y, ldY, om, ldO);
-    return set_error(CHEM_EUNSUPPORTED, "fp64: %d species exceed the SIMT kernel", m->ns);
+    static std::atomic<uint32_t> mask{0};
+    if (n <= 0) return CHEM_OK;
+    const size_t smem =
+        sizeof(double) * kF64Warps * (32 * (size_t)kCell64 + 2 * (size_t)m->ns + (size_t)m->nr);
+    if (smem > kMaxDynSmem)
+        return set_error(CHEM_EUNSUPPORTED, "fp64: %d species / %d reactions exceed the SIMT kernel",
+                         m->ns, m->nr);
+    chem_status st = smem_opt_in(k_source_f64, mask, "fp64");
+    if (st != CHEM_OK) return st;
+    int dev = 0, nsm = 0, blocks = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_source_f64, 32 * kF64Warps, smem);
+    const int64_t warps = (int64_t)(nsm > 0 ? nsm : 1) * (blocks > 0 ? blocks : 1) * kF64Warps;
+    int64_t cpw = (n + warps - 1) / warps;
+    cpw = cpw < 1 ? 1 : cpw > 32 ? 32 : cpw;
+    const int64_t per_block = cpw * kF64Warps;
+    k_source_f64<<<(unsigned)((n + per_block - 1) / per_block), 32 * kF64Warps, smem, s>>>(
+        m->v64, m->vint, n, (int)cpw, T, P, Y, ldY, om, ldO);
+    g_launches.fetch_add(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(CHEM_ECUDA, "fp64 launch: %s", cudaGetErrorString(e));
+    return CHEM_OK;
 }
 
 static size_t f32_warp_floats(const chem_mech *m, bool ann)
