@@ -19,8 +19,8 @@ constexpr double kR = 8.31446261815324e7;         // erg / (mol K)
 constexpr double kLog2e = 1.44269504088896340736;
 constexpr double kLn2 = 0.69314718055994530942;
 
-// One reaction for the FP64 SIMT path.  Natural-log units.  Every thread of a warp
-// reads the same record, so the loads are broadcasts.
+// One reaction for the FP64 paths (source term, derivatives, reactor).  Natural-log units.
+// The source-term kernel reads it from a slot-major copy (MechViewF64::rxn_t).
 struct alignas(16) RxnF64 {
     double lnA, b, EoR;          // ln k_inf = lnA + b ln T - EoR / T            (Eq. 6)
     double kc[2][7];             // ln K_c per T range on [1, ln T, tau, tau^2, tau^3, tau^4, 1/T],
