@@ -134,7 +134,10 @@ chem_status chem_mechanism_info(const chem_mech *mech, int32_t *n_species,
  * n_species..ldO-1 of omega are not written.  n_cells == 0 is a no-op.
  * Errors: CHEM_EINVAL (NULL pointers with n_cells > 0, n_cells < 0,
  * ldY/ldO < n_species, mechanism loaded on another device), CHEM_EUNSUPPORTED
- * (precision not built for this mechanism size), CHEM_ECUDA (launch failure).
+ * (precision not built for this mechanism size: CHEM_FP64 needs 2 n_species + n_reactions
+ * <= 3440, CHEM_FP32 5 n_species + n_reactions <= 6752; CHEM_SPLIT_BF16 at most 62 species,
+ * 64 third-body / falloff reactions of which 32 falloff, and tables that fit in shared
+ * memory), CHEM_ECUDA (launch failure).
  * Asynchronous on `stream`.
  */
 chem_status chem_source_term(const chem_mech *mech, int64_t n_cells, const void *T,
