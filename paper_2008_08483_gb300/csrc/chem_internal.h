@@ -150,6 +150,9 @@ struct chem_mech {
     chem::IntView vint;
     bool have_bf16;
     void *bf16;                  // split-BF16 tables (tensor-core path), see kern_bf16.cu
+    // resident warps of the SIMT source-term kernels on the mechanism's device (0: not yet
+    // queried): FP64, FP32, FP32 with the ln K_c network
+    std::atomic<int> simt_warps[3];
 };
 
 namespace chem {

@@ -505,6 +505,31 @@ static chem_status smem_opt_in(K kern, std::atomic<uint32_t> &done_mask, const c
 }
 
 
+// Resident warps of a kernel on the current device (SMs x blocks per SM x warps per block),
+// queried once per mechanism and path.
+template <typename K>
+static int64_t resident_warps(const chem_mech *m, int slot, K kern, int warps_per_block, size_t smem)
+{
+    int w = const_cast<chem_mech *>(m)->simt_warps[slot].load(std::memory_order_relaxed);
+    if (w <= 0) {
+        int dev = 0, nsm = 0, blocks = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, 32 * warps_per_block, smem);
+        w = (nsm > 0 ? nsm : 1) * (blocks > 0 ? blocks : 1) * warps_per_block;
+        const_cast<chem_mech *>(m)->simt_warps[slot].store(w, std::memory_order_relaxed);
+    }
+    return w;
+}
+
+// Cells per warp: 32 when the batch fills every resident warp 32 times over, else just
+// enough to cover the batch with the resident warps.
+static int cells_per_warp(int64_t n, int64_t warps)
+{
+    const int64_t cpw = (n + warps - 1) / warps;
+    return (int)(cpw < 1 ? 1 : cpw > 32 ? 32 : cpw);
+}
+
 chem_status launch_source_fp64(const chem_mech *m, int64_t n, const double *T, const double *P,
                                const double *Y, int64_t ldY, double *om, int64_t ldO,
                                cudaStream_t s)
@@ -518,16 +543,10 @@ chem_status launch_source_fp64(const chem_mech *m, int64_t n, const double *T, c
                          m->ns, m->nr);
     chem_status st = smem_opt_in(k_source_f64, mask, "fp64");
     if (st != CHEM_OK) return st;
-    int dev = 0, nsm = 0, blocks = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_source_f64, 32 * kF64Warps, smem);
-    const int64_t warps = (int64_t)(nsm > 0 ? nsm : 1) * (blocks > 0 ? blocks : 1) * kF64Warps;
-    int64_t cpw = (n + warps - 1) / warps;
-    cpw = cpw < 1 ? 1 : cpw > 32 ? 32 : cpw;
-    const int64_t per_block = cpw * kF64Warps;
+    const int cpw = cells_per_warp(n, resident_warps(m, 0, k_source_f64, kF64Warps, smem));
+    const int64_t per_block = (int64_t)cpw * kF64Warps;
     k_source_f64<<<(unsigned)((n + per_block - 1) / per_block), 32 * kF64Warps, smem, s>>>(
-        m->v64, m->vint, n, (int)cpw, T, P, Y, ldY, om, ldO);
+        m->v64, m->vint, n, cpw, T, P, Y, ldY, om, ldO);
     g_launches.fetch_add(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(CHEM_ECUDA, "fp64 launch: %s", cudaGetErrorString(e));
@@ -538,20 +557,6 @@ static size_t f32_warp_floats(const chem_mech *m, bool ann)
 {
     return 32 * (size_t)kCellScalars + 5 * (size_t)m->ns + (size_t)m->nr +
            (ann ? 2 * (size_t)kAnnMaxHidden : 0);
-}
-
-// Cells per warp: 32 when the batch fills every resident warp 32 times over, else just
-// enough to cover the batch with the resident warps.
-template <typename K>
-static int f32_cells_per_warp(K kern, size_t smem, int64_t n)
-{
-    int dev = 0, nsm = 0, blocks = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, 32 * kF32Warps, smem);
-    const int64_t warps = (int64_t)(nsm > 0 ? nsm : 1) * (blocks > 0 ? blocks : 1) * kF32Warps;
-    const int64_t cpw = (n + warps - 1) / warps;
-    return (int)(cpw < 1 ? 1 : cpw > 32 ? 32 : cpw);
 }
 
 template <bool ANN>
@@ -567,7 +572,8 @@ static chem_status launch_f32(const chem_mech *m, const KcAnnView &av, int64_t n
                          name, m->ns, m->nr);
     chem_status st = smem_opt_in(k_source_f32<ANN>, mask, name);
     if (st != CHEM_OK) return st;
-    const int cpw = f32_cells_per_warp(k_source_f32<ANN>, smem, n);
+    const int cpw =
+        cells_per_warp(n, resident_warps(m, ANN ? 2 : 1, k_source_f32<ANN>, kF32Warps, smem));
     const int64_t per_block = (int64_t)cpw * kF32Warps;
     k_source_f32<ANN><<<(unsigned)((n + per_block - 1) / per_block), 32 * kF32Warps, smem, s>>>(
         m->v32, m->vint, av, n, cpw, T, P, Y, ldY, om, ldO);
