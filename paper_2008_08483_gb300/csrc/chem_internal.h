@@ -114,7 +114,6 @@ struct KcAnnView {
 
 struct MechViewF32 {
     int ns, nr;
-    const RxnF32 *rxn;
     const SpecF32 *spec;
     const uint16_t *tb_sp;
     const float *tb_e;

@@ -301,8 +301,7 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
     // one device blob
     auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t o_r64 = 0;
-    size_t o_r32 = align(o_r64 + sizeof(RxnF64) * nr);
-    size_t o_s32 = align(o_r32 + sizeof(RxnF32) * nr);
+    size_t o_s32 = align(o_r64 + sizeof(RxnF64) * nr);
     size_t o_tbsp = align(o_s32 + sizeof(SpecF32) * ns);
     size_t ntb = tb_sp.size() ? tb_sp.size() : 1;
     size_t o_tbe64 = align(o_tbsp + sizeof(uint16_t) * ntb);
@@ -400,7 +399,6 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
     size_t total = align(o_rt64 + sizeof(uint32_t) * rt64.size());
     std::vector<unsigned char> h(total, 0);
     memcpy(h.data() + o_r64, r64.data(), sizeof(RxnF64) * nr);
-    memcpy(h.data() + o_r32, r32.data(), sizeof(RxnF32) * nr);
     memcpy(h.data() + o_s32, s32.data(), sizeof(SpecF32) * ns);
     if (!tb_sp.empty()) {
         memcpy(h.data() + o_tbsp, tb_sp.data(), sizeof(uint16_t) * tb_sp.size());
@@ -461,7 +459,6 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
     m->v64.t_mid = d->t_mid;
     m->v32.ns = ns;
     m->v32.nr = nr;
-    m->v32.rxn = (const RxnF32 *)(base + o_r32);
     m->v32.spec = (const SpecF32 *)(base + o_s32);
     m->v32.tb_sp = (const uint16_t *)(base + o_tbsp);
     m->v32.tb_e = (const float *)(base + o_tbe32);
