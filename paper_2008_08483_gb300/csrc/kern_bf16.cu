@@ -1,48 +1,48 @@
-// kern_bf16.cu -- split-BF16 source term on tcgen05 tensor cores (sm_103a).
+// kern_bf16.cu -- split 16-bit source term on tcgen05 tensor cores (sm_103a).
 //
-// Per tile of 128 cells (one cell per tensor-memory lane), for reaction chunks of RC = 64:
-//   contraction 1 (Eqs. 4, 11): S = log2 X . [nu' | nu''] (M=128, N=2 RC=128, K=NSP), and
-//       the reverse half also accumulates G . nu, the Gibbs layer of Eq. 11 (G_k = g_k/(RT)
-//       log2 e - log2(p_ref/(RT)), per cell and species, three BF16 terms in tensor memory;
-//       nu is contraction 2's table read as an MN-major operand), so that S'' + log2 k_f =
-//       sum_k nu''_k log2 C_k + log2 k_r
-//       A = log2 X in tensor memory as three BF16 terms (hi + mid + lo); the extra
-//       column NSP_extra = log2 c_tot carries the reaction orders (and the third-body
-//       c_tot factor), so S = sum_k nu_k log2 C_k (+ log2 c_tot for third-body).
-//       B = the small-integer stoichiometric matrices, exact in BF16, in shared memory.
-//       When nine padding columns are free (NSP >= ns + 11), they carry the Arrhenius layer
-//       (Eq. 6) as well: features [1, log2 T, 1/T] (three BF16 terms each) against the
-//       coefficients [log2 A, b, -E/R log2 e] (three BF16 rows each), so that S' = log2 q_f and
-//       S'' = log2 q_r directly; an irreversible reaction's reverse column and an empty slot
-//       carry a bias of -1e4 (2^S = 0).
-//   epilogue (FP32, one thread per cell): without the folded Arrhenius layer, log2 k_f
-//       (Eq. 6) added to both halves; third-body / falloff factors (Sec. 2.4),
-//       q = 2^S' - 2^S'', q_net = q_f - q_r (Eq. 3), split into two BF16 terms written to
-//       tensor memory.
-//   contraction 2 (Eq. 2):  omega += q_net . nu^T          (M=128, N=NSP, K=RC)
-//   contraction 0 (Sec. 2.4), once per tile, issued after chunk 0's contraction 1 (before
-//       it when chunk 0 itself reads multipliers): the third-body sums
-//       sum_k (eff_jk - 1) z_k of the reactions that need them (M=128, N=64, K=NSP), A = z as
-//       two BF16 terms in contraction 2's operand columns (free until chunk 0's q_net), B =
-//       eff - 1 as two BF16 terms (hi.hi + hi.lo + lo.hi), into the multiplier columns.
-// omega accumulates in tensor memory across the chunks and is written once per tile.
-// Contraction 1 of chunk c + 1 runs while the epilogue works on chunk c (it starts as soon
-// as chunk c's S has been read out), contraction 2 of chunk c as soon as its q_net is in.
+// Per tile of 128 cells (one cell per tensor-memory lane), for reaction chunks of RC = 48
+// (the last chunk holds the remaining 16..48 reactions):
+//   contraction 1 (Eqs. 4, 6): S = A1 . [nu' | nu''] (M = 128, N = 2 RC, K = NSP), A1 =
+//       [log2 z_k (k < ns), log2 c_tot, log2 c_tot - log2 sum_k z_k, Arrhenius features]
+//       as two FP16 terms (hi + lo, 22 significant bits) in tensor memory.  The B rows are
+//       the small-integer stoichiometric coefficients (exact in FP16), the third-body flag,
+//       the reaction orders and the Arrhenius coefficients [log2 A, b, -E/R log2 e / 1000] on
+//       the features [1, log2 T, 1000/T] (three FP16 rows each), so that S' = log2 q_f and
+//       the reverse half = sum_k nu''_k log2 C_k + log2 k_f; an irreversible reaction's
+//       reverse column and an empty slot carry a bias of -1e4 (2^S = 0).
+//   Gibbs layer (Eqs. 8-11), folded per reaction: the reverse half also accumulates
+//       -log2 K_c = sum_m c_mj phi_m(T) over 14 temperature features (NASA-7 terms
+//       [1, log2 T, tau, tau^2, tau^3, tau^4, 1/tau], tau = T/1000, of the cell's
+//       temperature range, the other range's seven zero), with c = nu^T . (per-species
+//       coefficients) assembled in FP64 at load.  Features and coefficients are both two
+//       FP16 terms; hi.hi, hi.lo and lo.hi are issued.  M = 128, N = RC, K = 16 per MMA.
+//   epilogue (FP32, one thread per cell): q = 2^S' - 2^S'' (Eqs. 3-7); third-body factor
+//       M / c_tot and falloff factor Pr / (1 + Pr) F (Sec. 2.4, the latter folded into the
+//       exponents); q_net split into two BF16 terms (its range needs BF16's exponent)
+//       written to one of two tensor-memory buffers.
+//   contraction 2 (Eq. 2): omega += q_net . nu^T (M = 128, N = NSP, K = RC, BF16), in
+//       tensor memory across the chunks; written once per tile.
+//   contraction 0 (Sec. 2.4), once per tile: the third-body sums sum_k (eff_jk - 1) z_k of
+//       the reactions that need them (M = 128, N = FCN, K = NSP), A = z as two BF16 terms
+//       in the omega columns (free until contraction 2 of chunk 0), B = eff - 1 as two BF16
+//       terms (hi.hi + hi.lo + lo.hi), into columns of their own read by the chunks that
+//       hold those reactions.
 //
-// Tiles overlap: the next tile's prologue runs as soon as every contraction 1 of the current
-// tile has completed (A1FREE), before the current tile's omega is read out of tensor memory
-// and stored, so that the next tile's contraction 1 starts meanwhile.
-// Warp roles (608 threads): warp 0 bulk-copies the T, P, Y tile into shared memory;
-// warp 1 owns tensor memory and issues contractions 0 and 1 from one thread, warp 18
-// contraction 2 (an MMA issue blocks while the tensor pipe is busy, so one issuer would sit
-// on contraction 2 of chunk c while chunk c + 1's S has been read out); warps 2-17 form four
-// epilogue warpgroups, warpgroup g taking reactions 16 g .. 16 g + 15 of every chunk (warp
-// w reaches tensor-memory lanes 32 (w % 4) .. 32 (w % 4) + 31).  Reactions with a third-body
-// or falloff factor sit in the first 8 slots of the last chunks' quarters (falloff ones in
-// slots 0..3); the epilogue turns contraction 0's sums into M / c_tot and, for the falloff
-// slots, into Pr / (1 + Pr) F where the quarter's rates are formed.
+// S and q_net have two tensor-memory buffers each: contraction 1 of chunk c + 1 runs while
+// the epilogue works on chunk c, and the epilogue writes q_net of chunk c + 1 while
+// contraction 2 of chunk c waits in the tensor pipe.  The next tile's operands are written
+// during the last chunk (every contraction 1 of the current tile has completed by then), so
+// its first contractions 1 run while the current omega is read out.
+// Warp roles (480 threads): warp 0 bulk-copies the T, P, Y tile into shared memory;
+// warp 1 owns tensor memory and issues contractions 1 from one thread, warp 14 issues
+// contractions 0 and 2; warps 2-13 form three epilogue warpgroups, warpgroup g taking
+// reactions 16 g .. 16 g + 15 of every chunk (warp w reaches tensor-memory lanes
+// 32 (w % 4) .. 32 (w % 4) + 31).  Reactions with a third-body or falloff factor sit in the
+// first 8 slots of "multiplier shares" (falloff ones in slots 0..3), each with 8 columns of
+// third-body sums.
 // Every mbarrier wait is bounded: on timeout the kernel records an error code in the
 // mechanism's device status word and all roles wind down.
+#include <cuda_fp16.h>
 #include <math.h>
 #include <string.h>
 
@@ -54,34 +54,25 @@
 
 namespace chem {
 
-constexpr int RC = 64;                 // reactions per chunk
-constexpr int RH = RC / 4;             // reactions per warpgroup and chunk
-constexpr int NQ = RC / RH;            // warpgroups (chunk quarters)
+constexpr int RC = 48;                 // reactions per chunk
+constexpr int RH = 16;                 // reactions per warpgroup and chunk
+constexpr int NQ = RC / RH;            // epilogue warpgroups (chunk shares)
 constexpr int kEpiWarp0 = 2;           // first epilogue warp
-constexpr int kEpiWarps = 16;
-constexpr int kMma2Warp = kEpiWarp0 + kEpiWarps;   // issues contraction 2
+constexpr int kEpiWarps = 4 * NQ;
+constexpr int kMma2Warp = kEpiWarp0 + kEpiWarps;   // issues contractions 0 and 2
 constexpr int kThreads = 32 * (kMma2Warp + 1);
 constexpr uint32_t kTmemCols = 512;
 constexpr float kLog2Floor = -1000.0f; // log2 X of an absent species: 2^x underflows to 0
 constexpr float kDead = -1.0e4f;       // log2 of a rate constant that is zero
-constexpr int kFoldRows = 9;           // K rows of the folded Arrhenius layer: 3 features x 3 terms
+constexpr int kArrRows = 9;            // K rows of the Arrhenius layer: 3 features x 3 terms
+constexpr int kGibK = 32;              // K of the Gibbs contraction: 2 coefficient terms x 16
+constexpr int kMaxFc = 64;             // third-body / falloff columns (8 per multiplier share)
+// what a contraction-1 column holds: log2 z_k, log2 c_tot, the normalisation, the Arrhenius
+// features 1, log2 T, 1000/T, or nothing
+enum { kColSpecies, kColLgct, kColNorm, kColOne, kColLg2T, kColItau, kColZero };
 
-constexpr int kFacCols = 64;           // multiplier columns: 8 per quarter holding such reactions
-
-// per-reaction coefficients, copied to shared memory with the stoichiometric tables (read by
-// the epilogue when the Arrhenius layer is not folded into contraction 1)
-struct alignas(16) CoefS {
-    float4 kf;         // Arrhenius layer (Eq. 6): log2 k_inf = x + y log2 T + z / T;
-                       // w = 1 for a reversible reaction, 0 otherwise (Sec. 2.4)
-};
-// per species: G_k = g_k/(RT) log2 e - log2(p_ref/(RT)) on [1, log2 T, tau, tau^2, tau^3,
-// tau^4, 1/T] (tau = T/1000), one set per temperature range (Eq. 10 with the standard
-// concentration folded into the bias as in Eq. 11)
-struct alignas(16) GibbsS {
-    float c[2][8];
-};
-// slot 0..3 of a chunk quarter holding third-body / falloff reactions: the falloff layer
-// (Sec. 2.4), or neutral values with kf.w = 0 (the multiplier is then M / c_tot)
+// Falloff layer of slot 0..3 of a multiplier share (Sec. 2.4); neutral records (kf.w = 0)
+// leave the third-body factor M / c_tot.
 struct alignas(16) FallQ {
     float4 kf;         // log2 k_inf = x + y log2 T + z / T; w = 1 for a falloff reaction
     float4 k0;         // log2 k0 = x + y log2 T + z / T
@@ -89,11 +80,17 @@ struct alignas(16) FallQ {
     float4 t2;         // x = log2(e) T** (absent: 1e30, the term underflows to zero)
 };
 
+// per chunk share (chunk, warpgroup): its rank among the multiplier shares (-1: none; its
+// columns are 8 rank .. 8 rank + 7 of the third-body sums) and how many of its slots 0..3
+// hold falloff reactions
+struct QInfo {
+    int8_t rank, nfall, pad0, pad1;
+};
+
 struct Bf16Tables {
-    int nsp, nch, fac_chunk0;
-    bool fold;                                   // Arrhenius layer folded into contraction 1
-    size_t b1_bytes, blob_bytes;
-    uint32_t o_b2, o_e, o_coef, o_hmask, o_fq, o_gib;   // offsets from the blob start
+    int nsp, nch, rct, fcn;
+    size_t blob_bytes;
+    uint32_t o_bg, o_b2, o_e, o_qi, o_fq;   // offsets from the blob start
     void *d_blob;
     const uint16_t *btab;     // one contiguous block copied to shared memory
     const float *invW;
@@ -104,8 +101,7 @@ struct Bf16Params {
     const float *T, *P, *Y;
     float *om;
     int64_t n, ldY, ldO;
-    int ns, nch, ntiles;
-    int fac_chunk0;            // chunk 0 holds third-body / falloff reactions
+    int ns, nch, rct, fcn, ntiles;
     int stage_y;               // T, P, Y tiles staged in shared memory (the Y buffer then also
                                // stages omega on its way out)
     int bulk_out;              // omega rows contiguous (ldO == ns) and 16-byte aligned
@@ -114,21 +110,21 @@ struct Bf16Params {
     const float *invW;
     float t_mid, lg2R;
     int *status;
-    // shared-memory layout (byte offsets from the 1024-aligned base); the copied block
-    // holds B1, B2, the efficiency table, coefficients, quarter masks, falloff records and
-    // the Gibbs layer
-    uint32_t o_b2, o_e, o_coef, o_hmask, o_fq, o_gib, o_y, o_t, o_p, o_iw, o_psum, o_bar;
+    // shared-memory layout (byte offsets from the 1024-aligned base); the copied block holds
+    // B1, the Gibbs table, B2, the efficiency table, the share records and the falloff
+    // records
+    uint32_t o_bg, o_b2, o_e, o_qi, o_fq, o_y, o_t, o_p, o_iw, o_psum, o_bar;
 };
 
 enum {
-    BAR_BTAB, BAR_YFULL, BAR_YEMPTY, BAR_A1FULL, BAR_D1FULL, BAR_D1EMPTY, BAR_A2FULL, BAR_A2EMPTY,
-    BAR_D2FULL, BAR_D2EMPTY, BAR_XREADY, BAR_A1FREE, BAR_DRAIN, BAR_WREADY, BAR_ZFREE, BAR_COUNT
+    BAR_BTAB, BAR_YFULL, BAR_YEMPTY, BAR_A1FULL, BAR_D1FULL0, BAR_D1FULL1, BAR_D1EMPTY0,
+    BAR_D1EMPTY1, BAR_ZFULL, BAR_FCFULL, BAR_A2FULL0, BAR_A2FULL1, BAR_A2EMPTY0, BAR_A2EMPTY1,
+    BAR_D2FULL, BAR_XREADY, BAR_WREADY, BAR_DRAIN, BAR_COUNT
 };
 
 struct SmemCtl {
     uint32_t tmem_base;
     volatile int abort;
-    volatile int mma1_issued;   // contractions 1 issued so far (an ordering hint only)
 };
 
 // Bounded mbarrier wait: gives up after ~2^31 cycles (about a second), or as soon as
@@ -151,77 +147,60 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, SmemCtl 
 
 template <int NSP>
 struct Cols {                                     // tensor-memory column map
-    static constexpr uint32_t A1 = 0;             // log2 z: 3 splits x NSP/2 columns
-    static constexpr uint32_t AG = ((3 * NSP / 2 + 31) / 32) * 32;   // G: 3 splits x NSP/2
-    static constexpr uint32_t D1 = AG + ((3 * NSP / 2 + 31) / 32) * 32;   // 2 RC: S', S''
-    static constexpr uint32_t A2 = D1 + 2 * RC;   // 2 splits x RC/2
-    static constexpr uint32_t D2 = A2 + RC;       // NSP columns
-    static constexpr uint32_t FC = D2 + NSP;      // third-body sums (contraction 0)
-    static_assert(FC + kFacCols <= kTmemCols, "tensor memory over budget");
+    static constexpr uint32_t A1 = 0;             // contraction-1 operand: 2 terms x NSP/2
+    static constexpr uint32_t AG = NSP;           // Gibbs features: 2 terms x 8
+    static constexpr uint32_t S0 = ((AG + 16 + 31) / 32) * 32;   // two S buffers of 2 RC
+    static constexpr uint32_t A2 = S0 + 4 * RC;   // two q_net buffers: 2 terms x RC/2 each
+    static constexpr uint32_t FC = A2 + 2 * RC;   // third-body sums (contraction 0)
+    static constexpr uint32_t D2 = FC + kMaxFc;   // omega; z (2 terms x NSP/2) at tile start
+    static_assert(D2 + NSP <= kTmemCols, "tensor memory over budget");
 };
 
 // Per-cell features kept in registers by every epilogue thread.
 struct CellF {
-    float lg2T, invT, tau, tau2, lgct, inv_sum;
-    int rg;
+    float lg2T, invT, itau, T, lgct, inv_sum;
 };
 
-// Shared-memory view of the per-reaction tables.
-struct SmemTabs {
-    const CoefS *coef;
-    const uint32_t *hmask;     // per chunk quarter: nonzero if it holds third-body / falloff
-                               // reactions (in its first 8 slots)
-    const int *fbase;          // per chunk quarter: its first multiplier column (8 each)
-    const FallQ *fq;           // per such quarter, slots 0..3
-};
-
-// Multipliers of q_net for slots 0..3 of a quarter holding third-body / falloff reactions
-// (Sec. 2.4), from s = M / c_tot: Pr / (1 + Pr) F for a falloff reaction (F = 1 for
-// Lindemann, the Troe form otherwise), s itself for the others.  Branch-free over the four
-// slots so that their dependency chains interleave.
+// Factors of slots 0..3 of a multiplier share from s = M / c_tot (Sec. 2.4): a falloff
+// slot (u < nfall) gets fac = log2(Pr / (1 + Pr) F) (F = 1 for Lindemann, the Troe form
+// otherwise), added to both exponents, and mul = 1; the others keep fac = 0, mul = s.
 __device__ __forceinline__ void falloff4(const FallQ *F, const float (&s)[8], const CellF &c,
-                                         float (&out)[4])
+                                         int nfall, float (&fac)[4], float (&mul)[4])
 {
-    const float Tn = c.tau * 1000.0f;
+    constexpr float kLog10_2 = 0.30102999566398120f;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        const float4 kf = F[u].kf, k0 = F[u].k0, tr = F[u].troe;
-        const float t2 = F[u].t2.x;
-        const float lkf = fmaf(kf.z, c.invT, fmaf(kf.y, c.lg2T, kf.x));
-        const float lk0 = fmaf(k0.z, c.invT, fmaf(k0.y, c.lg2T, k0.x));
-        const float lpr = lk0 - lkf + c.lgct + tc::lg2(fmaxf(s[u], 1e-30f));   // log2 Pr
-        float fac = -tc::lg2(1.0f + tc::ex2(-lpr));               // log2(Pr / (1 + Pr))
-        const float fc = tr.x * tc::ex2(-Tn * tr.z) + tr.y * tc::ex2(-Tn * tr.w) +
-                         tc::ex2(-t2 * c.invT);
-        const float lfc = tc::lg2(fc);                             // log2 F_cent
-        const float l10 = lfc * 0.30102999566398120f;
-        const float cc = -0.4f - 0.67f * l10, nn = 0.75f - 1.27f * l10;
-        const float x = lpr * 0.30102999566398120f + cc;
-        const float f1 = __fdividef(x, nn - 0.14f * x);
-        fac += __fdividef(lfc, 1.0f + f1 * f1);                   // log2 F (Troe)
-        out[u] = kf.w != 0.0f ? tc::ex2(fac) : s[u];
+        fac[u] = 0.0f;
+        mul[u] = s[u];
+        if (u < nfall) {                                          // warp-uniform
+            const float4 kf = F[u].kf, k0 = F[u].k0, tr = F[u].troe;
+            const float t2 = F[u].t2.x;
+            const float lkf = fmaf(kf.z, c.invT, fmaf(kf.y, c.lg2T, kf.x));
+            const float lk0 = fmaf(k0.z, c.invT, fmaf(k0.y, c.lg2T, k0.x));
+            const float lpr = lk0 - lkf + c.lgct + tc::lg2(fmaxf(s[u], 1e-30f));   // log2 Pr
+            float f = -tc::lg2(1.0f + tc::ex2(-lpr));                 // log2(Pr / (1 + Pr))
+            const float fc = tr.x * tc::ex2(-c.T * tr.z) + tr.y * tc::ex2(-c.T * tr.w) +
+                             tc::ex2(-t2 * c.invT);
+            const float lfc = tc::lg2(fc);                            // log2 F_cent
+            const float l10 = lfc * kLog10_2;
+            const float cc = -0.4f - 0.67f * l10, nn = 0.75f - 1.27f * l10;
+            const float x = fmaf(lpr, kLog10_2, cc);
+            const float dd = fmaf(-0.14f, x, nn);
+            // log2 F = log2 F_cent / (1 + (x / dd)^2)
+            f += lfc * __fdividef(dd * dd, fmaf(dd, dd, x * x));
+            fac[u] = f;
+            mul[u] = 1.0f;
+        }
     }
 }
 
-// q_net of one reaction for one cell before any third-body / falloff factor (Eqs. 3-7),
-// log2 domain: the contraction already holds sum nu' log2 C and sum nu'' log2 C - log2 K_c.
-// Branch-free: kf.w zeroes the reverse rate of an irreversible reaction, and an empty slot's
-// log2 k_f of -1e4 with S = 0 gives q = 0.
-__device__ __forceinline__ float rate_plain(const CoefS *C, float sf, float sr, const CellF &c)
+// two values -> two packed FP16x2 words (hi, lo terms; value a in the low halves)
+__device__ __forceinline__ void split2h(float a, float b, uint32_t &h, uint32_t &l)
 {
-    const float4 kf = C->kf;
-    const float lkf = fmaf(kf.z, c.invT, fmaf(kf.y, c.lg2T, kf.x));
-    return fmaf(-kf.w, tc::ex2(sr + lkf), tc::ex2(sf + lkf));
-}
-
-// two values -> three packed BF16x2 words (hi, mid, lo terms; value a in the low halves)
-__device__ __forceinline__ void split3x2(float a, float b, uint32_t &h, uint32_t &m, uint32_t &l)
-{
-    h = tc::pack_bf16x2(a, b);
-    const float a1 = a - __uint_as_float(h << 16), b1 = b - __uint_as_float(h & 0xFFFF0000u);
-    m = tc::pack_bf16x2(a1, b1);
-    const float a2 = a1 - __uint_as_float(m << 16), b2 = b1 - __uint_as_float(m & 0xFFFF0000u);
-    l = tc::pack_bf16x2(a2, b2);
+    h = tc::pack_f16x2(a, b);
+    float ha, hb;
+    tc::unpack_f16x2(h, ha, hb);
+    l = tc::pack_f16x2(a - ha, b - hb);
 }
 
 // two values -> two packed BF16x2 words (hi, lo terms; value a in the low halves)
@@ -231,64 +210,59 @@ __device__ __forceinline__ void split2x2(float a, float b, uint32_t &h, uint32_t
     l = tc::pack_bf16x2(a - __uint_as_float(h << 16), b - __uint_as_float(h & 0xFFFF0000u));
 }
 
-__device__ __forceinline__ void split3(float x, uint16_t &h, uint16_t &m, uint16_t &l)
-{
-    // x = hi + mid + lo with each term the nearest BF16 of the remaining residual
-    const uint32_t ph = tc::pack_bf16x2(x, 0.0f) & 0xFFFFu;
-    const float r1 = x - __uint_as_float(ph << 16);
-    const uint32_t pm = tc::pack_bf16x2(r1, 0.0f) & 0xFFFFu;
-    const float r2 = r1 - __uint_as_float(pm << 16);
-    const uint32_t pl = tc::pack_bf16x2(r2, 0.0f) & 0xFFFFu;
-    h = (uint16_t)ph;
-    m = (uint16_t)pm;
-    l = (uint16_t)pl;
-}
-
-template <int NSP, bool FOLD>
+template <int NSP>
 __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
 {
     using CL = Cols<NSP>;
-    constexpr int SQ = NSP / 4;                   // species columns per warpgroup
+    // the prologue, z and omega columns are handled in blocks of 8, block i by warpgroup
+    // i % NQ
+    constexpr int NB = NSP / 8;
+    constexpr int BPW = (NB + NQ - 1) / NQ;       // blocks per warpgroup, at most
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned base, offset on the shared array itself so that every access below
     // stays a shared-memory access (an integer round trip would make them generic)
     unsigned char *sm = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
     const uint32_t sbase = tc::smem_u32(sm);
-    SmemTabs tabs;
-    tabs.coef = (const CoefS *)(sm + p.o_coef);
-    tabs.hmask = (const uint32_t *)(sm + p.o_hmask);
-    tabs.fbase = (const int *)(tabs.hmask + NQ * p.nch);
-    tabs.fq = (const FallQ *)(sm + p.o_fq);
-    const GibbsS *gib = (const GibbsS *)(sm + p.o_gib);
+    const QInfo *qinfo = (const QInfo *)(sm + p.o_qi);
+    const FallQ *fallq = (const FallQ *)(sm + p.o_fq);
     float *Ys = (float *)(sm + p.o_y);
     float *Ts = (float *)(sm + p.o_t);
     float *Ps = (float *)(sm + p.o_p);
-    float *Ws = (float *)(sm + p.o_y);            // omega [128][ns], in the Y buffer between
-                                                  // the next tile's prologue and its reload
-    float *iW = (float *)(sm + p.o_iw);
-    float *Psum = (float *)(sm + p.o_psum);      // [4][128] partial sums of z_k per warpgroup
+    float *Ws = (float *)(sm + p.o_y);            // omega [128][ns], in the Y buffer once the
+                                                  // next tile's prologue has read it
+    float *iW = (float *)(sm + p.o_iw);          // [NSP] 1 / W_k, zero past the species
+    int *ccode = (int *)(iW + NSP);               // [NSP] what each contraction-1 column holds
+    float *zrow = (float *)(ccode + NSP);         // [NSP] zeros: the Y row of a cell past n
+    float *Psum = (float *)(sm + p.o_psum);      // [NQ][128] partial sums of z_k
     uint64_t *bars = (uint64_t *)(sm + p.o_bar);
     SmemCtl *ctl = (SmemCtl *)(bars + BAR_COUNT);
     auto BAR = [&](int i) { return tc::smem_u32(bars + i); };
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        const uint32_t cnt[BAR_COUNT] = {1, 1, 16, 16, 1, 16, 16, 1, 1, 16, 16, 1, 2, 16, 1};
+        constexpr uint32_t E = kEpiWarps;
+        const uint32_t cnt[BAR_COUNT] = {1, 1, E, E, 1, 1, E, E, E, 1, E, E, 1, 1, 1, E, E, 2};
         for (int i = 0; i < BAR_COUNT; ++i) tc::mbar_init(BAR(i), cnt[i]);
         tc::mbar_fence_init();
         ctl->abort = 0;
-        ctl->mma1_issued = 0;
     }
-    for (int k = tid; k < p.ns; k += kThreads) iW[k] = p.invW[k];
     if (warp == 1) {
         tc::tmem_alloc(tc::smem_u32(&ctl->tmem_base), kTmemCols);
         tc::tmem_relinquish();
+    }
+    for (int k = tid; k < NSP; k += kThreads) {
+        iW[k] = k < p.ns ? p.invW[k] : 0.0f;
+        zrow[k] = 0.0f;
+        const int a = k - p.ns - 2;
+        ccode[k] = k < p.ns ? kColSpecies : k == p.ns ? kColLgct : k == p.ns + 1 ? kColNorm
+                 : (a >= 0 && a < kArrRows) ? kColOne + a / 3 : kColZero;
     }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = ctl->tmem_base;
     const int64_t n = p.n;
+    const int nch = p.nch;
 
     if (warp == 0) {
         // ------------------------------------------------------------- tile loader
@@ -322,101 +296,84 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
     } else if (warp == 1 || warp == kMma2Warp) {
         // ------------------------------------------------------------- MMA issuers
         if (lane == 0) {
-            constexpr uint32_t id1 = tc::idesc_bf16_f32(128, 2 * RC);
             constexpr uint32_t id2 = tc::idesc_bf16_f32(128, NSP);
-            constexpr uint32_t id0 = tc::idesc_bf16_f32(128, kFacCols);
-            const uint32_t b1 = sbase, b2 = sbase + p.o_b2, be = sbase + p.o_e;
-            uint32_t u_d1 = 0, u_a2 = 0;        // contractions 1 and 2 issued so far
+            const uint32_t b1 = sbase, bg = sbase + p.o_bg, b2 = sbase + p.o_b2,
+                           be = sbase + p.o_e;
             bool ok = wait_bar(BAR(BAR_BTAB), 0, ctl, p.status, 2);
-            constexpr uint32_t id1g = tc::idesc_bf16_f32(128, RC, true);
-            auto issue_mma1 = [&](int c) {
-                const uint32_t bc = b1 + (uint32_t)c * (2 * RC * NSP * 2);
-#pragma unroll
-                for (int s = 0; s < 3; ++s)
-#pragma unroll
-                    for (int kk = 0; kk < NSP / 16; ++kk)
-                        tc::mma_ts(tmem + CL::D1, tmem + CL::A1 + s * (NSP / 2) + kk * 8,
-                                   tc::sdesc_noswz(bc + kk * 256, 128, (NSP / 8) * 128), id1,
-                                   (s | kk) != 0);
-                // Gibbs layer into the reverse half: B = nu of contraction 2 ([species][reaction]
-                // core matrices) read MN-major: K step = 2 species core rows, lbo = K stride
-                const uint32_t bg = b2 + (uint32_t)c * (NSP * RC * 2);
-#pragma unroll
-                for (int s = 0; s < 3; ++s)
-#pragma unroll
-                    for (int kk = 0; kk < NSP / 16; ++kk)
-                        tc::mma_ts(tmem + CL::D1 + RC, tmem + CL::AG + s * (NSP / 2) + kk * 8,
-                                   tc::sdesc_noswz(bg + kk * 2 * (RC / 8) * 128, (RC / 8) * 128, 128),
-                                   id1g, 1);
-                tc::commit(BAR(BAR_D1FULL));
-                ++u_d1;
-            };
-            // contraction 0: z (hi, lo) . (eff - 1) (hi, lo) as hi.hi + hi.lo + lo.hi into the
-            // multiplier columns.  Issued after chunk 0's contraction 1 (it then runs while
-            // chunk 0's S is read out) unless chunk 0 reads multipliers; either way a D1FULL
-            // commit of this thread covers it before the first chunk that reads them, and its
-            // operand columns are free for chunk 0's q_net at ZFREE.
-            auto issue_mma0 = [&]() {
-#pragma unroll
-                for (int s = 0; s < 3; ++s)
-#pragma unroll
-                    for (int kk = 0; kk < NSP / 16; ++kk)
-                        tc::mma_ts(tmem + CL::FC, tmem + CL::A2 + (s == 2 ? NSP / 2 : 0) + kk * 8,
-                                   tc::sdesc_noswz(be + (s == 1 ? kFacCols * NSP * 2 : 0) + kk * 256,
-                                                   128, (NSP / 8) * 128),
-                                   id0, (s | kk) != 0);
-                tc::commit(BAR(BAR_ZFREE));
-            };
-            auto mma2 = [&](int c) {
-                const uint32_t bc = b2 + (uint32_t)c * (NSP * RC * 2);
-#pragma unroll
-                for (int s = 0; s < 2; ++s)
-#pragma unroll
-                    for (int kk = 0; kk < RC / 16; ++kk)
-                        tc::mma_ts(tmem + CL::D2, tmem + CL::A2 + s * (RC / 2) + kk * 8,
-                                   tc::sdesc_noswz(bc + kk * 256, 128, (RC / 8) * 128), id2,
-                                   (c | s | kk) != 0);
-                tc::commit(BAR(BAR_A2EMPTY));
-                ++u_a2;
-                if (c == p.nch - 1) tc::commit(BAR(BAR_D2FULL));
-            };
             int it = 0;
             if (warp == 1) {
+                // contraction 1 (+ the Gibbs layer) of each chunk into S buffer u & 1 as soon
+                // as the epilogue has read that buffer's previous chunk
+                uint32_t u = 0;
                 for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x, ++it) {
                     if (!(ok = wait_bar(BAR(BAR_A1FULL), it & 1, ctl, p.status, 2))) break;
-                    tc::fence_after();
-                    // chunk 0 reads multipliers: contraction 0 first (its D1FULL covers it)
-                    if (p.fac_chunk0) issue_mma0();
-                    // contraction 1 of each chunk as soon as the previous S has been read out
-                    for (int c = 0; ok && c < p.nch; ++c) {
-                        if (!(ok = wait_bar(BAR(BAR_D1EMPTY), (u_d1 & 1) ^ 1, ctl, p.status, 2)))
+                    for (int c = 0; c < nch; ++c, ++u) {
+                        const int b = (int)(u & 1);
+                        if (!(ok = wait_bar(BAR(BAR_D1EMPTY0 + b), ((u >> 1) & 1) ^ 1, ctl,
+                                            p.status, 2)))
                             break;
                         tc::fence_after();
-                        issue_mma1(c);
-                        ctl->mma1_issued = (int)u_d1;
-                        if (c == 0 && !p.fac_chunk0) issue_mma0();
+                        const int rcc = c == nch - 1 ? p.rct : RC;
+                        const uint32_t d = tmem + CL::S0 + (uint32_t)b * (2 * RC);
+                        const uint32_t id1 = tc::idesc_f16_f32(128, 2 * rcc);
+                        const uint32_t bc = b1 + (uint32_t)c * (2 * RC * NSP * 2);
+#pragma unroll
+                        for (int s = 0; s < 2; ++s)
+#pragma unroll
+                            for (int kk = 0; kk < NSP / 16; ++kk)
+                                tc::mma_ts(d, tmem + CL::A1 + s * (NSP / 2) + kk * 8,
+                                           tc::sdesc_noswz(bc + kk * 256, 128, (NSP / 8) * 128),
+                                           id1, (s | kk) != 0);
+                        // Gibbs layer into the reverse half: feature term s against the
+                        // coefficient terms 0 .. 1 - s
+                        const uint32_t idg = tc::idesc_f16_f32(128, rcc);
+                        const uint32_t gc = bg + (uint32_t)c * (RC * kGibK * 2);
+#pragma unroll
+                        for (int s = 0; s < 2; ++s)
+#pragma unroll
+                            for (int tt = 0; tt < 2 - s; ++tt)
+                                tc::mma_ts(d + rcc, tmem + CL::AG + s * 8,
+                                           tc::sdesc_noswz(gc + tt * 256, 128, (kGibK / 8) * 128),
+                                           idg, 1);
+                        tc::commit(BAR(BAR_D1FULL0 + b));
                     }
-                    // completes when every contraction 1 of the tile has read its operands
-                    if (ok) tc::commit(BAR(BAR_A1FREE));
                 }
             } else {
-                // contraction 2 in chunk order (the omega accumulation order, hence the
-                // rounding, is fixed), the first of a tile once omega of the tile before has
-                // been read out
+                // per tile: contraction 0 once z is in the omega columns (ZFULL: the tile
+                // before's omega has been read out and the third-body sums of its last
+                // chunks as well), then contraction 2 of each chunk in chunk order (the
+                // accumulation order, hence the rounding, is fixed)
+                const uint32_t id0 = tc::idesc_bf16_f32(128, p.fcn);
+                uint32_t u = 0;
                 for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x, ++it) {
-                    if (!(ok = wait_bar(BAR(BAR_D2EMPTY), (it & 1) ^ 1, ctl, p.status, 2))) break;
-                    for (int c = 0; ok && c < p.nch; ++c) {
-                        if (!(ok = wait_bar(BAR(BAR_A2FULL), u_a2 & 1, ctl, p.status, 2))) break;
-                        // Let contraction 1 of the next chunk go first: it gates the epilogue,
-                        // while this one fills the pipe during the next S read-out.  Only the
-                        // order on the tensor pipe depends on this (the two are independent),
-                        // so the wait is short and bounded and then proceeds regardless.
-                        if (c + 1 < p.nch)
-                            for (int spin = 0; spin < 4096 && ctl->mma1_issued < (int)u_a2 + 2; ++spin)
-                                __nanosleep(20);
+                    if (!(ok = wait_bar(BAR(BAR_ZFULL), it & 1, ctl, p.status, 2))) break;
+                    tc::fence_after();
+#pragma unroll
+                    for (int s = 0; s < 3; ++s)
+#pragma unroll
+                        for (int kk = 0; kk < NSP / 16; ++kk)
+                            tc::mma_ts(tmem + CL::FC, tmem + CL::D2 + (s == 2 ? NSP / 2 : 0) + kk * 8,
+                                       tc::sdesc_noswz(be + (s == 1 ? p.fcn * NSP * 2 : 0) + kk * 256,
+                                                       128, (NSP / 8) * 128),
+                                       id0, (s | kk) != 0);
+                    tc::commit(BAR(BAR_FCFULL));
+                    for (int c = 0; c < nch; ++c, ++u) {
+                        const int ab = (int)(u & 1);
+                        if (!(ok = wait_bar(BAR(BAR_A2FULL0 + ab), (u >> 1) & 1, ctl, p.status, 2)))
+                            break;
                         tc::fence_after();
-                        mma2(c);
+                        const int rcc = c == nch - 1 ? p.rct : RC;
+                        const uint32_t bc = b2 + (uint32_t)c * (NSP * RC * 2);
+                        const uint32_t a2 = tmem + CL::A2 + (uint32_t)ab * RC;
+#pragma unroll
+                        for (int s = 0; s < 2; ++s)
+                            for (int kk = 0; kk < rcc / 16; ++kk)
+                                tc::mma_ts(tmem + CL::D2, a2 + s * (RC / 2) + kk * 8,
+                                           tc::sdesc_noswz(bc + kk * 256, 128, (rcc / 8) * 128), id2,
+                                           (c | s | kk) != 0);
+                        tc::commit(BAR(BAR_A2EMPTY0 + ab));
                     }
+                    if (ok) tc::commit(BAR(BAR_D2FULL));
                 }
             }
             // every MMA issued (by both issuers) has completed before tensor memory is released
@@ -425,255 +382,301 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
         }
     } else if (warp < kMma2Warp) {
         // ------------------------------------------------------------- epilogue
-        const int ew = warp - kEpiWarp0;             // 0..15
-        const int g = ew >> 2;                        // warpgroup 0..3: quarter of each chunk
+        const int ew = warp - kEpiWarp0;             // 0 .. kEpiWarps - 1
+        const int g = ew >> 2;                        // warpgroup: share of each chunk
         const int q = warp & 3;                       // lane quarter of tensor memory
         const int row = q * 32 + lane;
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         const int ns = p.ns;
-        int it = 0, u = 0;
-        bool ok = wait_bar(BAR(BAR_BTAB), 0, ctl, p.status, 3);   // coefficients in smem
+        int it = 0;
+        uint32_t u = 0;
+        bool ok = wait_bar(BAR(BAR_BTAB), 0, ctl, p.status, 3);   // tables in smem
         CellF cf;
-        // ---- prologue of tile t: features, X and split log2 X (Eq. 4 input layer); ends
-        // with the tile's contraction-1 operands in tensor memory (A1FULL)
-        auto prologue = [&](int t, int itp) -> bool {
+        // this thread's species row of tile t: staged in shared memory (full tiles) or read
+        // from global memory
+        auto y_row = [&](int t) -> const float * {
+            const int64_t i0 = (int64_t)t * 128, ci = i0 + row;
+            if (p.stage_y && i0 + 128 <= n) return Ys + (int64_t)row * p.ldY;
+            return ci < n ? p.Y + ci * p.ldY : zrow;
+        };
+        // ---- prologue of tile t: features, z, split log2 z (Eq. 4 input layer), the
+        // Arrhenius and Gibbs features; ends with contraction 1's operands in tensor memory
+        // (A1FULL)
+        auto prologue = [&](int t, int itp, CellF &cf) -> bool {
             const int64_t i0 = (int64_t)t * 128;
             const int64_t ci = i0 + row;
             const bool full = p.stage_y && i0 + 128 <= n;
             if (!wait_bar(BAR(BAR_YFULL), itp & 1, ctl, p.status, 3)) return false;
-            // ---- prologue: features, X and split log2 X (Eq. 4 input layer)
             float Tc = 1000.0f, Pc = 1.0e6f;
-            const float *yrow = nullptr;
             if (full) {
                 Tc = Ts[row];
                 Pc = Ps[row];
-                yrow = Ys + (int64_t)row * p.ldY;
             } else if (ci < n) {
                 Tc = __ldg(p.T + ci);
                 Pc = __ldg(p.P + ci);
-                yrow = p.Y + ci * p.ldY;
             }
+            const float *yrow = y_row(t);
             cf.lg2T = log2f(Tc);
             cf.invT = 1.0f / Tc;
-            cf.tau = Tc * 1e-3f;
-            cf.tau2 = cf.tau * cf.tau;
-            cf.rg = Tc >= p.t_mid ? 1 : 0;
+            cf.itau = 1000.0f / Tc;
+            cf.T = Tc;
             cf.lgct = log2f(Pc) - p.lg2R - cf.lg2T;
-            // This warpgroup's quarter of the species columns: z_k = Y_k / W_k, whose log2
-            // goes to the contraction; X_k = z_k / sum_k z_k is completed by the column
-            // ns + 1 below (log2 c_tot - log2 sum, weighted by the reaction order).
+            // this warpgroup's blocks of columns: z_k = Y_k / W_k (species), whose log2 goes
+            // to the contraction; X_k = z_k / sum_k z_k is completed by column ns + 1
+            // (log2 c_tot - log2 sum_k z_k, weighted by the reaction order), written once the
+            // warpgroups' partial sums are in.  Every contraction 1 of the previous tile has
+            // completed (the epilogue waited for the last one's D1FULL), so A1 and AG are free
+            // and each block goes to tensor memory as soon as it is formed.
+            tc::fence_after();
             float psum = 0.0f;
-            uint32_t wh[SQ / 2], wm[SQ / 2], wl[SQ / 2];   // log2 z, three BF16 terms
-            uint32_t gh[SQ / 2], gm[SQ / 2], gl[SQ / 2];   // G, three BF16 terms
-            uint32_t zh[SQ / 2], zl[SQ / 2];               // z, two BF16 terms (contraction 0)
 #pragma unroll
-            for (int e = 0; e < SQ / 2; ++e) {
-                float lx[2], gk[2], zz[2];
+            for (int bi = 0; bi < BPW; ++bi) {
+                const int blk = g + NQ * bi;
+                if (blk >= NB) continue;
+                float lx[8];
+                const float4 w0 = *(const float4 *)(iW + 8 * blk), w1 = *(const float4 *)(iW + 8 * blk + 4);
+                const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+                if (8 * blk + 8 <= ns) {
+                    // species only (straight-line, so that the loads and logarithms overlap)
 #pragma unroll
-                for (int hlf = 0; hlf < 2; ++hlf) {
-                    const int k = g * SQ + 2 * e + hlf;
-                    lx[hlf] = 0.0f;
-                    gk[hlf] = 0.0f;
-                    zz[hlf] = 0.0f;
-                    if (k < ns) {
-                        const float z = yrow ? fmaxf(yrow[k], 0.0f) * iW[k] : 0.0f;
+                    for (int e = 0; e < 8; ++e) {
+                        const float z = fmaxf(yrow[8 * blk + e], 0.0f) * wv[e];
                         psum += z;
-                        zz[hlf] = z;
-                        lx[hlf] = fmaxf(tc::lg2(z), kLog2Floor);
-                        // Gibbs layer (Eq. 10) for this species at this cell's temperature
-                        const float4 g0 = *(const float4 *)&gib[k].c[cf.rg][0];
-                        const float4 g1 = *(const float4 *)&gib[k].c[cf.rg][4];
-                        const float pt = fmaf(fmaf(fmaf(g1.y, cf.tau, g1.x), cf.tau, g0.w), cf.tau, g0.z);
-                        gk[hlf] = fmaf(pt, cf.tau, fmaf(g1.z, cf.invT, fmaf(g0.y, cf.lg2T, g0.x)));
-                    } else if (k == ns) {
-                        lx[hlf] = cf.lgct;            // third-body c_tot column
-                    } else if (FOLD && k >= ns + 2 && k < ns + 2 + kFoldRows) {
-                        // Arrhenius features 1, log2 T, 1/T, each against three rows
-                        const int f = (k - ns - 2) / 3;
-                        lx[hlf] = f == 0 ? 1.0f : (f == 1 ? cf.lg2T : cf.invT);
+                        lx[e] = fmaxf(tc::lg2(z), kLog2Floor);
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        // loads clamped to the row, z = 0 past the species
+                        const int k = 8 * blk + e;
+                        const float z = fmaxf(yrow[min(k, ns - 1)], 0.0f) * wv[e];
+                        psum += z;
+                        const float lz = fmaxf(tc::lg2(z), kLog2Floor);
+                        const int cc = ccode[k];
+                        // species, the third-body c_tot column, the Arrhenius features 1,
+                        // log2 T, 1000/T (each against three coefficient rows); the
+                        // normalisation later
+                        lx[e] = cc == kColSpecies ? lz : cc == kColLgct ? cf.lgct
+                              : cc == kColOne ? 1.0f : cc == kColLg2T ? cf.lg2T
+                              : cc == kColItau ? cf.itau : 0.0f;
                     }
                 }
-                split3x2(lx[0], lx[1], wh[e], wm[e], wl[e]);
-                split3x2(gk[0], gk[1], gh[e], gm[e], gl[e]);
-                split2x2(zz[0], zz[1], zh[e], zl[e]);
+                uint32_t wh[4], wl[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) split2h(lx[2 * e], lx[2 * e + 1], wh[e], wl[e]);
+                const uint32_t a1 = tmem + lane_off + CL::A1 + 4 * blk;
+                tc::tmem_st4(a1, wh);
+                tc::tmem_st4(a1 + NSP / 2, wl);
             }
-            // the previous tile's contractions 1 have read their operands
-            if (itp > 0 && !wait_bar(BAR(BAR_A1FREE), (itp - 1) & 1, ctl, p.status, 3)) return false;
-            // ... and the previous tile's last contraction 2 has read its q_net operand, whose
-            // columns take z now
-            if (!wait_bar(BAR(BAR_A2EMPTY), (u & 1) ^ 1, ctl, p.status, 3)) return false;
-            tc::fence_after();
-            const uint32_t az = tmem + lane_off + CL::A2 + g * (SQ / 2);
-            const uint32_t a1 = tmem + lane_off + CL::A1 + g * (SQ / 2);
-            const uint32_t ag = tmem + lane_off + CL::AG + g * (SQ / 2);
-            if constexpr (SQ / 2 == 8) {
-                tc::tmem_st8(a1 + 0 * (NSP / 2), wh);
-                tc::tmem_st8(a1 + 1 * (NSP / 2), wm);
-                tc::tmem_st8(a1 + 2 * (NSP / 2), wl);
-                tc::tmem_st8(ag + 0 * (NSP / 2), gh);
-                tc::tmem_st8(ag + 1 * (NSP / 2), gm);
-                tc::tmem_st8(ag + 2 * (NSP / 2), gl);
-                tc::tmem_st8(az, zh);
-                tc::tmem_st8(az + NSP / 2, zl);
-            } else {
-                static_assert(SQ / 2 == 4, "warpgroup species quarter of 8 or 16 columns");
-                tc::tmem_st4(a1 + 0 * (NSP / 2), wh);
-                tc::tmem_st4(a1 + 1 * (NSP / 2), wm);
-                tc::tmem_st4(a1 + 2 * (NSP / 2), wl);
-                tc::tmem_st4(ag + 0 * (NSP / 2), gh);
-                tc::tmem_st4(ag + 1 * (NSP / 2), gm);
-                tc::tmem_st4(ag + 2 * (NSP / 2), gl);
+            Psum[g * 128 + row] = psum;
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(BAR(BAR_XREADY));
+            if (g == NQ - 1) {
+                // Gibbs features: NASA-7 terms of the cell's temperature range
+                const float tau = Tc * 1e-3f, t2 = tau * tau;
+                const float ph[7] = {1.0f, cf.lg2T, tau, t2, t2 * tau, t2 * t2, cf.itau};
+                const bool hi = Tc >= p.t_mid;
+                float fv[16];
+#pragma unroll
+                for (int m = 0; m < 7; ++m) {
+                    fv[m] = hi ? 0.0f : ph[m];
+                    fv[7 + m] = hi ? ph[m] : 0.0f;
+                }
+                fv[14] = fv[15] = 0.0f;
+                uint32_t gh[8], gl[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) split2h(fv[2 * e], fv[2 * e + 1], gh[e], gl[e]);
+                const uint32_t ag = tmem + lane_off + CL::AG;
+                tc::tmem_st8(ag + 0, gh);
+                tc::tmem_st8(ag + 8, gl);
+            }
+            if (!wait_bar(BAR(BAR_XREADY), itp & 1, ctl, p.status, 3)) return false;
+            float sum = 0.0f;
+#pragma unroll
+            for (int gg = 0; gg < NQ; ++gg) sum += Psum[gg * 128 + row];
+            cf.inv_sum = sum > 0.0f ? 1.0f / sum : 0.0f;
+            {
+                // the packed word holding the normalisation column ns + 1 and its neighbour
+                // (column ns, log2 c_tot, or ns + 2, the Arrhenius feature 1 or padding)
+                const int kn = ns + 1;
+                tc::tmem_wait_st();                   // the block holding it has landed
+                if ((kn >> 3) % NQ == g) {
+                    const float vn = sum > 0.0f ? cf.lgct - log2f(sum) : 0.0f;
+                    const int ko = kn ^ 1;
+                    const int co = ccode[ko];
+                    const float vo = co == kColLgct ? cf.lgct : co == kColOne ? 1.0f : 0.0f;
+                    const float lo = (kn & 1) ? vo : vn, hi = (kn & 1) ? vn : vo;
+                    uint32_t h, l;
+                    split2h(lo, hi, h, l);
+                    const uint32_t col = tmem + lane_off + CL::A1 + kn / 2;
+                    tc::tmem_st1(col, h);
+                    tc::tmem_st1(col + NSP / 2, l);
+                }
+            }
+            tc::tmem_wait_st();
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(BAR(BAR_A1FULL));
+            return true;
+        };
+        // z of tile t (two BF16 terms, contraction 0's operand) into the omega columns once
+        // the tile before's omega has been read out; recomputed from the tile's Y, which
+        // that omega has not yet replaced in the staging buffer
+        auto write_z = [&](int t) {
+            const float *yrow = y_row(t);
+#pragma unroll
+            for (int bi = 0; bi < BPW; ++bi) {
+                if (g + NQ * bi >= NB) continue;
+                const int blk = g + NQ * bi;
+                const float4 w0 = *(const float4 *)(iW + 8 * blk), w1 = *(const float4 *)(iW + 8 * blk + 4);
+                const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+                float zz[8];
+                if (8 * blk + 8 <= ns) {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) zz[e] = fmaxf(yrow[8 * blk + e], 0.0f) * wv[e];
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) zz[e] = fmaxf(yrow[min(8 * blk + e, ns - 1)], 0.0f) * wv[e];
+                }
+                uint32_t zh[4], zl[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) split2x2(zz[2 * e], zz[2 * e + 1], zh[e], zl[e]);
+                const uint32_t az = tmem + lane_off + CL::D2 + 4 * (g + NQ * bi);
                 tc::tmem_st4(az, zh);
                 tc::tmem_st4(az + NSP / 2, zl);
             }
             tc::tmem_wait_st();
-            Psum[g * 128 + row] = psum;
-            __syncwarp();
-            if (lane == 0) {
-                // the first tile's Y buffer is free now; later ones hold omega of the tile
-                // before until it has been stored
-                if (itp == 0) tc::mbar_arrive(BAR(BAR_YEMPTY));
-                tc::mbar_arrive(BAR(BAR_XREADY));
-            }
-            if (!wait_bar(BAR(BAR_XREADY), itp & 1, ctl, p.status, 3)) return false;
-            {
-                const float sum = Psum[row] + Psum[128 + row] + Psum[256 + row] + Psum[384 + row];
-                cf.inv_sum = sum > 0.0f ? 1.0f / sum : 0.0f;
-                const int kn = ns + 1;                    // normalisation column
-                if (kn / SQ == g) {
-                    // the packed word holding column kn; its other half is column kn - 1
-                    // (= ns, log2 c_tot) or kn + 1 (the first Arrhenius feature, 1, or
-                    // padding, zero)
-                    const float other = (kn & 1) ? cf.lgct : (FOLD ? 1.0f : 0.0f);
-                    const float vn = sum > 0.0f ? cf.lgct - log2f(sum) : 0.0f;
-                    uint16_t ho, mo, lo_, hn, mn, ln;
-                    split3(other, ho, mo, lo_);
-                    split3(vn, hn, mn, ln);
-                    auto pk = [&](uint16_t o, uint16_t nn) {
-                        return (kn & 1) ? ((uint32_t)o | ((uint32_t)nn << 16))
-                                        : ((uint32_t)nn | ((uint32_t)o << 16));
-                    };
-                    const uint32_t col = tmem + lane_off + CL::A1 + kn / 2;
-                    tc::tmem_st1(col + 0 * (NSP / 2), pk(ho, hn));
-                    tc::tmem_st1(col + 1 * (NSP / 2), pk(mo, mn));
-                    tc::tmem_st1(col + 2 * (NSP / 2), pk(lo_, ln));
-                }
-                tc::tmem_wait_st();
+        };
+        if ((int)blockIdx.x < p.ntiles) {
+            ok = ok && prologue(blockIdx.x, 0, cf);
+            if (ok) {
+                write_z(blockIdx.x);
                 tc::fence_before();
                 __syncwarp();
-                if (lane == 0) tc::mbar_arrive(BAR(BAR_A1FULL));
+                if (lane == 0) tc::mbar_arrive(BAR(BAR_ZFULL));
+                if (lane == 0) tc::mbar_arrive(BAR(BAR_YEMPTY));   // Y(0) fully consumed
             }
-            return true;
-        };
-        if ((int)blockIdx.x < p.ntiles) ok = ok && prologue(blockIdx.x, 0);
+        }
+        CellF cfn;                                    // features of the next tile
         for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x, ++it) {
             const int64_t i0 = (int64_t)t * 128;
             const int64_t ci = i0 + row;
-            // ---- every chunk, this warpgroup's quarter of its reactions
-            for (int c = 0; c < p.nch; ++c, ++u) {
-                if (!(ok = wait_bar(BAR(BAR_D1FULL), u & 1, ctl, p.status, 3))) break;
+            const int t_next = t + gridDim.x;
+            const bool has_next = t_next < p.ntiles;
+            bool fc_ready = false;
+            // ---- every chunk, this warpgroup's share of its reactions.  The S read-out of
+            // chunk c + 1 is issued before chunk c's q_net goes out, so that its latency
+            // overlaps that store.
+            uint32_t sf[RH], sr[RH];
+            auto load_s = [&](int c, uint32_t uu) -> bool {
+                const int b = (int)(uu & 1);
+                if (!wait_bar(BAR(BAR_D1FULL0 + b), (uu >> 1) & 1, ctl, p.status, 3)) return false;
                 tc::fence_after();
-                uint32_t sf[RH], sr[RH], fv[8];
-                const uint32_t d1 = tmem + lane_off + CL::D1 + g * RH;
-                // both halves of contraction 1 and this quarter's (at most 8) multipliers,
-                // consecutive columns, behind one completion wait
-                const int mq = c * NQ + g;
-                const uint32_t hm = tabs.hmask[mq];
-                const int lb = hm ? tabs.fbase[mq] : 0;
-                tc::tmem_ld16_nw(d1, sf);
-                tc::tmem_ld16_nw(d1 + RC, sr);
-                if (hm) {
-                    tc::tmem_ld8_nw(tmem + lane_off + CL::FC + lb, fv);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) fv[e] = 0u;
+                const int rcc = c == nch - 1 ? p.rct : RC;
+                if (g * RH < rcc) {
+                    const uint32_t d1 = tmem + lane_off + CL::S0 + (uint32_t)b * (2 * RC) + g * RH;
+                    tc::tmem_ld16_nw(d1, sf);
+                    tc::tmem_ld16_nw(d1 + rcc, sr);
                 }
-                tc::tmem_wait_ld_tie(sf, sr, fv);
+                return true;
+            };
+            auto release_s = [&](int c, uint32_t uu) {
+                const int rcc = c == nch - 1 ? p.rct : RC;
+                if (g * RH < rcc) tc::tmem_wait_ld_tie16(sf, sr);
                 tc::fence_before();
                 __syncwarp();
-                if (lane == 0) tc::mbar_arrive(BAR(BAR_D1EMPTY));
-                const int j0 = c * RC + g * RH;
-                float q[RH];
-                if constexpr (FOLD) {
+                if (lane == 0) tc::mbar_arrive(BAR(BAR_D1EMPTY0 + (int)(uu & 1)));
+            };
+            if (!(ok = load_s(0, u))) break;
+            release_s(0, u);
+            for (int c = 0; c < nch; ++c, ++u) {
+                const int rcc = c == nch - 1 ? p.rct : RC;
+                const bool active = g * RH < rcc;
+                const QInfo qi = qinfo[c * NQ + g];
+                float qv[RH];
+                if (active) {
+                    if (qi.rank >= 0) {
+                        // the share's third-body / falloff reactions sit in its first 8 slots
+                        // (falloff in 0..nfall-1); their columns hold sum_k (eff_k - 1) z_k
+                        // (0 for plain slots), so M / c_tot = 1 + that / sum_k z_k
+                        if (!fc_ready) {
+                            if (!(ok = wait_bar(BAR(BAR_FCFULL), it & 1, ctl, p.status, 3))) break;
+                            tc::fence_after();
+                            fc_ready = true;
+                        }
+                        uint32_t fv[8];
+                        tc::tmem_ld8(tmem + lane_off + CL::FC + 8 * qi.rank, fv);
+                        float s8[8], fac[4], mul[4];
 #pragma unroll
-                    for (int r = 0; r < RH; ++r)
-                        q[r] = tc::ex2(__uint_as_float(sf[r])) - tc::ex2(__uint_as_float(sr[r]));
-                } else {
+                        for (int r = 0; r < 8; ++r) s8[r] = fmaf(__uint_as_float(fv[r]), cf.inv_sum, 1.0f);
+                        falloff4(fallq + 4 * qi.rank, s8, cf, qi.nfall, fac, mul);
 #pragma unroll
-                    for (int r = 0; r < RH; ++r)
-                        q[r] = rate_plain(tabs.coef + j0 + r, __uint_as_float(sf[r]),
-                                          __uint_as_float(sr[r]), cf);
-                }
-                if (hm) {
-                    // the quarter's third-body / falloff reactions sit in its first 8 slots
-                    // (falloff in 0..3); their columns hold sum_k (eff_k - 1) z_k (0 for the
-                    // other slots), so M / c_tot = 1 + that / sum_k z_k
-                    float s8[8], fo[4];
+                        for (int r = 0; r < 4; ++r)
+                            qv[r] = (tc::ex2(__uint_as_float(sf[r]) + fac[r]) -
+                                     tc::ex2(__uint_as_float(sr[r]) + fac[r])) * mul[r];
 #pragma unroll
-                    for (int r = 0; r < 8; ++r)
-                        s8[r] = fmaf(__uint_as_float(fv[r]), cf.inv_sum, 1.0f);
-                    falloff4(tabs.fq + 4 * (lb / 8), s8, cf, fo);
+                        for (int r = 4; r < 8; ++r)
+                            qv[r] = (tc::ex2(__uint_as_float(sf[r])) -
+                                     tc::ex2(__uint_as_float(sr[r]))) * s8[r];
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) q[r] *= fo[r];
+                        for (int r = 8; r < RH; ++r)
+                            qv[r] = tc::ex2(__uint_as_float(sf[r])) - tc::ex2(__uint_as_float(sr[r]));
+                    } else {
 #pragma unroll
-                    for (int r = 4; r < 8; ++r) q[r] *= s8[r];
+                        for (int r = 0; r < RH; ++r)
+                            qv[r] = tc::ex2(__uint_as_float(sf[r])) - tc::ex2(__uint_as_float(sr[r]));
+                    }
                 }
                 uint32_t hw[RH / 2], lw[RH / 2];
+                if (active) {
 #pragma unroll
-                for (int r = 0; r < RH; r += 2) {
-                    const uint32_t h = tc::pack_bf16x2(q[r], q[r + 1]);
-                    const float r0 = q[r] - __uint_as_float(h << 16);
-                    const float r1 = q[r + 1] - __uint_as_float(h & 0xFFFF0000u);
-                    hw[r / 2] = h;
-                    lw[r / 2] = tc::pack_bf16x2(r0, r1);
+                    for (int r = 0; r < RH; r += 2) split2x2(qv[r], qv[r + 1], hw[r / 2], lw[r / 2]);
                 }
-                if (!(ok = wait_bar(BAR(BAR_A2EMPTY), (u & 1) ^ 1, ctl, p.status, 3))) break;
-                // chunk 0: contraction 0 has read z from these columns
-                if (c == 0 && !(ok = wait_bar(BAR(BAR_ZFREE), it & 1, ctl, p.status, 3))) break;
+                // next chunk's S read-out in flight during this chunk's store
+                if (c + 1 < nch && !(ok = load_s(c + 1, u + 1))) break;
+                // last chunk: every contraction 1 of this tile has completed, so the next
+                // tile's prologue writes its operands now and its contractions 1 run while
+                // this chunk's contraction 2 and the omega store finish
+                if (c == nch - 1 && has_next && !(ok = prologue(t_next, it + 1, cfn))) break;
+                const int ab = (int)(u & 1);
+                if (!(ok = wait_bar(BAR(BAR_A2EMPTY0 + ab), ((u >> 1) & 1) ^ 1, ctl, p.status, 3))) break;
                 tc::fence_after();
-                const uint32_t a2 = tmem + lane_off + CL::A2 + g * (RH / 2);
-                tc::tmem_st8(a2, hw);
-                tc::tmem_st8(a2 + RC / 2, lw);
-                tc::tmem_wait_st();
+                if (active) {
+                    const uint32_t a2 = tmem + lane_off + CL::A2 + (uint32_t)ab * RC + g * (RH / 2);
+                    tc::tmem_st8(a2, hw);
+                    tc::tmem_st8(a2 + RC / 2, lw);
+                    tc::tmem_wait_st();
+                }
                 tc::fence_before();
                 __syncwarp();
-                if (lane == 0) tc::mbar_arrive(BAR(BAR_A2FULL));
+                if (lane == 0) tc::mbar_arrive(BAR(BAR_A2FULL0 + ab));
+                if (c + 1 < nch) release_s(c + 1, u + 1);
             }
             if (!ok) break;
-            // ---- the next tile's prologue first: it needs none of this tile's tensor memory
-            // (every contraction 1 of this tile has completed), so its contraction 1 can
-            // start while this tile's omega is read out
-            const int t_next = t + gridDim.x;
-            if (t_next < p.ntiles && !(ok = prologue(t_next, it + 1))) break;
-            // ---- omega of the tile: tensor memory -> shared (the Y buffer, read by the next
-            // tile's prologue already) -> one coalesced bulk store; then the buffer is free
-            // for the tile after next (YEMPTY)
+            // ---- omega of the tile: tensor memory -> registers; then the next tile's z
+            // into the omega columns and ZFULL (z ready; this tile's third-body sums, read
+            // by its chunks, may be replaced)
             if (!(ok = wait_bar(BAR(BAR_D2FULL), it & 1, ctl, p.status, 3))) break;
             tc::fence_after();
-            {
-                uint32_t w[SQ];
-                const uint32_t d2 = tmem + lane_off + CL::D2 + g * SQ;
-                if constexpr (SQ == 16) tc::tmem_ld16(d2, w);
-                else tc::tmem_ld8(d2, w);
-                tc::fence_before();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(BAR(BAR_D2EMPTY));
-                if (p.stage_y) {
+            uint32_t w[BPW][8];
 #pragma unroll
-                    for (int e = 0; e < SQ; ++e) {
-                        const int k = g * SQ + e;
-                        if (k < ns) Ws[row * ns + k] = __uint_as_float(w[e]);
-                    }
-                } else if (ci < n) {                  // no staging buffer: direct stores
-                    float *orow = p.om + ci * p.ldO;
-#pragma unroll
-                    for (int e = 0; e < SQ; ++e) {
-                        const int k = g * SQ + e;
-                        if (k < ns) orow[k] = __uint_as_float(w[e]);
-                    }
-                }
-            }
+            for (int bi = 0; bi < BPW; ++bi)
+                if (g + NQ * bi < NB) tc::tmem_ld8(tmem + lane_off + CL::D2 + 8 * (g + NQ * bi), w[bi]);
+            if (has_next) write_z(t_next);
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(BAR(BAR_ZFULL));
+            // ---- omega -> shared (the Y buffer, read by the next tile's prologue and z
+            // already) -> one coalesced bulk store; then the buffer is free for the tile
+            // after next
             if (p.stage_y) {
+#pragma unroll
+                for (int bi = 0; bi < BPW; ++bi)
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int k = 8 * (g + NQ * bi) + e;
+                        if (k < ns) Ws[row * ns + k] = __uint_as_float(w[bi][e]);
+                    }
                 tc::fence_proxy_async_smem();            // visible to the bulk store
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(BAR(BAR_WREADY));
@@ -692,9 +695,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                         for (int k = lane; k < ns; k += 32) orow[k] = Ws[r * ns + k];
                     }
                 }
+            } else if (ci < n) {                      // no staging buffer: direct stores
+                float *orow = p.om + ci * p.ldO;
+#pragma unroll
+                for (int bi = 0; bi < BPW; ++bi)
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int k = 8 * (g + NQ * bi) + e;
+                        if (k < ns) orow[k] = __uint_as_float(w[bi][e]);
+                    }
             }
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(BAR(BAR_YEMPTY));
+            cf = cfn;
         }
     }
     if (warp == kEpiWarp0 && lane == 0) tc::bulk_wait0();   // omega stores have landed
@@ -734,205 +747,237 @@ static double f_of_bf16(uint16_t h)
     return f;
 }
 
-// x = hi + mid + lo, each term the nearest BF16 of the remaining residual
-static void bf16_split3(double x, uint16_t (&t)[3])
+static uint16_t f16_rn(double x)
 {
-    for (int i = 0; i < 3; ++i) {
-        t[i] = bf16_rn((float)x);
-        x -= f_of_bf16(t[i]);
+    const __half_raw r = __float2half_rn((float)x);
+    return r.x;
+}
+
+static double f_of_f16(uint16_t u)
+{
+    __half_raw r;
+    r.x = u;
+    return (double)__half2float(__half(r));
+}
+
+static uint16_t f16_of_int(int v) { return f16_rn((double)v); }   // exact for |v| <= 2048
+
+// x = t[0] + t[1] + ..., each term the nearest FP16 of the remaining residual
+template <int N>
+static void f16_split(double x, uint16_t (&t)[N])
+{
+    for (int i = 0; i < N; ++i) {
+        t[i] = f16_rn(x);
+        x -= f_of_f16(t[i]);
     }
 }
 
 chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
 {
     const int ns = d->n_species, nr = d->n_reactions;
-    // columns: species 0..ns-1, then log2 c_tot (third-body factor) and the
-    // normalisation column log2 c_tot - log2 sum_k z_k (weighted by the reaction order)
-    int nsp = ((ns + 2 + 15) / 16) * 16;
+    // contraction-1 columns: species 0..ns-1, log2 c_tot (third-body factor), the
+    // normalisation column log2 c_tot - log2 sum_k z_k (weighted by the reaction order), and
+    // the nine Arrhenius rows
+    int nsp = ns + 2 + kArrRows;
     if (nsp <= 32) nsp = 32;
     else if (nsp <= 64) nsp = 64;
-    else return set_error(CHEM_EUNSUPPORTED, "split-BF16 path supports up to 62 species");
-    const int nch = (nr + RC - 1) / RC;
-    const int nrp = nch * RC;
-    // the Arrhenius layer rides in contraction 1 when nine padding rows are free
-    const bool fold = ns + 2 + kFoldRows <= nsp;
+    else
+        return set_error(CHEM_EUNSUPPORTED, "split-BF16 path supports up to %d species",
+                         64 - 2 - kArrRows);
     const int kf0 = ns + 2;
-    // Reactions without a third-body or falloff factor fill the first chunks (spread evenly
-    // over their slots); those with one go to the first 8 slots of the last K chunks'
-    // quarters (falloff ones round-robin into slots 0..3, third-body ones into the least
-    // filled quarter), with the rest of the plain reactions.  Each such quarter owns 8
-    // multiplier columns: contraction 0 fills them with its third-body sums.
+    const int nrp = ((nr + 15) / 16) * 16;
+    const int nch = (nrp + RC - 1) / RC;
+    const int rct = nrp - (nch - 1) * RC;      // reactions of the last chunk, 16..RC
+    // chunk shares (chunk, warpgroup) of RH slots; multiplier shares are taken from the end,
+    // chunk 0 last (its multipliers would have to wait for contraction 0)
     std::vector<int> plain, fall, tbr;
     for (int j = 0; j < nr; ++j)
         (d->kind[j] == 0 ? plain : d->kind[j] == CHEM_RXN_THIRD_BODY ? tbr : fall).push_back(j);
-    const int S = (int)(fall.size() + tbr.size());
-    int K = 0;
-    if (S) K = std::max((S + NQ * 8 - 1) / (NQ * 8), ((int)fall.size() + NQ * 4 - 1) / (NQ * 4));
-    if (K > nch || NQ * K * 8 > kFacCols)
+    const int nspec = (int)(fall.size() + tbr.size());
+    int qm = 0;
+    if (nspec) qm = std::max((nspec + 7) / 8, ((int)fall.size() + 3) / 4);
+    std::vector<int> shares;                   // c * NQ + g, in the order they are taken
+    for (int c = nch - 1; c >= 1; --c)
+        for (int gq = (c == nch - 1 ? rct / RH : NQ) - 1; gq >= 0; --gq) shares.push_back(c * NQ + gq);
+    for (int gq = (nch == 1 ? rct / RH : NQ) - 1; gq >= 0; --gq) shares.push_back(gq);
+    const int fcn = std::max(16, ((8 * qm + 15) / 16) * 16);
+    if (qm > (int)shares.size() || fcn > kMaxFc)
         return set_error(CHEM_EUNSUPPORTED,
                          "split-BF16 path: %d third-body / falloff reactions (%d falloff) exceed "
-                         "its %d multiplier columns", S, (int)fall.size(), kFacCols);
-    std::vector<int> order(nrp, -1);        // slot -> reaction (-1: padding)
-    size_t pi = 0;
+                         "its %d multiplier columns", nspec, (int)fall.size(), kMaxFc);
+    std::vector<QInfo> qinfo((size_t)nch * NQ);
+    for (auto &x : qinfo) x = QInfo{-1, 0, 0, 0};
+    std::vector<int> qsel(shares.begin(), shares.begin() + qm);
+    std::sort(qsel.begin(), qsel.end());       // ascending chunk order
+    for (int r = 0; r < qm; ++r) qinfo[qsel[r]].rank = (int8_t)r;
+    // slot -> reaction (-1: empty): falloff round-robin into slots 0..3 of the multiplier
+    // shares, third-body into the least filled, then the plain reactions in order
+    std::vector<int> order((size_t)nch * RC, -1);
+    auto slot_of = [&](int qq, int pos) { return (qq / NQ) * RC + (qq % NQ) * RH + pos; };
     {
-        const int head_slots = (nch - K) * RC;
-        const int n_head = std::min((int)plain.size(), head_slots);
-        for (int i = 0; i < n_head; ++i)
-            order[(size_t)((int64_t)i * head_slots / n_head)] = plain[pi++];
-        const int nqt = NQ * K;
-        std::vector<int> fill(nqt, 0);
+        std::vector<int> fill(qm, 0);
         for (size_t i = 0; i < fall.size(); ++i) {
-            const int qq = (int)(i % nqt);
-            order[(size_t)((nch - K) * NQ + qq) * RH + fill[qq]++] = fall[i];
+            const int r = (int)(i % qm);
+            order[slot_of(qsel[r], fill[r]++)] = fall[i];
         }
+        for (int r = 0; r < qm; ++r) qinfo[qsel[r]].nfall = (int8_t)fill[r];
         for (size_t i = 0; i < tbr.size(); ++i) {
-            int qq = 0;
-            for (int x = 1; x < nqt; ++x)
-                if (fill[x] < fill[qq]) qq = x;
-            order[(size_t)((nch - K) * NQ + qq) * RH + fill[qq]++] = tbr[i];
+            int r = 0;
+            for (int x = 1; x < qm; ++x)
+                if (fill[x] < fill[r]) r = x;
+            if (fill[r] >= 8)
+                return set_error(CHEM_EUNSUPPORTED, "split-BF16 path: multiplier slot layout");
+            order[slot_of(qsel[r], fill[r]++)] = tbr[i];
         }
-        for (int jj = head_slots; jj < nrp && pi < plain.size(); ++jj)
-            if (order[jj] < 0) order[jj] = plain[pi++];
+        size_t pi = 0;
+        for (int c = 0; c < nch && pi < plain.size(); ++c)
+            for (int r = 0; r < (c == nch - 1 ? rct : RC) && pi < plain.size(); ++r)
+                if (order[(size_t)c * RC + r] < 0) order[(size_t)c * RC + r] = plain[pi++];
+        if (pi != plain.size()) return set_error(CHEM_EUNSUPPORTED, "split-BF16 path: slot layout");
     }
-    if (pi != plain.size()) return set_error(CHEM_EUNSUPPORTED, "split-BF16 path: slot layout");
-    std::vector<uint16_t> b1((size_t)nch * 2 * RC * nsp, 0), b2((size_t)nch * nsp * RC, 0);
-    const size_t e_term = (size_t)kFacCols * nsp;
-    std::vector<uint16_t> eb(2 * e_term, 0);          // eff - 1: [term][column][species]
-    std::vector<CoefS> cf(nrp);
-    // per chunk quarter: holds third-body / falloff reactions; its first multiplier column
-    std::vector<uint32_t> hmask((size_t)nch * 2 * NQ, 0);
-    std::vector<int> qrank((size_t)nch * NQ, -1);
-    int nq_special = 0;
-    for (int jj = 0; jj < nrp; ++jj)
-        if (order[jj] >= 0 && d->kind[order[jj]] != 0 && qrank[jj / RH] < 0) {
-            qrank[jj / RH] = nq_special++;
-            hmask[jj / RH] = 1;
-            hmask[(size_t)nch * NQ + jj / RH] = (uint32_t)(8 * qrank[jj / RH]);
-        }
-    FallQ neutral;
-    memset(&neutral, 0, sizeof neutral);
-    neutral.troe = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
-    neutral.t2 = make_float4(1e30f, 0.0f, 0.0f, 0.0f);
-    std::vector<FallQ> fq((size_t)std::max(nq_special, 1) * 4, neutral);
-    auto b1_at = [&](int c, int r, int k) -> uint16_t & {
-        return b1[(size_t)c * 2 * RC * nsp + ((r / 8) * (nsp / 8) + k / 8) * 64 + (r % 8) * 8 + k % 8];
+    // tables: B1 [chunk][2 rcc][nsp], BG [chunk][rcc][48], B2 [chunk][nsp][rcc] (core-matrix
+    // order, K-major), E [term][fcn][nsp]; each chunk at the stride of a full one
+    const size_t b1c = (size_t)2 * RC * nsp, bgc = (size_t)RC * kGibK, b2c = (size_t)nsp * RC;
+    std::vector<uint16_t> b1(b1c * nch, 0), bgt(bgc * nch, 0), b2(b2c * nch, 0);
+    const size_t e_term = (size_t)fcn * nsp;
+    std::vector<uint16_t> eb(2 * e_term, 0);
+    auto b1_at = [&](int c, int rcc, int r, int k) -> uint16_t & {
+        (void)rcc;
+        return b1[(size_t)c * b1c + ((r / 8) * (nsp / 8) + k / 8) * 64 + (r % 8) * 8 + k % 8];
     };
-    auto b2_at = [&](int c, int nrow, int r) -> uint16_t & {
-        return b2[(size_t)c * nsp * RC + ((nrow / 8) * (RC / 8) + r / 8) * 64 + (nrow % 8) * 8 + r % 8];
+    auto bg_at = [&](int c, int r, int k) -> uint16_t & {
+        return bgt[(size_t)c * bgc + ((r / 8) * (kGibK / 8) + k / 8) * 64 + (r % 8) * 8 + k % 8];
     };
-    auto e_at = [&](int term, int n, int k) -> uint16_t & {
-        return eb[term * e_term + ((n / 8) * (nsp / 8) + k / 8) * 64 + (n % 8) * 8 + k % 8];
+    auto b2_at = [&](int c, int rcc, int nrow, int r) -> uint16_t & {
+        return b2[(size_t)c * b2c + ((nrow / 8) * (rcc / 8) + r / 8) * 64 + (nrow % 8) * 8 + r % 8];
     };
-    for (int jj = 0; jj < nrp; ++jj) {
-        CoefS &C = cf[jj];
-        memset(&C, 0, sizeof C);
-        const int c = jj / RC, r = jj % RC;
-        if (order[jj] < 0) {                    // padding slot: q = 0
-            C.kf = make_float4(kDead, 0, 0, 0);
-            if (fold) {
-                uint16_t t3[3];
-                bf16_split3(kDead, t3);
-                for (int i = 0; i < 3; ++i) b1_at(c, r, kf0 + i) = b1_at(c, RC + r, kf0 + i) = t3[i];
-            }
-            continue;
-        }
-        const int j = order[jj];
-        const int kind = d->kind[j];
-        const double *ar = d->arrh + (size_t)j * 3;
-        int ordf = 0, ordr = 0;
-        for (int k = 0; k < ns; ++k) {
-            const int f = d->nu_f[(size_t)j * ns + k], pr = d->nu_r[(size_t)j * ns + k];
-            ordf += f;
-            ordr += pr;
-            b1_at(c, r, k) = bf16_of_int(f);
-            b1_at(c, RC + r, k) = bf16_of_int(pr);
-            b2_at(c, k, r) = bf16_of_int(pr - f);
-        }
-        const int tbx = kind == CHEM_RXN_THIRD_BODY ? 1 : 0;   // log2 M = log2 c_tot + log2(M/c_tot)
-        b1_at(c, r, ns) = bf16_of_int(tbx);
-        b1_at(c, RC + r, ns) = bf16_of_int(tbx);
-        b1_at(c, r, ns + 1) = bf16_of_int(ordf);
-        b1_at(c, RC + r, ns + 1) = bf16_of_int(ordr);
-        C.kf = make_float4((float)(ar[0] * kLog2e), (float)ar[1], (float)(-ar[2] * kLog2e),
-                           d->reversible[j] ? 1.0f : 0.0f);
-        if (fold) {
-            // rows kf0 + 3 f + i: term i of the coefficient of feature f (1, log2 T, 1/T)
-            const double co[3] = {ar[0] * kLog2e, ar[1], -ar[2] * kLog2e};
-            for (int f = 0; f < 3; ++f) {
-                uint16_t t3[3];
-                bf16_split3(co[f], t3);
-                for (int i = 0; i < 3; ++i) {
-                    b1_at(c, r, kf0 + 3 * f + i) = t3[i];
-                    if (d->reversible[j]) b1_at(c, RC + r, kf0 + 3 * f + i) = t3[i];
-                }
-            }
-            if (!d->reversible[j]) {
-                uint16_t t3[3];
-                bf16_split3(kDead, t3);
-                for (int i = 0; i < 3; ++i) b1_at(c, RC + r, kf0 + i) = t3[i];
-            }
-        }
-        if (kind == 0) continue;
-        // third-body sum column (contraction 0): eff - 1 in two BF16 terms
-        const int pos = jj % RH, col = 8 * qrank[jj / RH] + pos;
-        if (pos >= 8 || (kind != CHEM_RXN_THIRD_BODY && pos >= 4))
-            return set_error(CHEM_EUNSUPPORTED, "split-BF16 path: multiplier slot layout");
-        for (int k = 0; k < ns; ++k) {
-            const double e = (d->eff ? d->eff[(size_t)j * ns + k] : 1.0) - 1.0;
-            const uint16_t hi = bf16_rn((float)e);
-            e_at(0, col, k) = hi;
-            e_at(1, col, k) = bf16_rn((float)(e - f_of_bf16(hi)));
-        }
-        if (kind != CHEM_RXN_THIRD_BODY) {
-            FallQ &F = fq[(size_t)4 * qrank[jj / RH] + pos];
-            const double *al = d->arrh_low + (size_t)j * 3;
-            F.kf = make_float4(C.kf.x, C.kf.y, C.kf.z, 1.0f);
-            F.k0 = make_float4((float)(al[0] * kLog2e), (float)al[1], (float)(-al[2] * kLog2e), 0.f);
-            if (kind == CHEM_RXN_TROE) {
-                const double *tp = d->troe + (size_t)j * 4;
-                F.troe = make_float4((float)(1.0 - tp[0]), (float)tp[0], (float)(kLog2e / tp[1]),
-                                     (float)(kLog2e / tp[2]));
-                if (tp[3] > 0.0) F.t2 = make_float4((float)(tp[3] * kLog2e), 0, 0, 0);
-            }
-        }
-    }
-    // Gibbs layer per species (log2 units, the standard concentration folded into the bias):
+    auto e_at = [&](int term, int col, int k) -> uint16_t & {
+        return eb[term * e_term + ((col / 8) * (nsp / 8) + k / 8) * 64 + (col % 8) * 8 + k % 8];
+    };
+    // Gibbs layer per species on [1, log2 T, tau, tau^2, tau^3, tau^4, 1/tau] (tau = T/1000)
+    // in log2 units, the standard concentration folded into the bias (Eqs. 10-11):
     // G = (a1 - a7) log2e - log2(p_ref/R) + (1 - a1) log2 T - a2/2 T log2e - a3/6 T^2 log2e
     //     - a4/12 T^3 log2e - a5/20 T^4 log2e + a6 log2e / T
-    std::vector<GibbsS> gb(ns);
     const double lg2_pref_R = log2(d->p_ref / kR);
-    for (int k = 0; k < ns; ++k) {
-        memset(&gb[k], 0, sizeof gb[k]);
+    std::vector<double> gsp((size_t)ns * 14);
+    for (int k = 0; k < ns; ++k)
         for (int rg = 0; rg < 2; ++rg) {
             const double *a = d->nasa7 + (size_t)k * 14 + (size_t)rg * 7;
             const double cc[7] = {(a[0] - a[6]) * kLog2e - lg2_pref_R, 1.0 - a[0],
                                   -a[1] / 2.0 * 1e3 * kLog2e, -a[2] / 6.0 * 1e6 * kLog2e,
                                   -a[3] / 12.0 * 1e9 * kLog2e, -a[4] / 20.0 * 1e12 * kLog2e,
-                                  a[5] * kLog2e};
-            for (int q = 0; q < 7; ++q) gb[k].c[rg][q] = (float)cc[q];
+                                  a[5] * kLog2e * 1e-3};
+            for (int q = 0; q < 7; ++q) gsp[(size_t)k * 14 + rg * 7 + q] = cc[q];
+        }
+    FallQ neutral;
+    memset(&neutral, 0, sizeof neutral);
+    neutral.troe = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+    neutral.t2 = make_float4(1e30f, 0.0f, 0.0f, 0.0f);
+    std::vector<FallQ> fq((size_t)std::max(qm, 1) * 4, neutral);
+    std::vector<int> qrank((size_t)nch * NQ, -1);
+    for (int r = 0; r < qm; ++r) qrank[qsel[r]] = r;
+    for (int c = 0; c < nch; ++c) {
+        const int rcc = c == nch - 1 ? rct : RC;
+        for (int r = 0; r < rcc; ++r) {
+            const int j = order[(size_t)c * RC + r];
+            uint16_t dead[3];
+            f16_split<3>(kDead, dead);
+            if (j < 0) {                          // padding slot: q = 0
+                for (int i = 0; i < 3; ++i) b1_at(c, rcc, r, kf0 + i) = b1_at(c, rcc, rcc + r, kf0 + i) = dead[i];
+                continue;
+            }
+            const int kind = d->kind[j];
+            const double *ar = d->arrh + (size_t)j * 3;
+            int ordf = 0, ordr = 0;
+            for (int k = 0; k < ns; ++k) {
+                const int f = d->nu_f[(size_t)j * ns + k], pr = d->nu_r[(size_t)j * ns + k];
+                ordf += f;
+                ordr += pr;
+                b1_at(c, rcc, r, k) = f16_of_int(f);
+                b1_at(c, rcc, rcc + r, k) = f16_of_int(pr);
+                b2_at(c, rcc, k, r) = bf16_of_int(pr - f);
+            }
+            const int tbx = kind == CHEM_RXN_THIRD_BODY ? 1 : 0;   // log2 M = log2 c_tot + log2(M/c_tot)
+            b1_at(c, rcc, r, ns) = f16_of_int(tbx);
+            b1_at(c, rcc, rcc + r, ns) = f16_of_int(tbx);
+            b1_at(c, rcc, r, ns + 1) = f16_of_int(ordf);
+            b1_at(c, rcc, rcc + r, ns + 1) = f16_of_int(ordr);
+            // rows kf0 + 3 f + i: term i of the coefficient of feature f (1, log2 T, 1000/T)
+            const double co[3] = {ar[0] * kLog2e, ar[1], -ar[2] * kLog2e * 1e-3};
+            for (int f = 0; f < 3; ++f) {
+                uint16_t t3[3];
+                f16_split<3>(co[f], t3);
+                for (int i = 0; i < 3; ++i) {
+                    b1_at(c, rcc, r, kf0 + 3 * f + i) = t3[i];
+                    if (d->reversible[j]) b1_at(c, rcc, rcc + r, kf0 + 3 * f + i) = t3[i];
+                }
+            }
+            if (!d->reversible[j])
+                for (int i = 0; i < 3; ++i) b1_at(c, rcc, rcc + r, kf0 + i) = dead[i];
+            else {
+                // Gibbs layer folded through nu (FP64): coefficient of feature m of range rg
+                for (int rg = 0; rg < 2; ++rg)
+                    for (int q = 0; q < 7; ++q) {
+                        double cj = 0.0;
+                        for (int k = 0; k < ns; ++k) {
+                            const int nu = d->nu_r[(size_t)j * ns + k] - d->nu_f[(size_t)j * ns + k];
+                            if (nu) cj += nu * gsp[(size_t)k * 14 + rg * 7 + q];
+                        }
+                        uint16_t t2[2];
+                        f16_split<2>(cj, t2);
+                        for (int i = 0; i < 2; ++i) bg_at(c, r, 16 * i + 7 * rg + q) = t2[i];
+                    }
+            }
+            if (kind == 0) continue;
+            // third-body sum column (contraction 0): eff - 1 in two BF16 terms
+            const int qq = c * NQ + r / RH, pos = r % RH;
+            const int rk = qrank[qq];
+            if (rk < 0 || pos >= 8 || (kind != CHEM_RXN_THIRD_BODY && pos >= 4))
+                return set_error(CHEM_EUNSUPPORTED, "split-BF16 path: multiplier slot layout");
+            const int col = 8 * rk + pos;
+            for (int k = 0; k < ns; ++k) {
+                const double e = (d->eff ? d->eff[(size_t)j * ns + k] : 1.0) - 1.0;
+                const uint16_t hi = bf16_rn((float)e);
+                e_at(0, col, k) = hi;
+                e_at(1, col, k) = bf16_rn((float)(e - f_of_bf16(hi)));
+            }
+            if (kind != CHEM_RXN_THIRD_BODY) {
+                FallQ &F = fq[(size_t)4 * rk + pos];
+                const double *al = d->arrh_low + (size_t)j * 3;
+                F.kf = make_float4((float)co[0], (float)co[1], (float)(-ar[2] * kLog2e), 1.0f);
+                F.k0 = make_float4((float)(al[0] * kLog2e), (float)al[1], (float)(-al[2] * kLog2e), 0.f);
+                if (kind == CHEM_RXN_TROE) {
+                    const double *tp = d->troe + (size_t)j * 4;
+                    F.troe = make_float4((float)(1.0 - tp[0]), (float)tp[0], (float)(kLog2e / tp[1]),
+                                         (float)(kLog2e / tp[2]));
+                    if (tp[3] > 0.0) F.t2 = make_float4((float)(tp[3] * kLog2e), 0, 0, 0);
+                }
+            }
         }
     }
     std::vector<float> invW(ns);
     for (int k = 0; k < ns; ++k) invW[k] = (float)(1.0 / d->mol_weight[k]);
 
-    // B1 | B2 | E | coefficients | quarter masks | falloff | Gibbs: contiguous, copied to
-    // shared memory by one bulk transfer (16-byte granules)
+    // B1 | BG | B2 | E | share records | falloff: contiguous, copied to
+    // shared memory by bulk transfers (16-byte granules); the last chunk of each table is
+    // cut to its rows
     auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
     auto a256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t ob1 = 0, ob2 = b1.size() * 2, oe = ob2 + b2.size() * 2, ocf = oe + eb.size() * 2;
-    const size_t ohm = a16(ocf + cf.size() * sizeof(CoefS));
-    const size_t ofq = a16(ohm + hmask.size() * 4);
-    const size_t ogb = a16(ofq + fq.size() * sizeof(FallQ));
-    const size_t blob = a16(ogb + gb.size() * sizeof(GibbsS));
+    const size_t sb1 = (b1c * (nch - 1) + (size_t)2 * rct * nsp) * 2;
+    const size_t sbg = (bgc * (nch - 1) + (size_t)rct * kGibK) * 2;
+    const size_t sb2 = (b2c * (nch - 1) + (size_t)nsp * rct) * 2;
+    const size_t ob1 = 0, obg = a16(ob1 + sb1), ob2 = a16(obg + sbg), oe = a16(ob2 + sb2);
+    const size_t oqi = a16(oe + eb.size() * 2);
+    const size_t ofq = a16(oqi + qinfo.size() * sizeof(QInfo));
+    const size_t blob = a16(ofq + fq.size() * sizeof(FallQ));
     const size_t oiw = a256(blob), ost = a256(oiw + invW.size() * 4), total = a256(ost + 16);
     std::vector<unsigned char> h(total, 0);
-    memcpy(h.data() + ob1, b1.data(), b1.size() * 2);
-    memcpy(h.data() + ob2, b2.data(), b2.size() * 2);
+    memcpy(h.data() + ob1, b1.data(), sb1);
+    memcpy(h.data() + obg, bgt.data(), sbg);
+    memcpy(h.data() + ob2, b2.data(), sb2);
     memcpy(h.data() + oe, eb.data(), eb.size() * 2);
-    memcpy(h.data() + ocf, cf.data(), cf.size() * sizeof(CoefS));
-    memcpy(h.data() + ohm, hmask.data(), hmask.size() * 4);
+    memcpy(h.data() + oqi, qinfo.data(), qinfo.size() * sizeof(QInfo));
     memcpy(h.data() + ofq, fq.data(), fq.size() * sizeof(FallQ));
-    memcpy(h.data() + ogb, gb.data(), gb.size() * sizeof(GibbsS));
     memcpy(h.data() + oiw, invW.data(), invW.size() * 4);
     Bf16Tables *t = new (std::nothrow) Bf16Tables();
     if (!t) return set_error(CHEM_ENOMEM, "host allocation failed");
@@ -949,18 +994,15 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
     }
     unsigned char *base = (unsigned char *)t->d_blob;
     t->nsp = nsp;
-    t->fold = fold;
-    t->fac_chunk0 = 0;
-    for (int q = 0; q < NQ; ++q) t->fac_chunk0 |= hmask[q] ? 1 : 0;
     t->nch = nch;
-    t->b1_bytes = b1.size() * 2;
+    t->rct = rct;
+    t->fcn = fcn;
     t->blob_bytes = blob;
+    t->o_bg = (uint32_t)obg;
     t->o_b2 = (uint32_t)ob2;
     t->o_e = (uint32_t)oe;
-    t->o_coef = (uint32_t)ocf;
-    t->o_hmask = (uint32_t)ohm;
+    t->o_qi = (uint32_t)oqi;
     t->o_fq = (uint32_t)ofq;
-    t->o_gib = (uint32_t)ogb;
     t->btab = (const uint16_t *)(base + ob1);
     t->invW = (const float *)(base + oiw);
     t->status = (int *)(base + ost);
@@ -995,13 +1037,13 @@ static int sm_count(int dev)
     return cache[dev];
 }
 
-template <int NSP, bool FOLD>
+template <int NSP>
 static chem_status launch_nsp(const Bf16Params &prm, size_t smem, cudaStream_t s, int dev)
 {
     static std::atomic<uint32_t> done{0};
     const uint32_t bit = 1u << (dev & 31);
     if (!(done.load() & bit)) {
-        cudaError_t e = cudaFuncSetAttribute(k_source_bf16<NSP, FOLD>,
+        cudaError_t e = cudaFuncSetAttribute(k_source_bf16<NSP>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              227 * 1024);
         if (e != cudaSuccess)
@@ -1009,7 +1051,7 @@ static chem_status launch_nsp(const Bf16Params &prm, size_t smem, cudaStream_t s
         done.fetch_or(bit);
     }
     const int grid = std::min(prm.ntiles, sm_count(dev));
-    k_source_bf16<NSP, FOLD><<<grid, kThreads, smem, s>>>(prm);
+    k_source_bf16<NSP><<<grid, kThreads, smem, s>>>(prm);
     g_launches.fetch_add(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(CHEM_ECUDA, "split-BF16 launch: %s", cudaGetErrorString(e));
@@ -1034,8 +1076,10 @@ chem_status launch_source_bf16(const chem_mech *m, int64_t n, const float *T, co
     prm.ldO = ldO;
     prm.ns = m->ns;
     prm.nch = t->nch;
-    prm.fac_chunk0 = t->fac_chunk0;
+    prm.rct = t->rct;
+    prm.fcn = t->fcn;
     prm.bulk_out = (ldO == m->ns && (uintptr_t)om % 16 == 0) ? 1 : 0;
+    if ((n + 127) / 128 > 0x7fffffff) return set_error(CHEM_EINVAL, "n_cells too large");
     prm.ntiles = (int)((n + 127) / 128);
     prm.btab = t->btab;
     prm.blob_bytes = (uint32_t)t->blob_bytes;
@@ -1043,18 +1087,16 @@ chem_status launch_source_bf16(const chem_mech *m, int64_t n, const float *T, co
     prm.t_mid = (float)m->t_mid;
     prm.lg2R = (float)log2(kR);
     prm.status = t->status;
-    if ((int64_t)((n + 127) / 128) > 0x7fffffff) return set_error(CHEM_EINVAL, "n_cells too large");
     // shared memory layout
     auto al = [](size_t x, size_t a) { return (x + a - 1) & ~(a - 1); };
+    prm.o_bg = t->o_bg;
     prm.o_b2 = t->o_b2;
     prm.o_e = t->o_e;
-    prm.o_coef = t->o_coef;
-    prm.o_hmask = t->o_hmask;
+    prm.o_qi = t->o_qi;
     prm.o_fq = t->o_fq;
-    prm.o_gib = t->o_gib;
     size_t off = al(prm.blob_bytes, 128);
     const size_t ybytes = (size_t)128 * ldY * 4;
-    const size_t fixed = 2 * 512 + al(m->ns * 4, 128) + 2048 + BAR_COUNT * 8 + 64 + 1024;
+    const size_t fixed = 2 * 512 + al(3 * (size_t)t->nsp * 4, 128) + 2048 + BAR_COUNT * 8 + 64 + 1024;
     const bool aligned = ((uintptr_t)Y % 16 == 0) && ((uintptr_t)T % 16 == 0) && ((uintptr_t)P % 16 == 0);
     prm.stage_y = aligned && (off + ybytes + fixed <= 227 * 1024) ? 1 : 0;
     prm.o_y = (uint32_t)off;
@@ -1064,7 +1106,7 @@ chem_status launch_source_bf16(const chem_mech *m, int64_t n, const float *T, co
     prm.o_p = (uint32_t)off;
     off += 512;
     prm.o_iw = (uint32_t)off;
-    off = al(off + m->ns * 4, 128);
+    off = al(off + 3 * (size_t)t->nsp * 4, 128);
     prm.o_psum = (uint32_t)off;
     off += 4 * 128 * 4;
     prm.o_bar = (uint32_t)off;
@@ -1073,11 +1115,8 @@ chem_status launch_source_bf16(const chem_mech *m, int64_t n, const float *T, co
     if (smem > 227 * 1024)
         return set_error(CHEM_EUNSUPPORTED, "split-BF16 tables need %zu bytes of shared memory",
                          smem);
-    if (t->fold)
-        return t->nsp == 32 ? launch_nsp<32, true>(prm, smem, s, m->device)
-                            : launch_nsp<64, true>(prm, smem, s, m->device);
-    return t->nsp == 32 ? launch_nsp<32, false>(prm, smem, s, m->device)
-                        : launch_nsp<64, false>(prm, smem, s, m->device);
+    return t->nsp == 32 ? launch_nsp<32>(prm, smem, s, m->device)
+                        : launch_nsp<64>(prm, smem, s, m->device);
 }
 
 }  // namespace chem

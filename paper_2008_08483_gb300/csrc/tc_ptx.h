@@ -145,6 +145,12 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N, bool b_mn = 
            ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor of tcgen05.mma kind::f16: FP16 A and B, FP32 D, both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 // Shared-memory matrix descriptor, no swizzle: 8 x 16-byte core matrices.  K-major: lbo =
 // byte distance between core matrices adjacent in K, sbo = between 8-row groups (M/N).
 // MN-major: lbo = distance between core matrices adjacent in K, sbo = adjacent in M/N.
@@ -245,6 +251,18 @@ __device__ __forceinline__ void tmem_wait_ld_tie(uint32_t *a, uint32_t *b, uint3
         asm volatile("" : CHEM_T8(0) : : "memory");
     }
 }
+// Completion of the loads issued so far, tied to the registers of two 16-column loads.
+__device__ __forceinline__ void tmem_wait_ld_tie16(uint32_t *a, uint32_t *b)
+{
+    {
+        uint32_t *r = a;
+        asm volatile("tcgen05.wait::ld.sync.aligned;" : CHEM_T8(0), CHEM_T8(8) : : "memory");
+    }
+    {
+        uint32_t *r = b;
+        asm volatile("" : CHEM_T8(0), CHEM_T8(8) : : "memory");
+    }
+}
 #undef CHEM_T8
 
 // 16 / 8 / 4 consecutive 32-bit columns; completion awaited with tmem_wait_st.
@@ -301,6 +319,21 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
     uint32_t r;
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
     return r;
+}
+
+// {lo, hi} -> f16x2 with lo in the low half (round to nearest even)
+__device__ __forceinline__ uint32_t pack_f16x2(float lo, float hi)
+{
+    uint32_t r;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+// f16x2 -> the two values as FP32 (low half first)
+__device__ __forceinline__ void unpack_f16x2(uint32_t w, float &lo, float &hi)
+{
+    asm("{\n .reg .b16 l, h;\n mov.b32 {l, h}, %2;\n cvt.f32.f16 %0, l;\n cvt.f32.f16 %1, h;\n}"
+        : "=f"(lo), "=f"(hi)
+        : "r"(w));
 }
 
 }  // namespace tc

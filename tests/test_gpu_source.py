@@ -73,7 +73,8 @@ def as_prec(x, prec):
 
 
 PATHS = [chem.FP64, chem.FP32, chem.SPLIT_BF16]
-BF16_MAX_SPECIES = 62          # 64 padded columns: species, log2 c_tot and the normalisation
+# 64 contraction-1 columns: species, log2 c_tot, the normalisation and nine Arrhenius rows
+BF16_MAX_SPECIES = 53
 
 
 @pytest.mark.parametrize("prec", PATHS)
@@ -189,9 +190,10 @@ def with_inert_species(m, extra):
 
 
 @pytest.mark.parametrize("size,extra", [("h2air_9_21", 14), ("gri_53_325", 5)])
-def test_bf16_without_folded_arrhenius_rows(dev, size, extra):
-    """Species counts that leave fewer than nine padding columns (23 of 32, 58 of 64): the
-    split-BF16 kernel adds log2 k_f in its epilogue instead of in contraction 1."""
+def test_bf16_species_padding(dev, size, extra):
+    """Species counts between the padded column widths: 23 species (fills 34 of 64
+    contraction-1 columns) runs against the oracle; 58 species (69 columns) is refused with
+    CHEM_EUNSUPPORTED before anything is launched."""
     base, _, _ = loaded(size)
     m = with_inert_species(base, extra)
     h, om = chem.Mechanism(m), O.OracleMechanism(m)
@@ -200,6 +202,11 @@ def test_bf16_without_folded_arrhenius_rows(dev, size, extra):
     Y = np.concatenate([Yb, rng.uniform(0.0, 0.02, (len(T), extra))], axis=1)
     Y /= Y.sum(axis=1, keepdims=True)
     T, P, Y = (as_prec(x, chem.SPLIT_BF16) for x in (T, P, Y))
+    if m.n_species > BF16_MAX_SPECIES:
+        with pytest.raises(chem.ChemError) as e:
+            run(h, T, P, Y, chem.SPLIT_BF16, dev)
+        assert e.value.status == 4
+        return
     ref = O.source_term(om, T, P, Y)
     w, _ = run(h, T, P, Y, chem.SPLIT_BF16, dev)
     assert np.all(w[:, base.n_species:] == 0.0)
