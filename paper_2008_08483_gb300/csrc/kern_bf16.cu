@@ -117,9 +117,9 @@ struct Bf16Params {
 };
 
 enum {
-    BAR_BTAB, BAR_YFULL, BAR_YEMPTY, BAR_A1FULL, BAR_D1FULL0, BAR_D1FULL1, BAR_D1EMPTY0,
+    BAR_BTAB, BAR_YFULL, BAR_YEMPTY0, BAR_YEMPTY1, BAR_A1FULL, BAR_D1FULL0, BAR_D1FULL1, BAR_D1EMPTY0,
     BAR_D1EMPTY1, BAR_ZFULL, BAR_FCFULL, BAR_A2FULL0, BAR_A2FULL1, BAR_A2EMPTY0, BAR_A2EMPTY1,
-    BAR_D2FULL, BAR_XREADY, BAR_WREADY, BAR_DRAIN, BAR_COUNT
+    BAR_D2FULL, BAR_XREADY, BAR_DRAIN, BAR_COUNT
 };
 
 struct SmemCtl {
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         constexpr uint32_t E = kEpiWarps;
-        const uint32_t cnt[BAR_COUNT] = {1, 1, E, E, 1, 1, E, E, E, 1, E, E, 1, 1, 1, E, E, 2};
+        const uint32_t cnt[BAR_COUNT] = {1, 1, E, E, E, 1, 1, E, E, E, 1, E, E, 1, 1, 1, E, 2};
         for (int i = 0; i < BAR_COUNT; ++i) tc::mbar_init(BAR(i), cnt[i]);
         tc::mbar_fence_init();
         ctl->abort = 0;
@@ -272,10 +272,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
             for (uint32_t off = 0; off < bt; off += 16384)
                 tc::bulk_g2s(sbase + off, (const unsigned char *)p.btab + off,
                              min(16384u, bt - off), BAR(BAR_BTAB));
+            // The Y buffer holds Y of tile j from its load until the epilogue's prologue and z
+            // have read it; then the omega of tile j - 1 is staged in it.  Event j (barrier
+            // YEMPTY0 + (j & 1), its phase j >> 1): Y(j) read and omega(j - 1) staged (event 0:
+            // Y(0) read); two barriers, so that the epilogue running two events ahead at the
+            // end cannot alias a phase.  Before loading Y(j) this thread stores omega(j - 2)
+            // and waits until the store has read the buffer.
+            auto ywait = [&](int j) {
+                return wait_bar(BAR(BAR_YEMPTY0 + (j & 1)), (j >> 1) & 1, ctl, p.status, 1);
+            };
+            auto bulk_tile = [&](int64_t i0) { return p.stage_y && p.bulk_out && i0 + 128 <= n; };
+            auto store_omega = [&](int j) {           // omega of this CTA's tile j, if staged
+                const int64_t i0 = (int64_t)(blockIdx.x + (int64_t)j * gridDim.x) * 128;
+                if (j < 0 || !bulk_tile(i0)) return;
+                tc::bulk_s2g(p.om + i0 * p.ldO, sbase + p.o_y, (uint32_t)(128 * p.ns * 4));
+                tc::bulk_commit();
+                tc::bulk_wait_read0();
+            };
             int it = 0;
-            bool pending = false;
+            bool pending = false, okl = true;
             for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++it) {
-                if (!wait_bar(BAR(BAR_YEMPTY), (it & 1) ^ 1, ctl, p.status, 1)) break;
+                if (it > 0) {
+                    if (!(okl = ywait(it - 1))) break;
+                    store_omega(it - 2);
+                }
                 const int64_t i0 = (int64_t)t * 128;
                 if (p.stage_y && i0 + 128 <= n) {
                     const uint32_t yb = (uint32_t)(128 * p.ldY * 4);
@@ -289,8 +309,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                     pending = false;
                 }
             }
+            // the last two tiles' omega
+            if (okl && it > 0 && (okl = ywait(it - 1))) store_omega(it - 2);
+            if (okl && it > 0 && ywait(it)) store_omega(it - 1);
+            tc::bulk_wait0();                         // omega stores have landed
             // copies in flight are awaited before the CTA can exit
-            if (pending) wait_bar(BAR(BAR_YFULL), (it - 1) & 1, ctl, p.status, 1);
+            if (pending && !okl) wait_bar(BAR(BAR_YFULL), (it - 1) & 1, ctl, p.status, 1);
             wait_bar(BAR(BAR_BTAB), 0, ctl, p.status, 1);
         }
     } else if (warp == 1 || warp == kMma2Warp) {
@@ -554,7 +578,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 tc::fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(BAR(BAR_ZFULL));
-                if (lane == 0) tc::mbar_arrive(BAR(BAR_YEMPTY));   // Y(0) fully consumed
+                if (lane == 0) tc::mbar_arrive(BAR(BAR_YEMPTY0));   // event 0: Y(0) read
             }
         }
         CellF cfn;                                    // features of the next tile
@@ -634,10 +658,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 }
                 // next chunk's S read-out in flight during this chunk's store
                 if (c + 1 < nch && !(ok = load_s(c + 1, u + 1))) break;
-                // last chunk: every contraction 1 of this tile has completed, so the next
-                // tile's prologue writes its operands now and its contractions 1 run while
-                // this chunk's contraction 2 and the omega store finish
-                if (c == nch - 1 && has_next && !(ok = prologue(t_next, it + 1, cfn))) break;
                 const int ab = (int)(u & 1);
                 if (!(ok = wait_bar(BAR(BAR_A2EMPTY0 + ab), ((u >> 1) & 1) ^ 1, ctl, p.status, 3))) break;
                 tc::fence_after();
@@ -650,6 +670,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 tc::fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(BAR(BAR_A2FULL0 + ab));
+                // last chunk: every contraction 1 of this tile has completed, so the next
+                // tile's prologue writes its operands now; its contractions 1 run while this
+                // chunk's contraction 2 and the omega read-out finish
+                if (c == nch - 1 && has_next && !(ok = prologue(t_next, it + 1, cfn))) break;
                 if (c + 1 < nch) release_s(c + 1, u + 1);
             }
             if (!ok) break;
@@ -667,9 +691,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(BAR(BAR_ZFULL));
             // ---- omega -> shared (the Y buffer, read by the next tile's prologue and z
-            // already) -> one coalesced bulk store; then the buffer is free for the tile
-            // after next
-            if (p.stage_y) {
+            // already), stored by the loader thread; partial tiles and padded rows go out
+            // directly
+            if (p.stage_y && p.bulk_out && i0 + 128 <= n) {
 #pragma unroll
                 for (int bi = 0; bi < BPW; ++bi)
 #pragma unroll
@@ -678,24 +702,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                         if (k < ns) Ws[row * ns + k] = __uint_as_float(w[bi][e]);
                     }
                 tc::fence_proxy_async_smem();            // visible to the bulk store
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(BAR(BAR_WREADY));
-                if (!(ok = wait_bar(BAR(BAR_WREADY), it & 1, ctl, p.status, 3))) break;
-                if (p.bulk_out && i0 + 128 <= n) {
-                    if (ew == 0 && lane == 0) {
-                        tc::bulk_s2g(p.om + i0 * p.ldO, sbase + p.o_y, (uint32_t)(128 * ns * 4));
-                        tc::bulk_commit();
-                        tc::bulk_wait_read0();
-                    }
-                } else {
-                    for (int r = ew; r < 128; r += kEpiWarps) {
-                        const int64_t i = i0 + r;
-                        if (i >= n) break;
-                        float *orow = p.om + i * p.ldO;
-                        for (int k = lane; k < ns; k += 32) orow[k] = Ws[r * ns + k];
-                    }
-                }
-            } else if (ci < n) {                      // no staging buffer: direct stores
+            } else if (ci < n) {
                 float *orow = p.om + ci * p.ldO;
 #pragma unroll
                 for (int bi = 0; bi < BPW; ++bi)
@@ -706,11 +713,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                     }
             }
             __syncwarp();
-            if (lane == 0) tc::mbar_arrive(BAR(BAR_YEMPTY));
+            if (lane == 0) tc::mbar_arrive(BAR(BAR_YEMPTY0 + ((it + 1) & 1)));   // event it + 1
             cf = cfn;
         }
     }
-    if (warp == kEpiWarp0 && lane == 0) tc::bulk_wait0();   // omega stores have landed
     tc::fence_before();
     __syncthreads();
     if (warp == 1) {
