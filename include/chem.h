@@ -64,9 +64,10 @@ typedef enum {
     CHEM_FP64 = 0,          /* double I/O and arithmetic (SIMT) */
     CHEM_FP32 = 1,          /* float I/O; SIMT float arithmetic with double-float
                                exponent assembly */
-    CHEM_SPLIT_BF16 = 2     /* float I/O; both stoichiometric contractions on tcgen05
-                               tensor cores: log2 X split into three BF16 terms,
-                               q_net into two, FP32 accumulation in tensor memory */
+    CHEM_SPLIT_BF16 = 2     /* float I/O; the stoichiometric contractions on tcgen05
+                               tensor cores with split 16-bit operands and FP32
+                               accumulation in tensor memory: log2 X and the Arrhenius /
+                               Gibbs features as two FP16 terms, q_net as two BF16 terms */
 } chem_precision;
 
 /* Reaction kinds (chem_mech_desc.kind). */
@@ -135,8 +136,9 @@ chem_status chem_mechanism_info(const chem_mech *mech, int32_t *n_species,
  * Errors: CHEM_EINVAL (NULL pointers with n_cells > 0, n_cells < 0,
  * ldY/ldO < n_species, mechanism loaded on another device), CHEM_EUNSUPPORTED
  * (precision not built for this mechanism size: CHEM_FP64 needs 2 n_species + n_reactions
- * <= 3440, CHEM_FP32 5 n_species + n_reactions <= 6752; CHEM_SPLIT_BF16 at most 62 species,
- * 64 third-body / falloff reactions of which 32 falloff, and tables that fit in shared
+ * <= 3440, CHEM_FP32 5 n_species + n_reactions <= 6752; CHEM_SPLIT_BF16 at most 53 species
+ * (n_species + 11 contraction columns <= 64), at most 64 third-body / falloff reactions
+ * (8 per multiplier share, at most 4 of them falloff), and tables that fit in shared
  * memory), CHEM_ECUDA (launch failure).
  * Asynchronous on `stream`.
  */
@@ -315,10 +317,11 @@ chem_status chem_integrate_cells(const chem_mech *mech, int64_t n_cells, double 
  * time-step loop that must not pay an allocation's latency or implicit synchronisation).
  * The array is shared by all calls on a device: calls that overlap in time on one device
  * race on it and must not be issued.  Each call clears the part that must start at zero
- * (cell counter, failure count) on its stream.  The first call on a device sets up the
- * array's address with that device current; make it before any stream capture.
- * Additional error: CHEM_ENOMEM when the mechanism's workspace (per-warp matrices of
- * mechanisms too large for shared memory) exceeds the 1 MiB array.
+ * (cell counter, failure count) on its stream, and looks up the array's address on the
+ * current device (no allocation).  The first call on a device may load the module that
+ * holds the array; make it before any stream capture on that device.
+ * Additional error: CHEM_ENOMEM for a mechanism whose reactor matrices do not fit in
+ * shared memory (they would need per-warp matrices in device memory), whatever n_cells is.
  */
 chem_status chem_integrate_cells_noalloc(const chem_mech *mech, int64_t n_cells, double *T,
                                          const double *P, double *Y, int64_t ldY, double t_end,

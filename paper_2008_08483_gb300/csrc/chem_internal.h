@@ -157,6 +157,41 @@ struct chem_mech {
 namespace chem {
 
 chem_status set_error(chem_status st, const char *fmt, ...);
+
+// Opt-in of a kernel to more than the default dynamic shared memory on the current device,
+// cached per device.  The attribute lives in the device's context, which cudaDeviceReset
+// discards; a launcher whose launch fails therefore calls ensure(..., true) and retries
+// once (launch_opted).
+struct SmemOptIn {
+    std::atomic<uint64_t> done{0};
+    chem_status ensure(const void *func, int bytes, bool force, const char *name)
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        const uint64_t bit = 1ull << (dev & 63);
+        if (!force && (done.load() & bit)) return CHEM_OK;
+        cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return set_error(CHEM_ECUDA, "%s attribute: %s", name, cudaGetErrorString(e));
+        done.fetch_or(bit);
+        return CHEM_OK;
+    }
+};
+
+// Launch through `launch` (a callable doing the <<<>>> launch) after the opt-in; on a
+// launch error, opt in again and retry once.
+template <class F>
+chem_status launch_opted(SmemOptIn &opt, const void *func, int bytes, const char *name, F &&launch)
+{
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        chem_status st = opt.ensure(func, bytes, attempt > 0, name);
+        if (st != CHEM_OK) return st;
+        launch();
+        const cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) return CHEM_OK;
+        if (attempt > 0) return set_error(CHEM_ECUDA, "%s launch: %s", name, cudaGetErrorString(e));
+    }
+    return CHEM_OK;
+}
 // ln K_c of reaction j in temperature range r on [1, ln T, tau, tau^2, tau^3, tau^4, 1/T]
 void fold_kc(const chem_mech_desc *d, int j, int r, double out[7]);
 void clear_error();
@@ -166,6 +201,7 @@ extern std::atomic<uint64_t> g_launches;
 // workspace size for up to n_max cells, the argument checks of chem_integrate_cells, and the
 // launch itself (header clear + persistent kernel; n_dev optionally holds the cell count).
 size_t integrate_workspace_bytes(const chem_mech *m, int64_t n_max);
+size_t integrate_header_bytes();   // the part of the workspace that does not grow with n
 chem_status integrate_checks(const chem_mech *m, int64_t n, const double *T, const double *P,
                              const double *Y, int64_t ldY, double t_end, double rtol, double atol);
 chem_status integrate_launch(const chem_mech *m, int64_t n_max, const int64_t *n_dev, double *T,

@@ -16,11 +16,12 @@
 // kernel runs; nothing else needs initialising.  Calls that overlap in time on the same
 // device (different streams or host threads) race on this array and must not be issued.
 // Mechanisms whose reactor matrices do not fit in shared memory need per-warp matrices in
-// the workspace; when those exceed the array the call is rejected (CHEM_ENOMEM).
-// The first call on each device performs the set-up (cudaGetSymbolAddress of the array,
-// with that device current); make it before any stream capture on that device.
-#include <mutex>
-
+// device memory, which this entry point does not provide: they are rejected (CHEM_ENOMEM)
+// whatever the cell count, so the limit is a property of the mechanism alone.
+// Each call looks up the array's address with cudaGetSymbolAddress (which allocates
+// nothing) with the current device; a device reset therefore never leaves a stale address
+// behind.  The first call on a device may load the module that holds the array; make it
+// before any stream capture on that device.
 #include "chem_internal.h"
 
 namespace {
@@ -29,27 +30,15 @@ constexpr size_t kNoAllocScratchBytes = 1u << 20;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mu;
-void *g_scratch_ptr[kMaxDevices] = {};
-
-// Address of this device's scratch array (set up once per device, with it current).
+// Address of the scratch array on the current device, looked up on every call.
 chem_status scratch_for_current_device(void **out)
 {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return chem::set_error(CHEM_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return chem::set_error(CHEM_EUNSUPPORTED, "device index %d", dev);
-    std::lock_guard<std::mutex> g(g_setup_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return chem::set_error(CHEM_ECUDA, "cudaGetSymbolAddress of the static scratch: %s",
-                                   cudaGetErrorString(e));
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return chem::set_error(CHEM_ECUDA, "cudaGetSymbolAddress of the static scratch: %s",
+                               cudaGetErrorString(e));
+    *out = p;
     return CHEM_OK;
 }
 
@@ -67,12 +56,15 @@ extern "C" chem_status chem_integrate_cells_noalloc(const chem_mech *m, int64_t 
     chem_status st = integrate_checks(m, n, T, P, Y, ldY, t_end, rtol, atol);
     if (st != CHEM_OK) return st;
     if (n == 0) return CHEM_OK;
-    const size_t need = integrate_workspace_bytes(m, n);
-    if (need > kNoAllocScratchBytes)
+    // per-warp reactor matrices in device memory (mechanisms beyond shared memory) are not
+    // provided, whatever n is; the rest of the workspace is the fixed header
+    const size_t need = integrate_workspace_bytes(m, 1);
+    if (need > integrate_header_bytes() || need > kNoAllocScratchBytes)
         return set_error(CHEM_ENOMEM,
-                         "integrate (no allocation): needs %zu bytes of workspace, the static "
-                         "scratch holds %zu",
-                         need, kNoAllocScratchBytes);
+                         "integrate (no allocation): the mechanism's reactor matrices exceed "
+                         "shared memory and would need %zu bytes per cell-group of workspace "
+                         "beyond the static scratch's header",
+                         need - integrate_header_bytes());
     void *ws = nullptr;
     st = scratch_for_current_device(&ws);
     if (st != CHEM_OK) return st;

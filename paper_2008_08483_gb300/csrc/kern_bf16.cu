@@ -1046,22 +1046,12 @@ static int sm_count(int dev)
 template <int NSP>
 static chem_status launch_nsp(const Bf16Params &prm, size_t smem, cudaStream_t s, int dev)
 {
-    static std::atomic<uint32_t> done{0};
-    const uint32_t bit = 1u << (dev & 31);
-    if (!(done.load() & bit)) {
-        cudaError_t e = cudaFuncSetAttribute(k_source_bf16<NSP>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             227 * 1024);
-        if (e != cudaSuccess)
-            return set_error(CHEM_ECUDA, "split-BF16 attribute: %s", cudaGetErrorString(e));
-        done.fetch_or(bit);
-    }
+    static SmemOptIn opt;
     const int grid = std::min(prm.ntiles, sm_count(dev));
-    k_source_bf16<NSP><<<grid, kThreads, smem, s>>>(prm);
-    g_launches.fetch_add(1);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return set_error(CHEM_ECUDA, "split-BF16 launch: %s", cudaGetErrorString(e));
-    return CHEM_OK;
+    chem_status st = launch_opted(opt, (const void *)k_source_bf16<NSP>, 227 * 1024, "split-BF16",
+                                  [&] { k_source_bf16<NSP><<<grid, kThreads, smem, s>>>(prm); });
+    if (st == CHEM_OK) g_launches.fetch_add(1);
+    return st;
 }
 
 chem_status launch_source_bf16(const chem_mech *m, int64_t n, const float *T, const float *P,

@@ -740,19 +740,10 @@ static chem_status shape_for(const chem_mech *m, LaunchShape *out)
 }
 
 template <int MODE>
-static chem_status set_smem_attr()
+static SmemOptIn &smem_opt()
 {
-    static std::mutex mu;
-    static uint64_t done = 0;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    std::lock_guard<std::mutex> g(mu);
-    if (done & (1ull << (dev & 63))) return CHEM_OK;
-    cudaError_t e = cudaFuncSetAttribute(k_reactor<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSmemLimit);
-    if (e != cudaSuccess) return set_error(CHEM_ECUDA, "reactor kernel attribute: %s", cudaGetErrorString(e));
-    done |= 1ull << (dev & 63);
-    return CHEM_OK;
+    static SmemOptIn opt;
+    return opt;
 }
 
 static const RosCoef &coef()
@@ -781,8 +772,6 @@ static chem_status launch_pointwise(const chem_mech *m, IntegParams &p, cudaStre
     LaunchShape sh;
     chem_status st = shape_for(m, &sh);
     if (st != CHEM_OK) return st;
-    st = set_smem_attr<MODE>();
-    if (st != CHEM_OK) return st;
     p.L = sh.L;
     const int64_t blocks = (p.n + sh.wpb - 1) / sh.wpb;
     double *gmat = nullptr;
@@ -792,12 +781,12 @@ static chem_status launch_pointwise(const chem_mech *m, IntegParams &p, cudaStre
         if (e != cudaSuccess) return set_error(CHEM_ENOMEM, "%s: workspace of %zu bytes: %s", name, bytes, cudaGetErrorString(e));
     }
     p.gmat = gmat;
-    k_reactor<MODE><<<(unsigned)blocks, sh.wpb * 32, sh.smem, s>>>(m->v64, m->vint, p);
-    g_launches.fetch_add(1);
-    cudaError_t e = cudaGetLastError();
+    st = launch_opted(smem_opt<MODE>(), (const void *)k_reactor<MODE>, (int)kSmemLimit, name, [&] {
+        k_reactor<MODE><<<(unsigned)blocks, sh.wpb * 32, sh.smem, s>>>(m->v64, m->vint, p);
+    });
+    if (st == CHEM_OK) g_launches.fetch_add(1);
     if (gmat) cudaFreeAsync(gmat, s);
-    if (e != cudaSuccess) return set_error(CHEM_ECUDA, "%s launch: %s", name, cudaGetErrorString(e));
-    return CHEM_OK;
+    return st;
 }
 
 }  // namespace chem
@@ -863,6 +852,8 @@ static int64_t integrate_blocks(const LaunchShape &sh, int64_t n_max)
 
 static constexpr size_t kIntegHead = 256;   // cell queue and failure count
 
+size_t integrate_header_bytes() { return kIntegHead; }
+
 size_t integrate_workspace_bytes(const chem_mech *m, int64_t n_max)
 {
     LaunchShape sh;
@@ -885,8 +876,6 @@ chem_status integrate_launch(const chem_mech *m, int64_t n_max, const int64_t *n
 {
     LaunchShape sh;
     chem_status st = shape_for(m, &sh);
-    if (st != CHEM_OK) return st;
-    st = set_smem_attr<kModeIntegrate>();
     if (st != CHEM_OK) return st;
     const int64_t blocks = integrate_blocks(sh, n_max);
     const size_t mat = sh.L.oMat < 0 ? (size_t)blocks * sh.wpb * sh.L.n * sh.L.ldw * sizeof(double) : 0;
@@ -920,13 +909,14 @@ chem_status integrate_launch(const chem_mech *m, int64_t n_max, const int64_t *n
     p.queue = (unsigned int *)ws;
     p.gmat = mat ? (double *)((char *)ws + kIntegHead) : nullptr;
     cudaError_t e = cudaMemsetAsync(ws, 0, kIntegHead, s);
-    if (e == cudaSuccess) {
-        k_reactor<kModeIntegrate><<<(unsigned)blocks, sh.wpb * 32, sh.smem, s>>>(m->v64, m->vint, p);
-        g_launches.fetch_add(1);
-        e = cudaGetLastError();
-    }
-    if (e != cudaSuccess) return set_error(CHEM_ECUDA, "integrate launch: %s", cudaGetErrorString(e));
-    return CHEM_OK;
+    if (e != cudaSuccess) return set_error(CHEM_ECUDA, "integrate: %s", cudaGetErrorString(e));
+    st = launch_opted(smem_opt<kModeIntegrate>(), (const void *)k_reactor<kModeIntegrate>,
+                      (int)kSmemLimit, "integrate", [&] {
+                          k_reactor<kModeIntegrate><<<(unsigned)blocks, sh.wpb * 32, sh.smem, s>>>(
+                              m->v64, m->vint, p);
+                      });
+    if (st == CHEM_OK) g_launches.fetch_add(1);
+    return st;
 }
 
 chem_status integrate_checks(const chem_mech *m, int64_t n, const double *T, const double *P,

@@ -489,22 +489,6 @@ k_source_f64(MechViewF64 mv, IntView iv, int64_t n, int cpw, const double *__res
 
 constexpr size_t kMaxDynSmem = 227 * 1024;
 
-// Opt a kernel in to the full dynamic shared memory once per device.
-template <typename K>
-static chem_status smem_opt_in(K kern, std::atomic<uint32_t> &done_mask, const char *name)
-{
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const uint32_t bit = 1u << (dev & 31);
-    if (done_mask.load() & bit) return CHEM_OK;
-    cudaError_t e =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem);
-    if (e != cudaSuccess) return set_error(CHEM_ECUDA, "%s: %s", name, cudaGetErrorString(e));
-    done_mask.fetch_or(bit);
-    return CHEM_OK;
-}
-
-
 // Resident warps of a kernel on the current device (SMs x blocks per SM x warps per block),
 // queried once per mechanism and path.
 template <typename K>
@@ -534,23 +518,23 @@ chem_status launch_source_fp64(const chem_mech *m, int64_t n, const double *T, c
                                const double *Y, int64_t ldY, double *om, int64_t ldO,
                                cudaStream_t s)
 {
-    static std::atomic<uint32_t> mask{0};
+    static SmemOptIn opt;
     if (n <= 0) return CHEM_OK;
     const size_t smem =
         sizeof(double) * kF64Warps * (32 * (size_t)kCell64 + 2 * (size_t)m->ns + (size_t)m->nr);
     if (smem > kMaxDynSmem)
         return set_error(CHEM_EUNSUPPORTED, "fp64: %d species / %d reactions exceed the SIMT kernel",
                          m->ns, m->nr);
-    chem_status st = smem_opt_in(k_source_f64, mask, "fp64");
+    chem_status st = opt.ensure((const void *)k_source_f64, (int)kMaxDynSmem, false, "fp64");
     if (st != CHEM_OK) return st;
     const int cpw = cells_per_warp(n, resident_warps(m, 0, k_source_f64, kF64Warps, smem));
     const int64_t per_block = (int64_t)cpw * kF64Warps;
-    k_source_f64<<<(unsigned)((n + per_block - 1) / per_block), 32 * kF64Warps, smem, s>>>(
-        m->v64, m->vint, n, cpw, T, P, Y, ldY, om, ldO);
-    g_launches.fetch_add(1);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return set_error(CHEM_ECUDA, "fp64 launch: %s", cudaGetErrorString(e));
-    return CHEM_OK;
+    st = launch_opted(opt, (const void *)k_source_f64, (int)kMaxDynSmem, "fp64", [&] {
+        k_source_f64<<<(unsigned)((n + per_block - 1) / per_block), 32 * kF64Warps, smem, s>>>(
+            m->v64, m->vint, n, cpw, T, P, Y, ldY, om, ldO);
+    });
+    if (st == CHEM_OK) g_launches.fetch_add(1);
+    return st;
 }
 
 static size_t f32_warp_floats(const chem_mech *m, bool ann)
@@ -564,23 +548,23 @@ static chem_status launch_f32(const chem_mech *m, const KcAnnView &av, int64_t n
                               const float *P, const float *Y, int64_t ldY, float *om,
                               int64_t ldO, cudaStream_t s, const char *name)
 {
-    static std::atomic<uint32_t> mask{0};
+    static SmemOptIn opt;
     if (n <= 0) return CHEM_OK;
     const size_t smem = sizeof(float) * kF32Warps * f32_warp_floats(m, ANN);
     if (smem > kMaxDynSmem)
         return set_error(CHEM_EUNSUPPORTED, "%s: %d species / %d reactions exceed the SIMT kernel",
                          name, m->ns, m->nr);
-    chem_status st = smem_opt_in(k_source_f32<ANN>, mask, name);
+    chem_status st = opt.ensure((const void *)k_source_f32<ANN>, (int)kMaxDynSmem, false, name);
     if (st != CHEM_OK) return st;
     const int cpw =
         cells_per_warp(n, resident_warps(m, ANN ? 2 : 1, k_source_f32<ANN>, kF32Warps, smem));
     const int64_t per_block = (int64_t)cpw * kF32Warps;
-    k_source_f32<ANN><<<(unsigned)((n + per_block - 1) / per_block), 32 * kF32Warps, smem, s>>>(
-        m->v32, m->vint, av, n, cpw, T, P, Y, ldY, om, ldO);
-    g_launches.fetch_add(1);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return set_error(CHEM_ECUDA, "%s launch: %s", name, cudaGetErrorString(e));
-    return CHEM_OK;
+    st = launch_opted(opt, (const void *)k_source_f32<ANN>, (int)kMaxDynSmem, name, [&] {
+        k_source_f32<ANN><<<(unsigned)((n + per_block - 1) / per_block), 32 * kF32Warps, smem, s>>>(
+            m->v32, m->vint, av, n, cpw, T, P, Y, ldY, om, ldO);
+    });
+    if (st == CHEM_OK) g_launches.fetch_add(1);
+    return st;
 }
 
 chem_status launch_source_fp32(const chem_mech *m, int64_t n, const float *T, const float *P,

@@ -175,22 +175,14 @@ template <typename R, int MODE>
 static chem_status launch_tan(const chem_mech *m, const TanArgs<R> &a, cudaStream_t s,
                               const char *name)
 {
-    static std::atomic<uint32_t> done64{0}, done32{0};
+    static SmemOptIn done64, done32;
     const size_t per = 5 * sizeof(R) * (size_t)m->ns;
-    auto go = [&](auto kern, int blk, std::atomic<uint32_t> &done) -> chem_status {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (!(done.load() & (1u << (dev & 31)))) {
-            cudaError_t e =
-                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-            if (e != cudaSuccess) return set_error(CHEM_ECUDA, "%s: %s", name, cudaGetErrorString(e));
-            done.fetch_or(1u << (dev & 31));
-        }
-        kern<<<(unsigned)((a.n + blk - 1) / blk), blk, per * blk, s>>>(m->v64, a);
-        g_launches.fetch_add(1);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return set_error(CHEM_ECUDA, "%s launch: %s", name, cudaGetErrorString(e));
-        return CHEM_OK;
+    auto go = [&](auto kern, int blk, SmemOptIn &done) -> chem_status {
+        chem_status st = launch_opted(done, (const void *)kern, 227 * 1024, name, [&] {
+            kern<<<(unsigned)((a.n + blk - 1) / blk), blk, per * blk, s>>>(m->v64, a);
+        });
+        if (st == CHEM_OK) g_launches.fetch_add(1);
+        return st;
     };
     if (per * 64 <= 200 * 1024) return go(k_tangent<R, MODE, 64>, 64, done64);
     if (per * 32 <= 227 * 1024) return go(k_tangent<R, MODE, 32>, 32, done32);

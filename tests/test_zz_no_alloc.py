@@ -50,14 +50,17 @@ def test_noalloc_matches_integrate_cells():
     h.close()
 
 
-def test_noalloc_rejects_workspace_beyond_scratch():
+@pytest.mark.parametrize("n", [1, 64])
+def test_noalloc_rejects_workspace_beyond_scratch(n):
+    """A mechanism whose reactor matrices exceed shared memory is refused for any cell
+    count, a single cell included: the limit belongs to the mechanism."""
     B.build()
     dev = torch.device("cuda:0")
     m = synth.make_mechanism("heavy_160_1000", seed=1)   # reactor matrices exceed shared memory
     h = chem.Mechanism(m)
-    T, P, Y, _ = synth.make_ignition_states(m, 64, seed=3)
+    T, P, Y, _ = synth.make_ignition_states(m, n, seed=3)
     Tt, Pt, Yt = (torch.as_tensor(a, dtype=torch.float64, device=dev) for a in (T, P, Y))
-    status = torch.zeros((64,), dtype=torch.int32, device=dev)
+    status = torch.zeros((n,), dtype=torch.int32, device=dev)
     assert _call(h, Tt, Pt, Yt, status, 1e-9) == 2                # CHEM_ENOMEM
     assert b"static scratch" in chem.lib().chem_last_error()
     assert np.array_equal(Tt.cpu().numpy(), T)     # nothing ran
