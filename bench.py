@@ -476,7 +476,8 @@ def extras_sweep(line, h, T, P, Y, dev, stream):
 def extras_integrator(line, mech, dev, stream, n=4096, t_end=1e-2, rtol=1e-6, atol=1e-12):
     """Batched constant-pressure autoignition: 4096 reactors of the 53/325 mechanism,
     T0 ~ U[900,1400] K, P0 ~ U[1,20] atm, phi ~ U[0.5,2], integrated to 10 ms (Rodas3, FP64
-    LU and error control); the ignition delay of two reactors against the oracle's Radau."""
+    LU and error control); the ignition delay and end state of a stored sample against the
+    oracle's Radau integration."""
     import torch
     from paper_2008_08483_gb300 import chem, synth
     h = chem.Mechanism(mech)
@@ -516,9 +517,32 @@ def extras_integrator(line, mech, dev, stream, n=4096, t_end=1e-2, rtol=1e-6, at
     res["cpu_baseline"] = {"value": 2.0 / tc, "unit": "reactors/s", "cores": 1, "kind": "oracle",
                            "sample": "reactors 0 and 1, scipy Radau on the oracle right-hand "
                                      f"side and Jacobian at rtol {rtol}, atol {atol}"}
-    ref = O.integrate_reactor(om, T[0], P[0], Y[0], t_end, rtol=1e-9, atol=1e-20)
-    res["t_ign_rel_err_vs_radau"] = {"cell": 0, "err": float(abs(t_ign[0] / ref["t_ign"] - 1.0)),
-                                     "radau_rtol": 1e-9}
+    # ignition delay and 10 ms state of the stored sample (T0 / P0 / phi spread, extremes and
+    # reactors without ignition) against the oracle's Radau integration
+    # (tests/golden/ignition_53_325.json, written by make_ignition_reference.py)
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "ignition_53_325.json")) as f:
+            gold = json.load(f)
+    except OSError:
+        gold = None
+    if gold and gold["t_end"] == t_end and gold["states"]["n"] == n:
+        idx = np.array(gold["index"])
+        Tn, Yn = Tt.cpu().numpy(), Yt.cpu().numpy()
+        errs, miss = [], 0
+        for q, i in enumerate(idx):
+            tr = gold["t_ign"][q]
+            if tr is None:
+                miss += int(t_ign[i] > 0)
+            else:
+                errs.append(abs(t_ign[i] / tr - 1.0))
+        dy = [max(abs(Tn[i] / gold["y_end"][q][0] - 1.0),
+                  float(np.max(np.abs(Yn[i] - np.asarray(gold["y_end"][q][1:])))))
+              for q, i in enumerate(idx)]
+        res["t_ign_rel_err_vs_radau"] = {
+            "reactors": int(len(idx)), "igniting": len(errs),
+            "max": float(np.max(errs)), "median": float(np.median(errs)),
+            "non_igniting_reported_ignited": miss, "end_state_max_err": float(np.max(dy)),
+            "radau_rtol": gold["rtol"]}
     h.close()
     line["integrator"] = res
 

@@ -166,6 +166,34 @@ def test_ignition_delay_matches_radau(dev, mech53, ignition53):
         assert np.max(np.abs(r["Y"][q] - ref["y_end"][1:])) < 1e-5
 
 
+def test_ignition_delay_over_the_batch(dev, mech53, ignition53):
+    """A fixed sample of the 4096-reactor autoignition batch (T0 strata, the extremes of T0,
+    P0 and phi, and reactors that do not ignite by 10 ms), integrated to 10 ms at rtol 1e-6:
+    the ignition delay within 0.1 % of the oracle's Radau run (rtol 1e-10), a reactor that
+    does not ignite there not reported as ignited, and every reactor's 10 ms state within
+    1e-5 (tests/golden/ignition_53_325.json, from make_ignition_reference.py)."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "ignition_53_325.json")) as f:
+        ref = json.load(f)
+    assert ref["mechanism"] == {"size": "gri_53_325", "seed": 1}
+    assert ref["states"]["n"] == len(ignition53[0])
+    idx = np.array(ref["index"])
+    T, P, Y = (a[idx] for a in ignition53)
+    assert len(idx) >= 32 and sum(t is None for t in ref["t_ign"]) >= 2
+    h = chem.Mechanism(mech53)
+    r = _integrate(h, T, P, Y, dev, ref["t_end"], rtol=1e-6, atol=1e-12)
+    assert np.all(r["status"] == 0)
+    for q, (t_ref, y_ref) in enumerate(zip(ref["t_ign"], ref["y_end"])):
+        if t_ref is None:
+            assert not r["t_ign"][q] > 0, (idx[q], r["t_ign"][q])
+        else:
+            assert abs(r["t_ign"][q] / t_ref - 1.0) < 1e-3, (idx[q], r["t_ign"][q], t_ref)
+        assert abs(r["T"][q] / y_ref[0] - 1.0) < 1e-5, (idx[q], r["T"][q], y_ref[0])
+        assert np.max(np.abs(r["Y"][q] - np.asarray(y_ref[1:]))) < 1e-5, idx[q]
+    h.close()
+
+
 def test_invariants_along_the_batch(dev, mech53, ignition53):
     T, P, Y = ignition53
     n = 512
