@@ -44,7 +44,8 @@ def _stale(target, deps):
 
 def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     srcs = sources()
-    headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    headers = (glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
+               glob.glob(os.path.join(INCLUDE, "*.h")))
     if not force and not _stale(LIB, srcs + headers + [__file__]):
         return LIB
     os.makedirs(BUILD, exist_ok=True)

@@ -148,7 +148,9 @@ struct chem_mech {
     chem::MechViewF32 v32;
     chem::IntView vint;
     bool have_bf16;
-    void *bf16;                  // split-BF16 tables (tensor-core path), see kern_bf16.cu
+    bool bf16_wide;              // the tables are those of the large-mechanism kernel
+    void *bf16;                  // split-BF16 tables (tensor-core path): kern_bf16.cu, or
+                                 // kern_wide.cu when bf16_wide
     // resident warps of the SIMT source-term kernels on the mechanism's device (0: not yet
     // queried): FP64, FP32, FP32 with the ln K_c network
     std::atomic<int> simt_warps[3];

@@ -47,7 +47,7 @@ static float2 dsplit(double x)
     return make_float2(h, l);
 }
 
-void bf16_free_tables(void *p);
+void bf16_free_tables(chem_mech *m);
 chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d);
 
 }  // namespace chem
@@ -432,6 +432,7 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
     m->t_mid = d->t_mid;
     m->p_ref = d->p_ref;
     m->have_bf16 = false;
+    m->bf16_wide = false;
     m->bf16 = nullptr;
     if (cudaGetDevice(&m->device) != cudaSuccess) {
         delete m;
@@ -507,7 +508,7 @@ extern "C" chem_status chem_mechanism_free(chem_mech *m)
     cudaGetDevice(&cur);
     if (cur != m->device) cudaSetDevice(m->device);
     cudaDeviceSynchronize();
-    if (m->bf16) bf16_free_tables(m->bf16);
+    bf16_free_tables(m);
     cudaError_t e = cudaFree(m->d_blob);
     if (cur >= 0 && cur != m->device) cudaSetDevice(cur);
     delete m;

@@ -42,7 +42,6 @@
 // third-body sums.
 // Every mbarrier wait is bounded: on timeout the kernel records an error code in the
 // mechanism's device status word and all roles wind down.
-#include <cuda_fp16.h>
 #include <math.h>
 #include <string.h>
 
@@ -50,42 +49,15 @@
 #include <vector>
 
 #include "chem_internal.h"
+#include "kern_tc_common.cuh"
 #include "tc_ptx.h"
 
 namespace chem {
 
-constexpr int RC = 48;                 // reactions per chunk
-constexpr int RH = 16;                 // reactions per warpgroup and chunk
-constexpr int NQ = RC / RH;            // epilogue warpgroups (chunk shares)
-constexpr int kEpiWarp0 = 2;           // first epilogue warp
-constexpr int kEpiWarps = 4 * NQ;
-constexpr int kMma2Warp = kEpiWarp0 + kEpiWarps;   // issues contractions 0 and 2
-constexpr int kThreads = 32 * (kMma2Warp + 1);
-constexpr uint32_t kTmemCols = 512;
-constexpr float kLog2Floor = -1000.0f; // log2 X of an absent species: 2^x underflows to 0
-constexpr float kDead = -1.0e4f;       // log2 of a rate constant that is zero
-constexpr int kArrRows = 9;            // K rows of the Arrhenius layer: 3 features x 3 terms
-constexpr int kGibK = 32;              // K of the Gibbs contraction: 2 coefficient terms x 16
+using namespace tck;
+
 constexpr int kMaxFc = 64;             // third-body / falloff columns (8 per multiplier share)
-// what a contraction-1 column holds: log2 z_k, log2 c_tot, the normalisation, the Arrhenius
-// features 1, log2 T, 1000/T, or nothing
-enum { kColSpecies, kColLgct, kColNorm, kColOne, kColLg2T, kColItau, kColZero };
 
-// Falloff layer of slot 0..3 of a multiplier share (Sec. 2.4); neutral records (kf.w = 0)
-// leave the third-body factor M / c_tot.
-struct alignas(16) FallQ {
-    float4 kf;         // log2 k_inf = x + y log2 T + z / T; w = 1 for a falloff reaction
-    float4 k0;         // log2 k0 = x + y log2 T + z / T
-    float4 troe;       // 1 - alpha, alpha, log2(e)/T***, log2(e)/T* (Lindemann: 1, 0, 0, 0)
-    float4 t2;         // x = log2(e) T** (absent: 1e30, the term underflows to zero)
-};
-
-// per chunk share (chunk, warpgroup): its rank among the multiplier shares (-1: none; its
-// columns are 8 rank .. 8 rank + 7 of the third-body sums) and how many of its slots 0..3
-// hold falloff reactions
-struct QInfo {
-    int8_t rank, nfall, pad0, pad1;
-};
 
 struct Bf16Tables {
     int nsp, nch, rct, fcn;
@@ -122,29 +94,6 @@ enum {
     BAR_D2FULL, BAR_XREADY, BAR_DRAIN, BAR_COUNT
 };
 
-struct SmemCtl {
-    uint32_t tmem_base;
-    volatile int abort;
-};
-
-// Bounded mbarrier wait: gives up after ~2^31 cycles (about a second), or as soon as
-// another role has given up, recording `code` in the device status word.
-__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, SmemCtl *ctl, int *status,
-                                         int code)
-{
-    if (tc::mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    while (true) {
-        if (tc::mbar_try_wait_sleep(bar, parity, 20000)) return true;
-        if (ctl->abort) return false;
-        if (clock64() - t0 > (1ll << 31)) {
-            ctl->abort = 1;
-            atomicCAS(status, 0, code);
-            return false;
-        }
-    }
-}
-
 template <int NSP>
 struct Cols {                                     // tensor-memory column map
     static constexpr uint32_t A1 = 0;             // contraction-1 operand: 2 terms x NSP/2
@@ -155,60 +104,6 @@ struct Cols {                                     // tensor-memory column map
     static constexpr uint32_t D2 = FC + kMaxFc;   // omega; z (2 terms x NSP/2) at tile start
     static_assert(D2 + NSP <= kTmemCols, "tensor memory over budget");
 };
-
-// Per-cell features kept in registers by every epilogue thread.
-struct CellF {
-    float lg2T, invT, itau, T, lgct, inv_sum;
-};
-
-// Factors of slots 0..3 of a multiplier share from s = M / c_tot (Sec. 2.4): a falloff
-// slot (u < nfall) gets fac = log2(Pr / (1 + Pr) F) (F = 1 for Lindemann, the Troe form
-// otherwise), added to both exponents, and mul = 1; the others keep fac = 0, mul = s.
-__device__ __forceinline__ void falloff4(const FallQ *F, const float (&s)[8], const CellF &c,
-                                         int nfall, float (&fac)[4], float (&mul)[4])
-{
-    constexpr float kLog10_2 = 0.30102999566398120f;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        fac[u] = 0.0f;
-        mul[u] = s[u];
-        if (u < nfall) {                                          // warp-uniform
-            const float4 kf = F[u].kf, k0 = F[u].k0, tr = F[u].troe;
-            const float t2 = F[u].t2.x;
-            const float lkf = fmaf(kf.z, c.invT, fmaf(kf.y, c.lg2T, kf.x));
-            const float lk0 = fmaf(k0.z, c.invT, fmaf(k0.y, c.lg2T, k0.x));
-            const float lpr = lk0 - lkf + c.lgct + tc::lg2(fmaxf(s[u], 1e-30f));   // log2 Pr
-            float f = -tc::lg2(1.0f + tc::ex2(-lpr));                 // log2(Pr / (1 + Pr))
-            const float fc = tr.x * tc::ex2(-c.T * tr.z) + tr.y * tc::ex2(-c.T * tr.w) +
-                             tc::ex2(-t2 * c.invT);
-            const float lfc = tc::lg2(fc);                            // log2 F_cent
-            const float l10 = lfc * kLog10_2;
-            const float cc = -0.4f - 0.67f * l10, nn = 0.75f - 1.27f * l10;
-            const float x = fmaf(lpr, kLog10_2, cc);
-            const float dd = fmaf(-0.14f, x, nn);
-            // log2 F = log2 F_cent / (1 + (x / dd)^2)
-            f += lfc * __fdividef(dd * dd, fmaf(dd, dd, x * x));
-            fac[u] = f;
-            mul[u] = 1.0f;
-        }
-    }
-}
-
-// two values -> two packed FP16x2 words (hi, lo terms; value a in the low halves)
-__device__ __forceinline__ void split2h(float a, float b, uint32_t &h, uint32_t &l)
-{
-    h = tc::pack_f16x2(a, b);
-    float ha, hb;
-    tc::unpack_f16x2(h, ha, hb);
-    l = tc::pack_f16x2(a - ha, b - hb);
-}
-
-// two values -> two packed BF16x2 words (hi, lo terms; value a in the low halves)
-__device__ __forceinline__ void split2x2(float a, float b, uint32_t &h, uint32_t &l)
-{
-    h = tc::pack_bf16x2(a, b);
-    l = tc::pack_bf16x2(a - __uint_as_float(h << 16), b - __uint_as_float(h & 0xFFFF0000u));
-}
 
 template <int NSP>
 __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
@@ -730,53 +625,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
 // host side: tables, launch
 // ---------------------------------------------------------------------------------------
 
-static uint16_t bf16_of_int(int v)
-{
-    float f = (float)v;
-    uint32_t u;
-    memcpy(&u, &f, 4);
-    return (uint16_t)(u >> 16);              // exact for |v| <= 256
-}
-
-static uint16_t bf16_rn(float f)
-{
-    uint32_t u;
-    memcpy(&u, &f, 4);
-    return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);   // nearest, ties to even
-}
-
-static double f_of_bf16(uint16_t h)
-{
-    const uint32_t u = (uint32_t)h << 16;
-    float f;
-    memcpy(&f, &u, 4);
-    return f;
-}
-
-static uint16_t f16_rn(double x)
-{
-    const __half_raw r = __float2half_rn((float)x);
-    return r.x;
-}
-
-static double f_of_f16(uint16_t u)
-{
-    __half_raw r;
-    r.x = u;
-    return (double)__half2float(__half(r));
-}
-
-static uint16_t f16_of_int(int v) { return f16_rn((double)v); }   // exact for |v| <= 2048
-
-// x = t[0] + t[1] + ..., each term the nearest FP16 of the remaining residual
-template <int N>
-static void f16_split(double x, uint16_t (&t)[N])
-{
-    for (int i = 0; i < N; ++i) {
-        t[i] = f16_rn(x);
-        x -= f_of_f16(t[i]);
-    }
-}
+chem_status wide_build_tables(chem_mech *m, const chem_mech_desc *d, void **out);
+void wide_free_tables(void *p);
+int *wide_status_word(const void *p);
+chem_status wide_check(const void *p);
+chem_status launch_source_wide(const chem_mech *m, const void *tables, int64_t n, const float *T,
+                               const float *P, const float *Y, int64_t ldY, float *om, int64_t ldO,
+                               cudaStream_t s);
 
 chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
 {
@@ -787,9 +642,21 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
     int nsp = ns + 2 + kArrRows;
     if (nsp <= 32) nsp = 32;
     else if (nsp <= 64) nsp = 64;
-    else
-        return set_error(CHEM_EUNSUPPORTED, "split-BF16 path supports up to %d species",
-                         64 - 2 - kArrRows);
+    else {
+        // larger mechanisms: operands in shared memory, tables streamed (kern_wide.cu)
+        void *w = nullptr;
+        chem_status st = wide_build_tables(m, d, &w);
+        if (st != CHEM_OK) return st;
+        st = wide_check(w);
+        if (st != CHEM_OK) {
+            wide_free_tables(w);
+            return st;
+        }
+        m->bf16 = w;
+        m->bf16_wide = true;
+        m->have_bf16 = true;
+        return CHEM_OK;
+    }
     const int kf0 = ns + 2;
     const int nrp = ((nr + 15) / 16) * 16;
     const int nch = (nrp + RC - 1) / RC;
@@ -1018,29 +885,23 @@ chem_status bf16_build_tables(chem_mech *m, const chem_mech_desc *d)
     return CHEM_OK;
 }
 
-void bf16_free_tables(void *p)
+void bf16_free_tables(chem_mech *m)
 {
-    Bf16Tables *t = (Bf16Tables *)p;
-    if (!t) return;
-    cudaFree(t->d_blob);
-    delete t;
+    if (!m->bf16) return;
+    if (m->bf16_wide) {
+        wide_free_tables(m->bf16);
+    } else {
+        Bf16Tables *t = (Bf16Tables *)m->bf16;
+        cudaFree(t->d_blob);
+        delete t;
+    }
+    m->bf16 = nullptr;
 }
 
 int *bf16_status_word(const chem_mech *m)
 {
-    return m->have_bf16 ? ((Bf16Tables *)m->bf16)->status : nullptr;
-}
-
-static int sm_count(int dev)
-{
-    static int cache[64] = {0};
-    if (dev < 0 || dev >= 64) return 148;
-    if (!cache[dev]) {
-        int v = 0;
-        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-        cache[dev] = v > 0 ? v : 148;
-    }
-    return cache[dev];
+    if (!m->have_bf16) return nullptr;
+    return m->bf16_wide ? wide_status_word(m->bf16) : ((Bf16Tables *)m->bf16)->status;
 }
 
 template <int NSP>
@@ -1060,6 +921,7 @@ chem_status launch_source_bf16(const chem_mech *m, int64_t n, const float *T, co
 {
     if (!m->have_bf16)
         return set_error(CHEM_EUNSUPPORTED, "split-BF16 path not available for this mechanism");
+    if (m->bf16_wide) return launch_source_wide(m, m->bf16, n, T, P, Y, ldY, om, ldO, s);
     const Bf16Tables *t = (const Bf16Tables *)m->bf16;
     Bf16Params prm;
     memset(&prm, 0, sizeof prm);

@@ -73,8 +73,10 @@ def as_prec(x, prec):
 
 
 PATHS = [chem.FP64, chem.FP32, chem.SPLIT_BF16]
-# 64 contraction-1 columns: species, log2 c_tot, the normalisation and nine Arrhenius rows
-BF16_MAX_SPECIES = 53
+# the split-precision path: tables resident in shared memory up to 53 species (64 contraction-1
+# columns: species, log2 c_tot, the normalisation and nine Arrhenius rows), streamed beyond,
+# up to 192 species (omega columns in tensor memory)
+BF16_MAX_SPECIES = 192
 
 
 @pytest.mark.parametrize("prec", PATHS)
@@ -175,6 +177,19 @@ def test_full_size_sampled(dev, prec):
     assert cell_err(w[idx], ref).max() <= TOL[prec]
 
 
+def test_full_size_sampled_160_1000(dev):
+    """160 species / 1000 reactions at 2^18 cells (the large-mechanism workload's launch) on
+    the split-precision path: sampled cells and the last cell against the oracle."""
+    m, h, om = loaded("heavy_160_1000")
+    n = 1 << 18
+    T, P, Y = states(m, "heavy_160_1000", n, seed=1234)
+    T, P, Y = (as_prec(x, chem.SPLIT_BF16) for x in (T, P, Y))
+    w, _ = run(h, T, P, Y, chem.SPLIT_BF16, dev)
+    idx = np.concatenate([synth.subset_indices(n, 1024), [0, n - 1]])
+    ref = O.source_term(om, T[idx], P[idx], Y[idx])
+    assert cell_err(w[idx], ref).max() <= TOL[chem.SPLIT_BF16]
+
+
 def with_inert_species(m, extra):
     """The mechanism with `extra` species appended that take part in no reaction (copies of
     the first species' thermodynamics and composition, default third-body efficiency)."""
@@ -191,9 +206,9 @@ def with_inert_species(m, extra):
 
 @pytest.mark.parametrize("size,extra", [("h2air_9_21", 14), ("gri_53_325", 5)])
 def test_bf16_species_padding(dev, size, extra):
-    """Species counts between the padded column widths: 23 species (fills 34 of 64
-    contraction-1 columns) runs against the oracle; 58 species (69 columns) is refused with
-    CHEM_EUNSUPPORTED before anything is launched."""
+    """Species counts between the padded column widths: 23 species (34 of 64 contraction-1
+    columns, tables resident in shared memory) and 58 species (69 columns, past the resident
+    tables: the streamed-table kernel), both against the oracle."""
     base, _, _ = loaded(size)
     m = with_inert_species(base, extra)
     h, om = chem.Mechanism(m), O.OracleMechanism(m)
