@@ -46,10 +46,10 @@ def peaks():
         return 6800.0, 1900.0, "fallback"
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one 2^20-cell launch of the
-# split-BF16 kernel from the ncu capture summarised in
-# profiles/k_source_bf16_gri53_325_2p20cells.md; valid only for the kernel source it was
-# taken on (compared by hash, else reported as null).
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
+# split-precision kernel k_source_bf16 on 2^20 cells of the 53/325 workload, from one ncu
+# capture of that launch (--set full, --clock-control none); valid only for the kernel source
+# it was taken on (compared by hash, else reported as null).
 NCU_TRAFFIC = {"source": "paper_2008_08483_gb300/csrc/kern_bf16.cu",
                "sha256": "d4fa488ed111aec4cab8845ff67f75f986699c0f930a5aa8442010eb39e3f5d0",
                "bytes_per_launch": 407_946_752, "cells": 1 << 20}
@@ -566,6 +566,13 @@ def extras_heavy(line, dev, stream, n=1 << 18):
             ms = time_device(lambda: chem.source_term(h, *din, p, out=o, stream=stream),
                              5, 2, stream, 1, dev)
             res[name] = {"cells_per_s": n / (ms * 1e-3), "ms_per_call": ms}
+            if name == "split_bf16":
+                # the paper's dense form: 6 N_S N_R flops per cell; 4 (2 + 2 N_S) bytes
+                hbm, tfl, _ = peaks()
+                cps = n / (ms * 1e-3)
+                flops = 6 * mech.n_species * mech.n_reactions
+                res[name]["tensor_algorithmic_frac"] = cps * flops / (tfl * 1e12)
+                res[name]["hbm_frac"] = cps * 4 * (2 + 2 * mech.n_species) / (hbm * 1e9)
         except chem.ChemError as e:
             res[name] = {"status": str(e)}
     # (T, ln C) states of the first 256 cells: C_k = rho Y_k / W_k, rho = P / (R T sum Y/W)

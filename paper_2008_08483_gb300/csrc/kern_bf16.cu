@@ -233,27 +233,43 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                             break;
                         tc::fence_after();
                         const int rcc = c == nch - 1 ? p.rct : RC;
-                        const uint32_t d = tmem + CL::S0 + (uint32_t)b * (2 * RC);
+                        uint32_t d = tmem + CL::S0 + (uint32_t)b * (2 * RC), dr = d + rcc;
                         const uint32_t id1 = tc::idesc_f16_f32(128, 2 * rcc);
+                        const uint32_t idg = tc::idesc_f16_f32(128, rcc);
                         const uint32_t bc = b1 + (uint32_t)c * (2 * RC * NSP * 2);
+                        const uint32_t gc = bg + (uint32_t)c * (RC * kGibK * 2);
+                        // every operand address before the burst of MMAs
+                        uint64_t bd[NSP / 16], gd[2];
+                        uint32_t aa[2][NSP / 16], ag[2];
+#pragma unroll
+                        for (int kk = 0; kk < NSP / 16; ++kk) {
+                            bd[kk] = tc::sdesc_noswz(bc + kk * 256, 128, (NSP / 8) * 128);
+                            aa[0][kk] = tmem + CL::A1 + kk * 8;
+                            aa[1][kk] = tmem + CL::A1 + NSP / 2 + kk * 8;
+                            tc::pin(bd[kk]);
+                            tc::pin(aa[0][kk]);
+                            tc::pin(aa[1][kk]);
+                        }
+#pragma unroll
+                        for (int tt = 0; tt < 2; ++tt) {
+                            gd[tt] = tc::sdesc_noswz(gc + tt * 256, 128, (kGibK / 8) * 128);
+                            ag[tt] = tmem + CL::AG + tt * 8;
+                            tc::pin(gd[tt]);
+                            tc::pin(ag[tt]);
+                        }
+                        tc::pin(d);
+                        tc::pin(dr);
 #pragma unroll
                         for (int s = 0; s < 2; ++s)
 #pragma unroll
                             for (int kk = 0; kk < NSP / 16; ++kk)
-                                tc::mma_ts(d, tmem + CL::A1 + s * (NSP / 2) + kk * 8,
-                                           tc::sdesc_noswz(bc + kk * 256, 128, (NSP / 8) * 128),
-                                           id1, (s | kk) != 0);
+                                tc::mma_ts(d, aa[s][kk], bd[kk], id1, (s | kk) != 0);
                         // Gibbs layer into the reverse half: feature term s against the
                         // coefficient terms 0 .. 1 - s
-                        const uint32_t idg = tc::idesc_f16_f32(128, rcc);
-                        const uint32_t gc = bg + (uint32_t)c * (RC * kGibK * 2);
 #pragma unroll
                         for (int s = 0; s < 2; ++s)
 #pragma unroll
-                            for (int tt = 0; tt < 2 - s; ++tt)
-                                tc::mma_ts(d + rcc, tmem + CL::AG + s * 8,
-                                           tc::sdesc_noswz(gc + tt * 256, 128, (kGibK / 8) * 128),
-                                           idg, 1);
+                            for (int tt = 0; tt < 2 - s; ++tt) tc::mma_ts(dr, ag[s], gd[tt], idg, 1);
                         tc::commit(BAR(BAR_D1FULL0 + b));
                     }
                 }
@@ -267,14 +283,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                 for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x, ++it) {
                     if (!(ok = wait_bar(BAR(BAR_ZFULL), it & 1, ctl, p.status, 2))) break;
                     tc::fence_after();
+                    {
+                        uint64_t ed[2][NSP / 16];
+                        uint32_t za[2][NSP / 16], dfc = tmem + CL::FC;
 #pragma unroll
-                    for (int s = 0; s < 3; ++s)
+                        for (int kk = 0; kk < NSP / 16; ++kk) {
+                            ed[0][kk] = tc::sdesc_noswz(be + kk * 256, 128, (NSP / 8) * 128);
+                            ed[1][kk] = tc::sdesc_noswz(be + p.fcn * NSP * 2 + kk * 256, 128, (NSP / 8) * 128);
+                            za[0][kk] = tmem + CL::D2 + kk * 8;
+                            za[1][kk] = tmem + CL::D2 + NSP / 2 + kk * 8;
+                            tc::pin(ed[0][kk]);
+                            tc::pin(ed[1][kk]);
+                            tc::pin(za[0][kk]);
+                            tc::pin(za[1][kk]);
+                        }
+                        tc::pin(dfc);
+                        // z hi . E hi, z hi . E lo, z lo . E hi
 #pragma unroll
-                        for (int kk = 0; kk < NSP / 16; ++kk)
-                            tc::mma_ts(tmem + CL::FC, tmem + CL::D2 + (s == 2 ? NSP / 2 : 0) + kk * 8,
-                                       tc::sdesc_noswz(be + (s == 1 ? p.fcn * NSP * 2 : 0) + kk * 256,
-                                                       128, (NSP / 8) * 128),
-                                       id0, (s | kk) != 0);
+                        for (int s = 0; s < 3; ++s)
+#pragma unroll
+                            for (int kk = 0; kk < NSP / 16; ++kk)
+                                tc::mma_ts(dfc, za[s == 2][kk], ed[s == 1][kk], id0, (s | kk) != 0);
+                    }
                     tc::commit(BAR(BAR_FCFULL));
                     for (int c = 0; c < nch; ++c, ++u) {
                         const int ab = (int)(u & 1);
@@ -282,14 +312,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_bf16(const Bf16Params p)
                             break;
                         tc::fence_after();
                         const int rcc = c == nch - 1 ? p.rct : RC;
+                        const int nk = rcc / 16;
                         const uint32_t bc = b2 + (uint32_t)c * (NSP * RC * 2);
                         const uint32_t a2 = tmem + CL::A2 + (uint32_t)ab * RC;
+                        uint64_t bd[RC / 16];
+                        uint32_t aa[2][RC / 16], dd = tmem + CL::D2;
+#pragma unroll
+                        for (int kk = 0; kk < RC / 16; ++kk) {
+                            bd[kk] = tc::sdesc_noswz(bc + kk * 256, 128, (rcc / 8) * 128);
+                            aa[0][kk] = a2 + kk * 8;
+                            aa[1][kk] = a2 + RC / 2 + kk * 8;
+                            tc::pin(bd[kk]);
+                            tc::pin(aa[0][kk]);
+                            tc::pin(aa[1][kk]);
+                        }
+                        tc::pin(dd);
 #pragma unroll
                         for (int s = 0; s < 2; ++s)
-                            for (int kk = 0; kk < rcc / 16; ++kk)
-                                tc::mma_ts(tmem + CL::D2, a2 + s * (RC / 2) + kk * 8,
-                                           tc::sdesc_noswz(bc + kk * 256, 128, (rcc / 8) * 128), id2,
-                                           (c | s | kk) != 0);
+#pragma unroll
+                            for (int kk = 0; kk < RC / 16; ++kk)
+                                if (kk < nk) tc::mma_ts(dd, aa[s][kk], bd[kk], id2, (c | s | kk) != 0);
                         tc::commit(BAR(BAR_A2EMPTY0 + ab));
                     }
                     if (ok) tc::commit(BAR(BAR_D2FULL));

@@ -160,6 +160,11 @@ __device__ __forceinline__ uint64_t sdesc_noswz(uint32_t saddr, uint32_t lbo, ui
            ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
 
+// Materialise a value here: MMA operands computed before a burst of tcgen05.mma, so that
+// no dependent arithmetic sits between the (blocking) MMA issues.
+__device__ __forceinline__ void pin(uint64_t &x) { asm volatile("" : "+l"(x)); }
+__device__ __forceinline__ void pin(uint32_t &x) { asm volatile("" : "+r"(x)); }
+
 // D[tmem] (+)= A[tmem] * B[smem]^T, cta_group::1, kind::f16
 __device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t idesc,
                                        uint32_t accumulate)
