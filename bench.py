@@ -220,6 +220,21 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------------------
 
+EXTRAS = ("paths", "sweep", "integrator", "heavy", "kc_ann", "serving")
+
+
+def selected_extras(args):
+    if args.no_extras or args.extras == "none":
+        return set()
+    if args.extras == "all":
+        return set(EXTRAS)
+    want = {x.strip() for x in args.extras.split(",") if x.strip()}
+    bad = want - set(EXTRAS)
+    if bad:
+        raise SystemExit(f"unknown --extras section(s): {sorted(bad)}")
+    return want
+
+
 def time_device(fn, steps, warmup, stream, ws, device):
     import torch
     for _ in range(warmup):
@@ -249,7 +264,10 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=60.0,
                     help="reference arm: oracle seconds for the whole run (sample size)")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the secondary precision paths and the CPU baseline")
+                    help="skip every secondary section (same as --extras none)")
+    ap.add_argument("--extras", default="all",
+                    help="comma list of secondary sections to run after the headline: "
+                         + ",".join(EXTRAS) + " (or all, none)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -336,13 +354,20 @@ def main():
     else:
         measure_e2e(line, h, T, P, Y, dev_in, prec, ns, elt, ws, dev, stream, args)
 
-    if rank == 0 and not args.no_extras:
-        extras(line, h, mech, T, P, Y, dev, dev32, out32, ns, prec_name, stream, args)
-        extras_sweep(line, h, T, P, Y, dev, stream)
-        extras_integrator(line, mech, dev, stream)
-        extras_heavy(line, dev, stream)
-        extras_kc_ann(line, dev, stream)
-        extras_serving(line)
+    want = selected_extras(args)
+    if rank == 0:
+        if "paths" in want:
+            extras(line, h, mech, T, P, Y, dev, dev32, out32, ns, prec_name, stream, args)
+        if "sweep" in want:
+            extras_sweep(line, h, T, P, Y, dev, stream)
+        if "integrator" in want:
+            extras_integrator(line, mech, dev, stream)
+        if "heavy" in want:
+            extras_heavy(line, dev, stream)
+        if "kc_ann" in want:
+            extras_kc_ann(line, dev, stream)
+        if "serving" in want:
+            extras_serving(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
     h.close()
