@@ -662,13 +662,17 @@ def extras_kc_ann(line, dev, stream, n=100_000):
     line["kc_ann"] = res
 
 
-def extras_serving(line, n_ranks=64, req_per_rank=1, seed=42, budget=8 << 30):
-    """Serving: 64 simulated detonation-channel ranks (host threads) offload requests of
-    cells ~ logU[64, 65536] with a mechanism from {9/21, 53/325} and a kind from {source term
-    (split BF16), an integration over dt = 1e-8 s (adaptive, FP64)}, states from a ZND-like
-    profile along each rank's channel (a request takes a contiguous segment).  First all
-    requests at once (saturated cells/s), then Poisson arrivals offering 50 % and 80 % of it;
-    p50 / p99 of submit-to-result latency at each load."""
+def extras_serving(line, n_ranks=64, seed=42, budget=8 << 30, src_per_rank=16, mix_per_rank=3):
+    """Serving: 64 simulated detonation-channel ranks (host threads, one submitter and one
+    poller each) offload requests of cells ~ logU[64, 65536] with a mechanism from {9/21,
+    53/325}; a request is a contiguous segment of a ZND-like channel profile (T 300 -> 3000 K,
+    P 1 -> 30 atm, unburnt -> products).  Two request pools:
+      source : 16 source-term requests (split BF16) per rank (1024);
+      mixed  : 3 requests per rank (192), half source terms, half integrations over
+               dt = 1e-8 s (adaptive Rodas3, FP64, rtol 1e-6, atol 1e-10).
+    Each pool runs once with every request at once (saturated cells/s), then with Poisson
+    arrivals offering a fraction of that rate.  Latency is submit -> results in the caller's
+    host arrays; p50 / p99 are reported overall and per request kind."""
     import threading
     from paper_2008_08483_gb300 import chem, synth
     mechs = [synth.make_mechanism("h2air_9_21", seed=MECH_SEED),
@@ -676,25 +680,31 @@ def extras_serving(line, n_ranks=64, req_per_rank=1, seed=42, budget=8 << 30):
     hs = [chem.Mechanism(m) for m in mechs]
     srv = chem.Server(hs, budget)
     rng = np.random.default_rng(np.random.PCG64(seed))
-    reqs = []
-    for rank in range(n_ranks):
-        for q in range(req_per_rank):
-            mi = int(rng.integers(0, 2))
-            m = mechs[mi]
-            n = int(np.exp(rng.uniform(np.log(64), np.log(65536))))
-            s0 = rng.uniform(0.0, 0.95)
-            s = s0 + 0.05 * np.arange(n) / n
-            T, P, Y = synth.make_znd_states(m, n, seed=seed + 1000 * rank + q, s=s)
-            if rng.uniform() < 0.5:
-                reqs.append(dict(rank=rank, mi=mi, kind=chem.REQ_SOURCE, T=T.astype(np.float32),
-                                 P=P.astype(np.float32),
-                                 Y=np.ascontiguousarray(Y.astype(np.float32)),
-                                 out=np.empty(Y.shape, np.float32)))
-            else:
-                reqs.append(dict(rank=rank, mi=mi, kind=chem.REQ_INTEGRATE, T=T, P=P,
-                                 Y=np.ascontiguousarray(Y), Tout=np.empty_like(T),
-                                 Yout=np.empty_like(Y), st=np.empty(n, np.int32)))
-    cells = np.array([r["T"].shape[0] for r in reqs])
+    n_chan = 1 << 17                                   # channel profile per mechanism
+    chan = []
+    for mi, m in enumerate(mechs):
+        T, P, Y = synth.make_znd_states(m, n_chan, seed=seed + mi, s=np.arange(n_chan) / n_chan)
+        chan.append(dict(T64=T, P64=P, Y64=np.ascontiguousarray(Y), T32=T.astype(np.float32),
+                         P32=P.astype(np.float32), Y32=np.ascontiguousarray(Y.astype(np.float32))))
+
+    def make_pool(per_rank, p_integrate):
+        reqs = []
+        for rank in range(n_ranks):
+            for _ in range(per_rank):
+                mi = int(rng.integers(0, 2))
+                n = int(np.exp(rng.uniform(np.log(64), np.log(65536))))
+                i0 = int(rng.integers(0, n_chan - n + 1))
+                c, sl = chan[mi], slice(i0, i0 + n)
+                if rng.uniform() >= p_integrate:
+                    reqs.append(dict(rank=rank, mi=mi, kind=chem.REQ_SOURCE, T=c["T32"][sl],
+                                     P=c["P32"][sl], Y=c["Y32"][sl],
+                                     out=np.empty((n, mechs[mi].n_species), np.float32)))
+                else:
+                    reqs.append(dict(rank=rank, mi=mi, kind=chem.REQ_INTEGRATE, T=c["T64"][sl],
+                                     P=c["P64"][sl], Y=c["Y64"][sl], Tout=np.empty(n),
+                                     Yout=np.empty((n, mechs[mi].n_species)),
+                                     st=np.empty(n, np.int32)))
+        return reqs
 
     def submit(r):
         if r["kind"] == chem.REQ_SOURCE:
@@ -704,16 +714,17 @@ def extras_serving(line, n_ranks=64, req_per_rank=1, seed=42, budget=8 << 30):
                           rtol=1e-6, atol=1e-10, status=r["st"], T_out=r["Tout"],
                           Y_out=r["Yout"])
 
-    def run(arrivals):
-        """arrivals[i]: submit time (s after start) of request i; one submitting and one
-        polling thread per rank.  Returns (makespan s, latencies ms, failed count)."""
-        lat = [None] * len(reqs)
+    def run(reqs, arrivals):
+        """arrivals[i]: submit time (s after start) of request i.  Returns the run's figures."""
+        res = [None] * len(reqs)
         tick = [None] * len(reqs)
         evs = [threading.Event() for _ in reqs]
+        mine = [[i for i, r in enumerate(reqs) if r["rank"] == k] for k in range(n_ranks)]
+        i0 = srv.info()
         t0 = time.perf_counter() + 0.05
 
         def sub(rank):
-            for i in [i for i, r in enumerate(reqs) if r["rank"] == rank]:
+            for i in sorted(mine[rank], key=lambda i: arrivals[i]):
                 d = t0 + arrivals[i] - time.perf_counter()
                 if d > 0:
                     time.sleep(d)
@@ -721,10 +732,9 @@ def extras_serving(line, n_ranks=64, req_per_rank=1, seed=42, budget=8 << 30):
                 evs[i].set()
 
         def pol(rank):
-            for i in [i for i, r in enumerate(reqs) if r["rank"] == rank]:
+            for i in sorted(mine[rank], key=lambda i: arrivals[i]):
                 evs[i].wait()
-                res = srv.poll(tick[i], -1)
-                lat[i] = (res["latency_us"] * 1e-3, res["status"])
+                res[i] = srv.poll(tick[i], -1)
 
         th = [threading.Thread(target=f, args=(k,)) for k in range(n_ranks) for f in (sub, pol)]
         for t in th:
@@ -732,39 +742,65 @@ def extras_serving(line, n_ranks=64, req_per_rank=1, seed=42, budget=8 << 30):
         for t in th:
             t.join()
         span = time.perf_counter() - t0
-        return span, np.array([x[0] for x in lat]), sum(1 for x in lat if x[1] != 0)
-
-    span, l_sat, bad = run(np.zeros(len(reqs)))
-    sat = cells.sum() / span
-    res = {"workload": f"{n_ranks} ranks x {req_per_rank} requests, cells ~ logU[64, 65536], "
-                       "9/21 or 53/325, source term (split BF16) or integration over 1e-8 s "
-                       "(adaptive Rodas3, FP64, rtol 1e-6, atol 1e-10), ZND-like states", "requests": len(reqs),
-           "cells": int(cells.sum()), "saturated_cells_per_s": sat,
-           "saturated_p50_ms": float(np.median(l_sat)), "saturated_p99_ms":
-           float(np.quantile(l_sat, 0.99)), "failed": bad, "loads": []}
-    mean_cells = cells.mean()
-    for frac in (0.5, 0.8):
-        lam = frac * sat / mean_cells                 # requests per second, all ranks
-        gaps = rng.exponential(1.0 / lam, len(reqs))
-        order = rng.permutation(len(reqs))
-        arr = np.empty(len(reqs))
-        arr[order] = np.cumsum(gaps)
-        i0 = srv.info()
-        span, l, bad = run(arr)
         i1 = srv.info()
-        res["loads"].append({"offered_frac": frac, "offered_cells_per_s": frac * sat,
-                             "achieved_cells_per_s": cells.sum() / span,
-                             "p50_ms": float(np.median(l)), "p99_ms": float(np.quantile(l, 0.99)),
-                             "batches": int(i1["batches"] - i0["batches"]),
-                             "max_batch_requests": int(i1["max_batch_requests"]), "failed": bad})
+        cells = np.array([r["T"].shape[0] for r in reqs])
+        lat = np.array([x["latency_us"] * 1e-3 for x in res])
+        kinds = np.array([r["kind"] for r in reqs])
+        out = {"requests": len(reqs), "cells": int(cells.sum()), "seconds": span,
+               "cells_per_s": cells.sum() / span,
+               "p50_ms": float(np.median(lat)), "p99_ms": float(np.quantile(lat, 0.99)),
+               "batches": int(i1["batches"] - i0["batches"]),
+               "max_batch_requests": int(i1["max_batch_requests"]),
+               "memory_waits": int(i1["memory_waits"] - i0["memory_waits"]),
+               "failed": sum(1 for x in res if x["status"] != 0)}
+        for k, name in ((chem.REQ_SOURCE, "source"), (chem.REQ_INTEGRATE, "integrate")):
+            sel = kinds == k
+            if not sel.any():
+                continue
+            d = {"requests": int(sel.sum()), "cells": int(cells[sel].sum()),
+                 "p50_ms": float(np.median(lat[sel])), "p99_ms": float(np.quantile(lat[sel], 0.99))}
+            if k == chem.REQ_INTEGRATE:
+                acc = sum(res[i]["steps_accepted"] for i in np.flatnonzero(sel))
+                rej = sum(res[i]["steps_rejected"] for i in np.flatnonzero(sel))
+                d.update(steps_accepted_per_cell=acc / cells[sel].sum(),
+                         steps_rejected_per_cell=rej / cells[sel].sum())
+            out[name] = d
+        return out
+
+    def poisson(reqs, rate_cells):
+        lam = rate_cells / np.mean([r["T"].shape[0] for r in reqs])   # requests per second
+        arr = np.empty(len(reqs))
+        arr[rng.permutation(len(reqs))] = np.cumsum(rng.exponential(1.0 / lam, len(reqs)))
+        return arr
+
+    res = {"workload": f"{n_ranks} ranks; cells ~ logU[64, 65536]; 9/21 or 53/325; "
+                       "source term (split BF16) or integration over 1e-8 s (adaptive Rodas3, "
+                       "FP64, rtol 1e-6, atol 1e-10); segments of a ZND-like channel profile",
+           "budget_bytes": int(budget)}
+    for name, per_rank, p_int, fracs in (("source", src_per_rank, 0.0, (0.5, 0.8)),
+                                         ("mixed", mix_per_rank, 0.5, (0.8,))):
+        reqs = make_pool(per_rank, p_int)
+        sat = run(reqs, np.zeros(len(reqs)))
+        pool = {"saturated": sat, "loads": []}
+        for frac in fracs:
+            r = run(reqs, poisson(reqs, frac * sat["cells_per_s"]))
+            r["offered_frac"] = frac
+            r["offered_cells_per_s"] = frac * sat["cells_per_s"]
+            pool["loads"].append(r)
+        res[name] = pool
+        del reqs
     info = srv.info()
-    res.update(graphs_captured=int(info["graphs_captured"]), slot_cells=int(info["slot_cells"]),
-               device_bytes=int(info["device_bytes"]))
+    res.update(graphs_captured=int(info["graphs_captured"]), graph_updates=int(info["graph_updates"]),
+               graph_launches=int(info["graph_launches"]), lanes=int(info["n_slots"]),
+               bytes_in_use_max=int(info["bytes_in_use_max"]), device_bytes=int(info["device_bytes"]),
+               source_sms=int(info["source_sms"]), integrate_sms=int(info["integrate_sms"]),
+               green_contexts=bool(info["green_contexts"]))
     srv.close()
     for h in hs:
         h.close()
     line["serving"] = res
-    line["p99_latency_ms"] = res["loads"][-1]["p99_ms"]
+    line["p99_latency_ms"] = {"source_only_at_0.8": res["source"]["loads"][-1]["p99_ms"],
+                              "mixed_at_0.8": res["mixed"]["loads"][-1]["p99_ms"]}
 
 
 if __name__ == "__main__":

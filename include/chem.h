@@ -342,15 +342,23 @@ chem_status chem_rosenbrock_tableau(int32_t *stages, double *gamma_ii, double *a
 /*
  * Serving: a persistent request loop for many producers (the paper's offload pattern, in
  * which every CFD rank hands its cells to the GPU for the source term, Secs. 1 and 3.2).
- * A server owns one host worker thread, a fixed set of device slots (each a stream with
- * device buffers and page-locked host staging, sized from the HBM budget at creation) and
- * the CUDA graphs it has captured.  submit() only queues; the worker packs queued requests
- * that share (mechanism, kind, precision, dt, tolerances) into one batch for a free slot,
- * copies the batch to the device, replays the slot's graph for the batch's power-of-two
- * size bucket (capturing it on first use) and copies the results back, while other slots'
- * batches run: requests that arrive while the GPU is busy join the next free slot.  Slot 0
- * takes source-term batches only; integration batches hold at most 65536 cells.  Cells
- * are independent, so a request's result does not depend on the batch it ran in.
+ * A server owns one host worker thread, four streams ("lanes"), one device block of the
+ * HBM budget with a page-locked host mirror of the same size, and the CUDA graphs it has
+ * captured.  submit() only queues; when a lane is free the worker packs the oldest queued
+ * request that lane may run, with later queued requests that share (mechanism, kind,
+ * precision, dt, tolerances), into one batch, takes the batch's bytes from the budget
+ * (first fit), copies the batch to the device, replays the lane's graph for that key
+ * (updated in place with the batch's pointers and cell count) and copies the results back,
+ * while other lanes' batches run: requests that arrive while the GPU is busy are admitted
+ * as soon as a lane and enough of the budget are free; a request that does not fit yet
+ * waits for a batch to retire.  The SMs are split in two partitions (green contexts where
+ * the driver provides them, else by the persistent kernels' grid sizes): 16 SMs for lanes
+ * 0 and 1, which take source-term batches only, and the rest for lanes 2 and 3, which take
+ * integrations (and source-term batches while no integration is queued or running), so
+ * that source-term requests do not wait behind long integrations.  A source-term batch
+ * holds at most 2^20 cells and an integration batch at most 65536 (a larger single request
+ * runs alone).  Cells are independent, so a request's result does not depend on the batch
+ * it ran in.
  * The mechanisms must outlive the server.  All calls are thread-safe.
  */
 enum { CHEM_REQ_SOURCE = 0, CHEM_REQ_INTEGRATE = 1 };
@@ -376,23 +384,33 @@ typedef struct {
     int64_t n_cells;
     int64_t batch_cells;        /* cells of that batch */
     int32_t n_failed;           /* INTEGRATE: cells with a nonzero status */
-    int32_t slot;
+    int32_t slot;               /* lane the batch ran on */
     double queue_us;            /* submit -> batch launch */
     double latency_us;          /* submit -> results in the caller's host arrays */
+    int64_t steps_accepted;     /* INTEGRATE: accepted steps summed over the request's cells */
+    int64_t steps_rejected;     /* INTEGRATE: rejected steps summed over its cells */
 } chem_result;
 
 typedef struct {
-    int32_t n_slots;
-    int64_t slot_cells;         /* capacity of one slot (largest request) */
-    size_t device_bytes;        /* device memory the server holds */
+    int32_t n_slots;            /* lanes (streams) */
+    int64_t slot_cells;         /* most cells of one source-term batch */
+    size_t device_bytes;        /* device memory the server holds (the budget) */
     uint64_t submitted, completed, batches, graphs_captured, graph_launches;
     int32_t max_batch_requests; /* most requests seen in one batch */
+    uint64_t graph_updates;     /* launches whose cached graph was updated in place */
+    uint64_t memory_waits;      /* requests that waited for part of the budget to free up */
+    size_t bytes_in_use;        /* budget held by batches in flight now */
+    size_t bytes_in_use_max;    /* and the most held at once */
+    int32_t source_sms;         /* SMs of the source-term partition (lanes 0, 1) */
+    int32_t integrate_sms;      /* SMs of the integration partition (lanes 2, 3) */
+    int32_t green_contexts;     /* 1: partitions are green contexts; 0: kernel grids only */
 } chem_serve_info;
 
 /*
- * Create a server for n_mechs loaded mechanisms (same device) within hbm_budget bytes of
- * device memory, split into 4 slots.  Errors: CHEM_EINVAL, CHEM_ENOMEM (budget below one
- * slot of 64 cells of the largest mechanism, or an allocation failed), CHEM_ECUDA.
+ * Create a server for n_mechs loaded mechanisms (same device) holding hbm_budget bytes of
+ * device memory (one allocation, carved per batch) and as much page-locked host memory.
+ * Errors: CHEM_EINVAL, CHEM_ENOMEM (budget below one batch of 64 cells of the largest
+ * mechanism, or an allocation failed), CHEM_ECUDA.
  */
 chem_status chem_serve_create(const chem_mech *const *mechs, int32_t n_mechs, size_t hbm_budget,
                               void **server);
@@ -400,7 +418,7 @@ chem_status chem_serve_create(const chem_mech *const *mechs, int32_t n_mechs, si
 /*
  * Queue a request without blocking; *ticket identifies it.  The host arrays must stay valid
  * until chem_serve_poll reports the request complete.  Errors, synchronous: CHEM_EINVAL
- * (malformed request), CHEM_ENOMEM (n_cells above the slot capacity: over budget),
+ * (malformed request), CHEM_ENOMEM (the request alone needs more than the whole budget),
  * CHEM_EUNSUPPORTED (a path this mechanism does not support), CHEM_EBUSY (server stopping).
  */
 chem_status chem_serve_submit(void *server, const chem_request *req, uint64_t *ticket);

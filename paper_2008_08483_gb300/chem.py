@@ -71,14 +71,18 @@ class _Request(C.Structure):
 class _Result(C.Structure):
     _fields_ = [("status", C.c_int), ("batch_requests", C.c_int32), ("n_cells", C.c_int64),
                 ("batch_cells", C.c_int64), ("n_failed", C.c_int32), ("slot", C.c_int32),
-                ("queue_us", C.c_double), ("latency_us", C.c_double)]
+                ("queue_us", C.c_double), ("latency_us", C.c_double),
+                ("steps_accepted", C.c_int64), ("steps_rejected", C.c_int64)]
 
 
 class _ServeInfo(C.Structure):
     _fields_ = [("n_slots", C.c_int32), ("slot_cells", C.c_int64), ("device_bytes", C.c_size_t),
                 ("submitted", C.c_uint64), ("completed", C.c_uint64), ("batches", C.c_uint64),
                 ("graphs_captured", C.c_uint64), ("graph_launches", C.c_uint64),
-                ("max_batch_requests", C.c_int32)]
+                ("max_batch_requests", C.c_int32), ("graph_updates", C.c_uint64),
+                ("memory_waits", C.c_uint64), ("bytes_in_use", C.c_size_t),
+                ("bytes_in_use_max", C.c_size_t), ("source_sms", C.c_int32),
+                ("integrate_sms", C.c_int32), ("green_contexts", C.c_int32)]
 
 
 def lib():

@@ -198,6 +198,10 @@ chem_status launch_opted(SmemOptIn &opt, const void *func, int bytes, const char
 void fold_kc(const chem_mech_desc *d, int j, int r, double out[7]);
 void clear_error();
 extern std::atomic<uint64_t> g_launches;
+// Most SMs a persistent kernel's grid covers when launched from the calling thread (0: all
+// of the device).  The serving worker sets it while it records a batch for an SM partition.
+extern thread_local int tl_sm_limit;
+inline int sm_limit(int nsm) { return tl_sm_limit > 0 && tl_sm_limit < nsm ? tl_sm_limit : nsm; }
 
 // Reactor integration without allocation or synchronisation (kern_integrate.cu): the
 // workspace size for up to n_max cells, the argument checks of chem_integrate_cells, and the

@@ -22,6 +22,7 @@
 namespace chem {
 
 std::atomic<uint64_t> g_launches{0};
+thread_local int tl_sm_limit = 0;
 
 static thread_local std::string t_err;
 

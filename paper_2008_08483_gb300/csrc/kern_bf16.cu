@@ -950,7 +950,7 @@ template <int NSP>
 static chem_status launch_nsp(const Bf16Params &prm, size_t smem, cudaStream_t s, int dev)
 {
     static SmemOptIn opt;
-    const int grid = std::min(prm.ntiles, sm_count(dev));
+    const int grid = std::min(prm.ntiles, sm_limit(sm_count(dev)));
     chem_status st = launch_opted(opt, (const void *)k_source_bf16<NSP>, 227 * 1024, "split-BF16",
                                   [&] { k_source_bf16<NSP><<<grid, kThreads, smem, s>>>(prm); });
     if (st == CHEM_OK) g_launches.fetch_add(1);

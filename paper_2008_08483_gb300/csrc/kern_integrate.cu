@@ -845,7 +845,7 @@ static int64_t integrate_blocks(const LaunchShape &sh, int64_t n_max)
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_reactor<kModeIntegrate>, sh.wpb * 32, sh.smem);
     if (per_sm < 1) per_sm = 1;
-    int64_t blocks = (int64_t)nsm * per_sm;
+    int64_t blocks = (int64_t)sm_limit(nsm) * per_sm;
     const int64_t need = (n_max + sh.wpb - 1) / sh.wpb;
     return blocks > need ? need : blocks;
 }

@@ -772,7 +772,7 @@ chem_status launch_source_wide(const chem_mech *m, const void *tables, int64_t n
     prm.lg2R = (float)log2(kR);
     prm.status = t->status;
     static SmemOptIn opt;
-    const int grid = std::min(prm.ntiles, sm_count(m->device));
+    const int grid = std::min(prm.ntiles, sm_limit(sm_count(m->device)));
     chem_status st = launch_opted(opt, (const void *)k_source_wide, 227 * 1024, "split-BF16 (wide)",
                                   [&] { k_source_wide<<<grid, kThreads, smem, s>>>(prm); });
     if (st == CHEM_OK) g_launches.fetch_add(1);

@@ -1,7 +1,8 @@
 """Serving loop through the C ABI: results identical alone and in a concurrent mix (cells are
 independent), identical to the direct entry points, FP64 source term within 1e-10 of the
-oracle, admission by the slot capacity the HBM budget sets, poll time-outs, continuous
-batching with graph replay, and shutdown with abandoned tickets."""
+oracle, admission by the HBM budget (refusal only above the whole budget, waiting for memory
+otherwise), integration step counts, poll time-outs, continuous batching with graph replay and
+in-place graph updates, and shutdown with abandoned tickets."""
 import threading
 
 import numpy as np
@@ -130,12 +131,21 @@ def test_served_fp64_source_matches_oracle(env):
 
 def test_admission_and_errors(env):
     srv, m = env["srv"], env["mechs"][0]
-    cap = srv.info()["slot_cells"]
-    T, P, Y = synth.make_znd_states(m, cap + 1, seed=1)
+    # a request needing more than the whole budget is refused at once: 16 MiB hold
+    # 104857 cells of the 9-species FP64 source term ((2 + 2 * 9) * 8 bytes per cell)
+    small = chem.Server([env["handles"][0]], 16 << 20)
+    try:
+        n = (16 << 20) // 160 + 1
+        T, P = np.full(n, 1000.0), np.full(n, 1e6)
+        Y = np.zeros((n, m.n_species))
+        out = np.zeros_like(Y)
+        with pytest.raises(chem.ChemError) as e:
+            small.submit(0, chem.REQ_SOURCE, T, P, Y, chem.FP64, out=out)
+        assert e.value.status == 2                     # over budget: CHEM_ENOMEM
+    finally:
+        small.close()
+    T, P, Y = synth.make_znd_states(m, 8, seed=1)
     out = np.zeros_like(Y)
-    with pytest.raises(chem.ChemError) as e:
-        srv.submit(0, chem.REQ_SOURCE, T, P, Y, chem.FP64, out=out)
-    assert e.value.status == 2                         # over budget: CHEM_ENOMEM
     with pytest.raises(chem.ChemError) as e:
         srv.submit(5, chem.REQ_SOURCE, T[:8], P[:8], Y[:8], chem.FP64, out=out[:8])
     assert e.value.status == 1
@@ -184,6 +194,72 @@ def test_continuous_batching_and_graph_replay(env):
     assert after["batches"] - before["batches"] < len(reqs)
     assert after["graph_launches"] - before["graph_launches"] == after["batches"] - before["batches"]
     assert after["graphs_captured"] >= 1
+    assert after["graph_updates"] > before["graph_updates"]   # same key: graph updated in place
+
+
+def test_admission_waits_for_memory(env):
+    """Two requests that do not fit in the budget together: the second waits until the first
+    retires (no refusal, no split into fixed slots), and both results equal the direct call."""
+    h53, m = env["handles"][1], env["mechs"][1]
+    n = 20000                                          # 20000 * (2 + 2 * 53) * 8 B = 17.3 MB
+    srv = chem.Server([h53], 24 << 20)
+    try:
+        states = [synth.make_znd_states(m, n, seed=40 + q) for q in range(2)]
+        outs = [np.zeros_like(Y) for _, _, Y in states]
+        # submitted back to back, so the second arrives while the first holds its memory
+        tick = [srv.submit(0, chem.REQ_SOURCE, T, P, Y, chem.FP64, out=o)
+                for (T, P, Y), o in zip(states, outs)]
+        reqs = [(T, P, Y, o, t) for (T, P, Y), o, t in zip(states, outs, tick)]
+        res = [srv.poll(t, -1) for *_, t in reqs]
+        info = srv.info()
+        assert all(r["status"] == 0 and r["batch_requests"] == 1 for r in res)
+        assert info["memory_waits"] >= 1
+        assert info["bytes_in_use"] == 0 and 0 < info["bytes_in_use_max"] <= 24 << 20
+        dev = torch.device("cuda:0")
+        for T, P, Y, out, _ in reqs:
+            w = chem.source_term(h53, *(torch.as_tensor(a, device=dev) for a in (T, P, Y)), chem.FP64)
+            assert np.array_equal(w.cpu().numpy(), out)
+    finally:
+        srv.close()
+
+
+def test_source_term_not_held_behind_integration(env):
+    """A source-term request submitted while a long integration runs completes first: the
+    source-term lanes have SMs of their own."""
+    srv, m = env["srv"], env["mechs"][1]
+    info = srv.info()
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    assert info["source_sms"] >= 8 and info["integrate_sms"] >= 8
+    assert info["source_sms"] + info["integrate_sms"] <= nsm
+    T, P, Y, _ = synth.make_ignition_states(m, 4096, seed=9)
+    st = np.zeros(4096, np.int32)
+    ti = srv.submit(1, chem.REQ_INTEGRATE, T, P, Y, chem.FP64, dt=5e-6, status=st)
+    Ts, Ps, Ys = synth.make_znd_states(m, 1000, seed=8)
+    Ts, Ps, Ys = Ts.astype(np.float32), Ps.astype(np.float32), np.ascontiguousarray(Ys.astype(np.float32))
+    out = np.zeros_like(Ys)
+    ts = srv.submit(1, chem.REQ_SOURCE, Ts, Ps, Ys, chem.SPLIT_BF16, out=out)
+    rs = srv.poll(ts, -1)
+    with pytest.raises(chem.ChemError) as e:
+        srv.poll(ti, 0)
+    assert e.value.status == 7                         # the integration is still running
+    ri = srv.poll(ti, -1)
+    assert rs["status"] == 0 and ri["status"] == 0
+    assert rs["latency_us"] < ri["latency_us"]
+    dev = torch.device("cuda:0")
+    h53 = env["handles"][1]
+    w = chem.source_term(h53, *(torch.as_tensor(a, device=dev) for a in (Ts, Ps, Ys)), chem.SPLIT_BF16)
+    assert np.array_equal(w.cpu().numpy(), out)
+
+
+def test_integration_step_counts(env):
+    srv, m = env["srv"], env["mechs"][1]
+    T, P, Y = synth.make_znd_states(m, 300, seed=23)
+    st = np.full(300, -1, np.int32)
+    t = srv.submit(1, chem.REQ_INTEGRATE, T, P, Y, chem.FP64, dt=1e-8, rtol=1e-6, atol=1e-12,
+                   status=st)
+    res = srv.poll(t, -1)
+    assert res["status"] == 0 and np.all(st == 0)
+    assert res["steps_accepted"] >= 300 and res["steps_rejected"] >= 0
 
 
 def test_shutdown_with_abandoned_tickets(env):
