@@ -53,7 +53,7 @@ class _IntegOpts(C.Structure):
     _fields_ = [("h_init", C.c_double), ("h_min", C.c_double), ("h_max", C.c_double),
                 ("max_steps", C.c_int64), ("ign_dT", C.c_double), ("t_ign", C.c_void_p),
                 ("n_accepted", C.c_void_p), ("n_rejected", C.c_void_p),
-                ("fixed_steps", C.c_int32)]
+                ("fixed_steps", C.c_int32), ("jacobian_fp32", C.c_int32)]
 
 
 CELL_OK, CELL_STEP_UNDERFLOW, CELL_MAX_STEPS, CELL_NONFINITE = 0, 1, 2, 3
@@ -396,8 +396,9 @@ def ode_jacobian(mech: Mechanism, T, P, Y, stream=None):
 def integrate(mech: Mechanism, T, P, Y, t_end: float, rtol: float = 1e-6, atol: float = 1e-12,
               h_init: float = 0.0, h_min: float = 0.0, h_max: float = 0.0, max_steps: int = 0,
               ign_dT: float = 0.0, stats: bool = True, raise_on_failure: bool = False,
-              fixed_steps: int = 0, stream=None):
+              fixed_steps: int = 0, jacobian_fp32: bool = False, stream=None):
     """Integrate the reactors in place (T and Y are overwritten with the state at t_end).
+    jacobian_fp32 evaluates the stage Jacobian in FP32 (everything else stays FP64).
     Returns a dict with per-cell 'status', 't_ign', 'n_accepted', 'n_rejected' (CUDA tensors)
     and 'failed' (bool).  CHEM_ENONCONV raises only when raise_on_failure is set."""
     import torch
@@ -407,7 +408,7 @@ def integrate(mech: Mechanism, T, P, Y, t_end: float, rtol: float = 1e-6, atol: 
     status = torch.empty((n,), dtype=torch.int32, device=dev)
     out = {"status": status}
     opts = _IntegOpts(float(h_init), float(h_min), float(h_max), int(max_steps), float(ign_dT),
-                      None, None, None, int(fixed_steps))
+                      None, None, None, int(fixed_steps), int(bool(jacobian_fp32)))
     if stats:
         out["t_ign"] = torch.empty((n,), dtype=torch.float64, device=dev)
         out["n_accepted"] = torch.empty((n,), dtype=torch.int32, device=dev)

@@ -30,7 +30,10 @@
 //   (I / (h gamma) - J) U_i = f(y + sum_j a_ij U_j) + sum_j (c_ij / h) U_j
 //   y_new = y + sum_i m_i U_i,   err = sum_i e_i U_i
 // with (a, c, m, e) computed on the host from the classical table (alpha, gamma, b, bhat).
-// The LU (partial pivoting) and the error control are FP64.  Step size: RMS error norm
+// The right-hand side, the LU (partial pivoting), the solves and the error control are
+// FP64; the stage Jacobian J is FP64 too unless the caller asks for it in FP32
+// (reactor_jac_f32): J enters only the stage matrix, so an FP32 J changes the step's
+// arithmetic but not what the error control checks.  Step size: RMS error norm
 // with weights atol + rtol max(|y|, |y_new|), factor 0.9 err^(-1/3) clamped to [0.2, 5],
 // no growth right after a rejection; or, on request, a fixed number of equal steps without
 // error control (the L-stable step of an operator-split CFD solver).
@@ -164,6 +167,7 @@ struct IntegParams {
     double t_end, rtol, atol, h0, hmin, hmax, ign_dT;
     int64_t max_steps;
     int fixed_steps;          // > 0: this many equal steps, no error control
+    int jac32;                // integrate: stage Jacobian in FP32 (else FP64)
     int32_t *status, *nacc, *nrej;
     double *t_ign;
     const int64_t *n_dev;     // integrate: cell count read on the device (NULL: use n)
@@ -418,6 +422,248 @@ __device__ void jac_finish(const MechViewF64 &mv, const IntView &iv, const WarpL
     __syncwarp();
 }
 
+// ---------------------------------------------------------------------------------------
+// The stage Jacobian in FP32 (on request).  The integrator's right-hand side, LU, solves and
+// error control stay FP64; the Jacobian only enters the stage matrix (I / (h gamma) - J), and
+// here it is evaluated in FP32 with the structure of reactor_eval<true> and jac_finish: float scratch
+// laid over the warp's double scratch arrays, and a float matrix over the first half of the
+// matrix storage, widened to double in place at the end.  The mass-action products and their
+// column derivatives are formed from ln C (once per species): d q_f / dC_m = nu'_m q_f / C_m
+// for C_m > 0, and for C_m <= 0 (only nu'_m = 1 contributes) k_f prod_{u != m} C_u^nu'_u; the
+// exponentials are clamped below the float overflow, so k_r, which can exceed the float
+// range where the reverse products are tiny, is never formed on its own.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ float warp_sumf(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float exp_clamped(float x) { return expf(fminf(x, 88.0f)); }
+
+// float views of the warp's double scratch (each double array holds twice as many floats)
+struct CtxF {
+    float *C, *lnC, *H, *Cp, *Dcp, *Wo, *JT, *VM, *WC, *AK, *D, *Q, *A;
+};
+
+__device__ __forceinline__ CtxF ctx_f32(const Ctx &c, const WarpLayout &L)
+{
+    CtxF f;
+    f.C = (float *)c.C;
+    f.lnC = f.C + L.nsp;
+    f.H = (float *)c.H;
+    f.Cp = (float *)c.Cp;
+    f.Dcp = (float *)c.Dcp;
+    f.Wo = (float *)c.Wo;
+    f.JT = (float *)c.JT;
+    f.VM = (float *)c.VM;
+    f.WC = (float *)c.WC;
+    f.AK = (float *)c.AK;
+    f.D = (float *)c.D;
+    f.Q = (float *)c.Q;
+    f.A = (float *)c.A;
+    return f;
+}
+
+// d q / dC_m of one side of reaction I at column cc: nu_m prod C^nu / C_m from the side's
+// log-product Ls (which includes nu_m ln C_m), or, when C_m <= 0 and nu_m = 1, the product
+// of the side's other factors
+__device__ __forceinline__ float side_deriv(const RxnInt *I, const float *lnC, int cc, bool fwd,
+                                            float lk, float Ls, bool zero_other)
+{
+    const int nu = fwd ? I->col_nuf[cc] : I->col_nur[cc];
+    if (!nu) return 0.0f;
+    const float l = lnC[I->col_sp[cc]];
+    if (l > -INFINITY) return zero_other ? 0.0f : (float)nu * exp_clamped(Ls - l);
+    if (nu != 1) return 0.0f;
+    float Lo = lk;
+    for (int u = 0; u < I->ncol; ++u) {
+        const int nuu = fwd ? I->col_nuf[u] : I->col_nur[u];
+        if (u == cc || !nuu) continue;
+        const float lu = lnC[I->col_sp[u]];
+        if (!(lu > -INFINITY)) return 0.0f;
+        Lo += (float)nuu * lu;
+    }
+    return exp_clamped(Lo);
+}
+
+// The (T, Y) Jacobian of the reactor at ys in FP32, into c.A (double, row-major, ldw).
+__device__ void reactor_jac_f32(const MechViewF64 &mv, const IntView &iv, const WarpLayout &L,
+                                const Ctx &c, double Pd, const double *ys, int lane)
+{
+    const int ns = mv.ns, ldw = L.ldw;
+    const CtxF f = ctx_f32(c, L);
+    const float kRf = (float)kR;
+    const float T = (float)ys[0], P = (float)Pd;
+    float s = 0.0f;
+    for (int k = lane; k < ns; k += 32) s += (float)ys[1 + k] * (float)mv.invW[k];
+    const float S = warp_sumf(s);
+    const float rho = P / (kRf * T * S);
+    const TFeat<float> tf = t_features<float>(T, mv.t_mid);
+    for (int k = lane; k < ns; k += 32) {
+        const float Ck = rho * (float)ys[1 + k] * (float)mv.invW[k];
+        f.C[k] = Ck;
+        f.lnC[k] = Ck > 0.0f ? logf(Ck) : -INFINITY;
+        const double *a = iv.nasa + (size_t)k * 14 + tf.rg * 7;
+        const float a0 = (float)a[0], a1 = (float)a[1], a2 = (float)a[2], a3 = (float)a[3],
+                    a4 = (float)a[4], a5 = (float)a[5];
+        f.Cp[k] = a0 + T * (a1 + T * (a2 + T * (a3 + T * a4)));
+        f.H[k] = a0 + T * (a1 * 0.5f + T * (a2 * (1.0f / 3) + T * (a3 * 0.25f + T * a4 * 0.2f))) + a5 / T;
+        f.Dcp[k] = kRf * (a1 + T * (2.0f * a2 + T * (3.0f * a3 + T * 4.0f * a4)));
+        f.Wo[k] = 0.0f;
+        f.JT[k] = 0.0f;
+        f.VM[k] = 0.0f;
+    }
+    for (int k = 0; k < ns; ++k)
+        for (int m = lane; m < ns; m += 32) f.A[(1 + k) * ldw + 1 + m] = 0.0f;
+    __syncwarp();
+    const float ctot = P / (kRf * T);
+    for (int g = 0; g < iv.n_slots; g += 32) {
+        // phase A: one reaction per lane
+        const int j = iv.order[g + lane];
+        float qn = 0.0f, dqT = 0.0f, dqM = 0.0f;
+        if (j >= 0) {
+            const RxnF64 *X = mv.rxn + j;
+            const RxnInt *I = iv.rxn + j;
+            const int ncol = I->ncol;
+            float M = 1.0f;
+            if (X->kind != 0) {
+                M = ctot;
+                for (int t = X->tb_begin; t < X->tb_end; ++t) M += (float)mv.tb_e[t] * f.C[mv.tb_sp[t]];
+            }
+            const RxnTerms<float> rt = rxn_terms<float>(X, tf, M);
+            float *Dl = f.D + lane * kDStride;
+            if (!rt.dead) {
+                const float lkf = rt.lkinf + rt.lmod, lkr = lkf - rt.lKc;
+                float Lf = lkf, Lr = lkr;
+                bool zf = false, zr = false;
+                for (int cc = 0; cc < ncol; ++cc) {
+                    const float l = f.lnC[I->col_sp[cc]];
+                    const int ef = I->col_nuf[cc], er = I->col_nur[cc];
+                    if (ef) {
+                        if (l > -INFINITY) Lf += (float)ef * l;
+                        else zf = true;
+                    }
+                    if (er) {
+                        if (l > -INFINITY) Lr += (float)er * l;
+                        else zr = true;
+                    }
+                }
+                const bool rev = X->rev != 0;
+                const float pf = zf ? 0.0f : exp_clamped(Lf);
+                const float pr = (!rev || zr) ? 0.0f : exp_clamped(Lr);
+                qn = pf - pr;
+                const float dlkf = rt.dlkinf + rt.dmod_dT;
+                dqT = pf * dlkf - pr * (dlkf - rt.dlKc);
+                if (X->kind != 0) dqM = qn * rt.dmod_dlM / M;
+                for (int cc = 0; cc < ncol; ++cc) {
+                    const float df = side_deriv(I, f.lnC, cc, true, lkf, Lf, zf);
+                    const float dr = rev ? side_deriv(I, f.lnC, cc, false, lkr, Lr, zr) : 0.0f;
+                    Dl[cc] = df - dr;
+                }
+            } else {
+                for (int cc = 0; cc < ncol; ++cc) Dl[cc] = 0.0f;
+            }
+        }
+        f.Q[lane] = qn;
+        f.Q[32 + lane] = dqT;
+        f.Q[64 + lane] = dqM;
+        __syncwarp();
+        // phase B: each lane gathers the group's contributions to its own species rows
+        const int *gp = iv.gptr + (g >> 5) * (ns + 1);
+        for (int k = lane; k < ns; k += 32) {
+            const int e0 = gp[k], e1 = gp[k + 1];
+            float w = 0.0f, jt = 0.0f, vm = 0.0f;
+            float *Ak = f.A + (1 + k) * ldw + 1;
+            for (int e = e0; e < e1; ++e) {
+                const int r = iv.gent_slot[e];
+                const float nu = (float)iv.gent_nu[e];
+                w += nu * f.Q[r];
+                jt += nu * f.Q[32 + r];
+                vm += nu * f.Q[64 + r];
+                const int jr = iv.order[g + r];
+                const RxnInt *I = iv.rxn + jr;
+                const int ncol = I->ncol;
+                for (int cc = 0; cc < ncol; ++cc) Ak[I->col_sp[cc]] += nu * f.D[r * kDStride + cc];
+                const float dm = f.Q[64 + r];
+                if (dm != 0.0f) {
+                    const RxnF64 *X = mv.rxn + jr;
+                    const float sm = nu * dm;
+                    for (int t = X->tb_begin; t < X->tb_end; ++t) Ak[mv.tb_sp[t]] += sm * (float)mv.tb_e[t];
+                }
+            }
+            f.Wo[k] += w;
+            f.JT[k] += jt;
+            f.VM[k] += vm;
+        }
+        __syncwarp();
+    }
+    __syncwarp();
+    // heat release and heat capacity (as the right-hand side), then jac_finish's chain rule
+    float cp = 0.0f, q = 0.0f;
+    for (int k = lane; k < ns; k += 32) {
+        cp += (float)ys[1 + k] * f.Cp[k] * (float)mv.invW[k];
+        q += f.H[k] * f.Wo[k];
+    }
+    cp = warp_sumf(cp) * kRf;
+    const float Qh = warp_sumf(q) * kRf * T;
+    const float rc = rho * cp;
+    for (int k = 0; k < ns; ++k) {
+        const float v = f.VM[k];
+        for (int m = lane; m < ns; m += 32) f.A[(1 + k) * ldw + 1 + m] += v;
+    }
+    __syncwarp();
+    const float invS = 1.0f / S;
+    float hw = 0.0f, dqt = 0.0f, dcpt = 0.0f;
+    for (int k = lane; k < ns; k += 32) {
+        float w = 0.0f;
+        for (int m = 0; m < ns; ++m) w += f.A[(1 + k) * ldw + 1 + m] * f.C[m];
+        f.WC[k] = w;
+        const float dwT = f.JT[k] - w / T;
+        f.JT[k] = dwT;
+        f.AK[k] = (float)iv.W[k] * (f.Wo[k] - w) * invS / rho;
+        hw += f.H[k] * w;
+        dqt += f.Cp[k] * f.Wo[k] + T * f.H[k] * dwT;
+        dcpt += (float)ys[1 + k] * f.Dcp[k] * (float)mv.invW[k];
+    }
+    hw = warp_sumf(hw);
+    dqt = warp_sumf(dqt) * kRf;
+    dcpt = warp_sumf(dcpt);
+    __syncwarp();
+    for (int m = lane; m < ns; m += 32) {
+        const float iWm = (float)mv.invW[m];
+        float hs = 0.0f;
+        for (int k = 0; k < ns; ++k) {
+            float *e = f.A + (1 + k) * ldw + 1 + m;
+            const float jc = *e;
+            hs += f.H[k] * jc;
+            *e = (float)iv.W[k] * iWm * jc + f.AK[k] * iWm;
+        }
+        const float dQ = kRf * T * (rho * iWm * hs - invS * iWm * hw);
+        const float drc = -rc * invS * iWm + rho * kRf * f.Cp[m] * iWm;
+        f.A[1 + m] = -dQ / rc + Qh * drc / (rc * rc);
+    }
+    for (int k = lane; k < ns; k += 32)
+        f.A[(1 + k) * ldw] = (float)iv.W[k] * f.JT[k] / rho + (float)iv.W[k] * f.Wo[k] / (rho * T);
+    if (lane == 0) {
+        const float drcT = -rc / T + rho * dcpt;
+        f.A[0] = -dqt / rc + Qh * drcT / (rc * rc);
+    }
+    __syncwarp();
+    // widen in place, from the end: double i covers floats 2i and 2i + 1, which (for i >= 1)
+    // lie above float i, so every float is read (by the whole warp, before a write) ahead of
+    // the write that covers it
+    const int tot = L.n * ldw;
+    for (int base = tot - 1; base >= 0; base -= 32) {
+        const int i = base - lane;
+        const float v = i >= 0 ? f.A[i] : 0.0f;
+        __syncwarp();
+        if (i >= 0) c.A[i] = (double)v;
+        __syncwarp();
+    }
+}
+
 // In-place LU with partial pivoting of the n x n matrix A (leading dimension ldw); unit
 // lower L below the diagonal, U on and above it, 1/U_kk in invd, row interchanges in piv
 // and their combined permutation in pv ((P b)_i = b_{pv_i}).  False if a pivot is zero or
@@ -597,8 +843,13 @@ __global__ void __launch_bounds__(256) k_reactor(MechViewF64 mv, IntView iv, Int
                 status = CHEM_CELL_STEP_UNDERFLOW;
                 break;
             }
-            // Jacobian and f(y) (the first stage's right-hand side)
-            reactor_eval<true>(mv, iv, L, c, Pi, c.y, c.r, lane);
+            // f(y) (the first stage's right-hand side, FP64) and the stage Jacobian
+            if (p.jac32) {
+                reactor_eval<false>(mv, iv, L, c, Pi, c.y, c.r, lane);
+                reactor_jac_f32(mv, iv, L, c, Pi, c.y, lane);
+            } else {
+                reactor_eval<true>(mv, iv, L, c, Pi, c.y, c.r, lane);
+            }
             if (first && p.h0 <= 0.0 && !fixed) {
                 // starting step: 0.01 |y| / |f| in the weighted RMS norm (Hairer, Norsett &
                 // Wanner, Solving ODEs I, Sec. II.4), at most the interval
@@ -900,6 +1151,7 @@ chem_status integrate_launch(const chem_mech *m, int64_t n_max, const int64_t *n
     p.max_steps = (opts && opts->max_steps > 0) ? opts->max_steps : 100000;
     p.ign_dT = (opts && opts->ign_dT > 0.0) ? opts->ign_dT : 400.0;
     p.fixed_steps = (opts && opts->fixed_steps > 0) ? opts->fixed_steps : 0;
+    p.jac32 = (opts && opts->jacobian_fp32) ? 1 : 0;
     p.t_ign = opts ? opts->t_ign : nullptr;
     p.nacc = opts ? opts->n_accepted : nullptr;
     p.nrej = opts ? opts->n_rejected : nullptr;

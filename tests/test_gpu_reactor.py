@@ -102,6 +102,26 @@ def test_convergence_order_on_linear_problem(dev):
     assert np.all((orders > 2.8) & (orders < 3.2)), orders
 
 
+def test_fp32_stage_jacobian(dev, mech53, ignition53):
+    """The FP32 stage Jacobian (opt-in) against the FP64 one on 256 reactors of the
+    autoignition batch integrated to 1 ms at rtol 1e-6: both are error-controlled to the
+    same tolerance, so ignition delays agree within 0.1 %, end states within 5e-5 (each run
+    is within 1e-5 of Radau at rtol 1e-10 on the reference reactors), and step counts within
+    10 %."""
+    h = chem.Mechanism(mech53)
+    T, P, Y = (a[::16] for a in ignition53)
+    a = _integrate(h, T, P, Y, dev, 1e-3, rtol=1e-6, atol=1e-12, jacobian_fp32=True)
+    b = _integrate(h, T, P, Y, dev, 1e-3, rtol=1e-6, atol=1e-12)
+    assert np.all(a["status"] == 0) and np.all(b["status"] == 0)
+    ig = b["t_ign"] > 0
+    assert np.array_equal(a["t_ign"] > 0, ig)
+    assert np.max(np.abs(a["t_ign"][ig] / b["t_ign"][ig] - 1.0)) < 1e-3
+    assert np.max(np.abs(a["T"] / b["T"] - 1.0)) < 5e-5
+    assert np.max(np.abs(a["Y"] - b["Y"])) < 5e-5
+    assert abs(a["n_accepted"].sum() / b["n_accepted"].sum() - 1.0) < 0.1
+    h.close()
+
+
 def test_fixed_steps_mode(dev, mech53):
     # fixed_steps = K takes K equal steps without error control: the same arithmetic as an
     # adaptive run pinned to h = t_end / K with a tolerance every step passes
@@ -166,7 +186,8 @@ def test_ignition_delay_matches_radau(dev, mech53, ignition53):
         assert np.max(np.abs(r["Y"][q] - ref["y_end"][1:])) < 1e-5
 
 
-def test_ignition_delay_over_the_batch(dev, mech53, ignition53):
+@pytest.mark.parametrize("j32", [False, True], ids=["jacobian_fp64", "jacobian_fp32"])
+def test_ignition_delay_over_the_batch(dev, mech53, ignition53, j32):
     """A fixed sample of the 4096-reactor autoignition batch (T0 strata, the extremes of T0,
     P0 and phi, and reactors that do not ignite by 10 ms), integrated to 10 ms at rtol 1e-6:
     the ignition delay within 0.1 % of the oracle's Radau run (rtol 1e-10), a reactor that
@@ -182,7 +203,7 @@ def test_ignition_delay_over_the_batch(dev, mech53, ignition53):
     T, P, Y = (a[idx] for a in ignition53)
     assert len(idx) >= 32 and sum(t is None for t in ref["t_ign"]) >= 2
     h = chem.Mechanism(mech53)
-    r = _integrate(h, T, P, Y, dev, ref["t_end"], rtol=1e-6, atol=1e-12)
+    r = _integrate(h, T, P, Y, dev, ref["t_end"], rtol=1e-6, atol=1e-12, jacobian_fp32=j32)
     assert np.all(r["status"] == 0)
     for q, (t_ref, y_ref) in enumerate(zip(ref["t_ign"], ref["y_end"])):
         if t_ref is None:

@@ -1,6 +1,6 @@
 """jvp / vjp / dense Jacobian kernels of omega(T, ln C) against the oracle's analytic
 Jacobian (itself pinned to central differences), the adjoint identity, and the autograd
-path.  Bars: 1e-10 (FP64) and 1e-4 (FP32) per cell, relative to the cell's largest entry."""
+path.  Bars: 1e-10 (FP64) and 2e-5 (FP32) per cell, relative to the cell's largest entry."""
 import numpy as np
 import pytest
 import torch
@@ -10,7 +10,7 @@ from paper_2008_08483_gb300 import build as B
 from paper_2008_08483_gb300 import chem, synth
 
 pytestmark = pytest.mark.gpu
-TOL = {chem.FP64: 1e-10, chem.FP32: 1e-4}
+TOL = {chem.FP64: 1e-10, chem.FP32: 2e-5}
 
 
 @pytest.fixture(scope="module")
