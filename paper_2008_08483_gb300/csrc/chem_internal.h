@@ -98,6 +98,12 @@ struct MechViewF64 {
     const int32_t *col_ptr, *col_rxn;
     const float *col_nu;
     const int32_t *lane_ptr, *lane_sp;
+    // species-major reaction sides (nu', nu'' of each reaction on which species k appears)
+    // and listed third-body efficiencies (eff - 1), for the vjp gather
+    const int32_t *sd_ptr, *sd_rxn;
+    const float *sd_nuf, *sd_nur;
+    const int32_t *ts_ptr, *ts_rxn;
+    const double *ts_e;
 };
 
 // Approximate-ANN ln K_c (Sec. 2.3, Eqs. 12-14): standardised ln T -> N_L hidden layers of

@@ -346,6 +346,32 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
     }
     cptr[ns] = (int32_t)crxn.size();
     const size_t nce = crxn.size() ? crxn.size() : 1;
+    // species-major reaction sides (nu', nu'' of every reaction the species is on) and
+    // listed third-body efficiencies (eff - 1), for the warp-per-cell vjp gather
+    std::vector<int32_t> sdptr(ns + 1, 0), sdrxn, tsptr(ns + 1, 0), tsrxn;
+    std::vector<float> sdnuf, sdnur;
+    std::vector<double> tse;
+    for (int k = 0; k < ns; ++k) {
+        sdptr[k] = (int32_t)sdrxn.size();
+        for (int j = 0; j < nr; ++j) {
+            const int f = d->nu_f[(size_t)j * ns + k], r = d->nu_r[(size_t)j * ns + k];
+            if (f || r) {
+                sdrxn.push_back(j);
+                sdnuf.push_back((float)f);
+                sdnur.push_back((float)r);
+            }
+        }
+        tsptr[k] = (int32_t)tsrxn.size();
+        for (int j = 0; j < nr; ++j)
+            for (int t = r64[j].tb_begin; t < r64[j].tb_end; ++t)
+                if (tb_sp[t] == k) {
+                    tsrxn.push_back(j);
+                    tse.push_back(tb_e64[t]);
+                }
+    }
+    sdptr[ns] = (int32_t)sdrxn.size();
+    tsptr[ns] = (int32_t)tsrxn.size();
+    const size_t nsd = sdrxn.size() ? sdrxn.size() : 1, nts = tsrxn.size() ? tsrxn.size() : 1;
     // species -> lanes for the gather: longest lists first, each to the least loaded lane
     std::vector<int32_t> lptr(33, 0), lsp;
     {
@@ -397,7 +423,14 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
     size_t o_lsp = align(o_lptr + sizeof(int32_t) * lptr.size());
     size_t o_rt = align(o_lsp + sizeof(int32_t) * (lsp.size() ? lsp.size() : 1));
     size_t o_rt64 = align(o_rt + sizeof(uint32_t) * rt.size());
-    size_t total = align(o_rt64 + sizeof(uint32_t) * rt64.size());
+    size_t o_sdptr = align(o_rt64 + sizeof(uint32_t) * rt64.size());
+    size_t o_sdrxn = align(o_sdptr + sizeof(int32_t) * sdptr.size());
+    size_t o_sdnuf = align(o_sdrxn + sizeof(int32_t) * nsd);
+    size_t o_sdnur = align(o_sdnuf + sizeof(float) * nsd);
+    size_t o_tsptr = align(o_sdnur + sizeof(float) * nsd);
+    size_t o_tsrxn = align(o_tsptr + sizeof(int32_t) * tsptr.size());
+    size_t o_tse = align(o_tsrxn + sizeof(int32_t) * nts);
+    size_t total = align(o_tse + sizeof(double) * nts);
     std::vector<unsigned char> h(total, 0);
     memcpy(h.data() + o_r64, r64.data(), sizeof(RxnF64) * nr);
     memcpy(h.data() + o_s32, s32.data(), sizeof(SpecF32) * ns);
@@ -424,6 +457,17 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
     if (!crxn.empty()) {
         memcpy(h.data() + o_crxn, crxn.data(), sizeof(int32_t) * crxn.size());
         memcpy(h.data() + o_cnu, cnu.data(), sizeof(float) * cnu.size());
+    }
+    memcpy(h.data() + o_sdptr, sdptr.data(), sizeof(int32_t) * sdptr.size());
+    memcpy(h.data() + o_tsptr, tsptr.data(), sizeof(int32_t) * tsptr.size());
+    if (!sdrxn.empty()) {
+        memcpy(h.data() + o_sdrxn, sdrxn.data(), sizeof(int32_t) * sdrxn.size());
+        memcpy(h.data() + o_sdnuf, sdnuf.data(), sizeof(float) * sdnuf.size());
+        memcpy(h.data() + o_sdnur, sdnur.data(), sizeof(float) * sdnur.size());
+    }
+    if (!tsrxn.empty()) {
+        memcpy(h.data() + o_tsrxn, tsrxn.data(), sizeof(int32_t) * tsrxn.size());
+        memcpy(h.data() + o_tse, tse.data(), sizeof(double) * tse.size());
     }
 
     chem_mech *m = new (std::nothrow) chem_mech();
@@ -480,6 +524,13 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
     m->v64.col_nu = m->v32.col_nu;
     m->v64.lane_ptr = m->v32.lane_ptr;
     m->v64.lane_sp = m->v32.lane_sp;
+    m->v64.sd_ptr = (const int32_t *)(base + o_sdptr);
+    m->v64.sd_rxn = (const int32_t *)(base + o_sdrxn);
+    m->v64.sd_nuf = (const float *)(base + o_sdnuf);
+    m->v64.sd_nur = (const float *)(base + o_sdnur);
+    m->v64.ts_ptr = (const int32_t *)(base + o_tsptr);
+    m->v64.ts_rxn = (const int32_t *)(base + o_tsrxn);
+    m->v64.ts_e = (const double *)(base + o_tse);
     m->vint.rxn = (const RxnInt *)(base + o_rint);
     m->vint.nasa = (const double *)(base + o_nasa);
     m->vint.W = (const double *)(base + o_w);

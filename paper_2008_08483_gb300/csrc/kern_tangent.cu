@@ -1,5 +1,5 @@
-// kern_tangent.cu -- derivatives of omega with respect to (ln C, T): jvp, vjp and the dense
-// Jacobian, one thread per cell (SIMT, double or float).
+// kern_tangent.cu -- derivatives of omega with respect to (ln C, T): jvp and vjp one warp per
+// cell, the dense Jacobian one thread per cell (SIMT, double or float).
 //
 // With q_f = k_f prod C^nu' and q_r = k_f / K_c prod C^nu'' (Eqs. 3, 7), per reaction
 //   d ln q_f = sum_m nu'_m d ln C_m + d ln k_f
@@ -11,6 +11,8 @@
 //   d omega_k = sum_j nu_kj (q_f d ln q_f - q_r d ln q_r)                        (Eq. 2)
 // sum_m eff_m C_m x_m is evaluated as sum_m C_m x_m + sum_{listed m} (eff_m - 1) C_m x_m.
 #include <math.h>
+
+#include <algorithm>
 #include <string.h>
 
 #include "chem_internal.h"
@@ -171,6 +173,147 @@ __global__ void __launch_bounds__(BLK) k_tangent(MechViewF64 mv, TanArgs<R> a)
     }
 }
 
+
+// ---------------------------------------------------------------------------------------
+// Warp-per-cell jvp and vjp.  One warp per cell: the lanes take the species (C = exp ln C
+// and the tangent or cotangent rows, coalesced), then the reactions (one slot of the
+// kind-grouped order per lane: the rate terms, q_f, q_r and the reaction's tangent scalars,
+// written to per-reaction arrays in shared memory), then the species again, gathering from
+// the species-major lists in a fixed order (no atomics: results do not depend on the
+// launch).  The per-cell arithmetic is that of k_tangent above.
+// ---------------------------------------------------------------------------------------
+constexpr int kTanWarps = 8;           // warps per block, at most
+
+template <typename R>
+__device__ __forceinline__ R tw_sum(R v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(32 * kTanWarps) k_tangent_w(MechViewF64 mv, IntView iv, TanArgs<R> a)
+{
+    extern __shared__ unsigned char smem_tw[];
+    const int ns = mv.ns, nr = mv.nr, lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    if (i >= a.n) return;
+    R *sC = (R *)smem_tw + (size_t)wib * (3 * ns + 3 * nr);
+    R *sL = sC + ns;               // ln C_m
+    R *sA = sL + ns;               // jvp: d ln C_m; vjp: cotangent of omega_k
+    R *sP = sA + ns;               // jvp: q_net,j; vjp: u_j q_f,j
+    R *sQ = sP + nr;               // jvp: d q_net,j; vjp: u_j q_r,j
+    R *sV = sQ + nr;               // vjp: (u_j q_net,j) d ln mod / d ln M / M (third body)
+    const R Ti = a.T[i];
+    R ctot = 0, sdl = 0;
+    for (int m = lane; m < ns; m += 32) {
+        const R l = a.lnC[i * a.ldC + m];
+        const R c = rt_exp(l);
+        sL[m] = l;
+        sC[m] = c;
+        ctot += c;
+        if (MODE == kJvp) {
+            const R d = a.dlnC[i * a.ldC + m];
+            sA[m] = d;
+            sdl += c * d;
+        } else {
+            sA[m] = a.gw[i * a.ldO + m];
+        }
+    }
+    ctot = tw_sum(ctot);
+    if (MODE == kJvp) sdl = tw_sum(sdl);
+    const R dT = MODE == kJvp ? a.dT[i] : R(0);
+    const TFeat<R> tfe = t_features<R>(Ti, mv.t_mid);
+    __syncwarp();
+    R gT = 0, Wtb = 0;
+    for (int sl = lane; sl < iv.n_slots; sl += 32) {
+        const int j = iv.order[sl];
+        if (j < 0) continue;
+        const RxnF64 *X = mv.rxn + j;
+        const int kind = X->kind;
+        R M = 1;
+        if (kind != 0) {
+            M = ctot;
+            for (int t = X->tb_begin; t < X->tb_end; ++t) M += R(mv.tb_e[t]) * sC[mv.tb_sp[t]];
+        }
+        const RxnTerms<R> rt = rxn_terms<R>(X, tfe, M);
+        if (rt.dead) {
+            sP[j] = 0;
+            sQ[j] = 0;
+            if (MODE == kVjp) sV[j] = 0;
+            continue;
+        }
+        R sf = rt.lkinf + rt.lmod, sr = rt.lkinf + rt.lmod - rt.lKc;
+        for (int t = 0; t < X->nf; ++t) sf += R(X->nuf[t]) * sL[X->spf[t]];
+        for (int t = 0; t < X->nr; ++t) sr += R(X->nur[t]) * sL[X->spr[t]];
+        const R qf = rt_exp(sf);
+        const R qr = X->rev ? rt_exp(sr) : R(0);
+        const R dlkf_dT = rt.dlkinf + rt.dmod_dT;
+        if (MODE == kJvp) {
+            R dlM = 0;
+            if (kind != 0) {
+                R s = sdl;
+                for (int t = X->tb_begin; t < X->tb_end; ++t) {
+                    const int m = mv.tb_sp[t];
+                    s += R(mv.tb_e[t]) * sC[m] * sA[m];
+                }
+                dlM = s / M;
+            }
+            R tf = dlkf_dT * dT + rt.dmod_dlM * dlM, tr = (dlkf_dT - rt.dlKc) * dT + rt.dmod_dlM * dlM;
+            for (int t = 0; t < X->nf; ++t) tf += R(X->nuf[t]) * sA[X->spf[t]];
+            for (int t = 0; t < X->nr; ++t) tr += R(X->nur[t]) * sA[X->spr[t]];
+            sP[j] = qf - qr;
+            sQ[j] = qf * tf - qr * tr;
+        } else {
+            R aa = 0;                              // sum_k nu_kj g omega_k
+            for (int t = 0; t < X->nf; ++t) aa -= R(X->nuf[t]) * sA[X->spf[t]];
+            for (int t = 0; t < X->nr; ++t) aa += R(X->nur[t]) * sA[X->spr[t]];
+            const R uf = aa * qf, ur = aa * qr;
+            sP[j] = uf;
+            sQ[j] = ur;
+            gT += uf * dlkf_dT - ur * (dlkf_dT - rt.dlKc);
+            R w = 0;
+            if (kind != 0) {
+                w = (uf - ur) * rt.dmod_dlM / M;   // times eff_m C_m for every m
+                Wtb += w;
+            }
+            sV[j] = w;
+        }
+    }
+    if (MODE == kVjp) {
+        gT = tw_sum(gT);
+        Wtb = tw_sum(Wtb);
+    }
+    __syncwarp();
+    for (int e = mv.lane_ptr[lane]; e < mv.lane_ptr[lane + 1]; ++e) {
+        const int k = mv.lane_sp[e];
+        if (MODE == kJvp) {
+            // d omega_k = sum_j nu_kj d q_net,j and omega_k, in the species-major order
+            R d = 0, w = 0;
+            for (int q = mv.col_ptr[k]; q < mv.col_ptr[k + 1]; ++q) {
+                const int j = mv.col_rxn[q];
+                const R nu = R(mv.col_nu[q]);
+                d += nu * sQ[j];
+                w += nu * sP[j];
+            }
+            a.dom[i * a.ldO + k] = d;
+            if (a.om) a.om[i * a.ldO + k] = w;
+        } else {
+            // g ln C_m = sum_j (nu'_mj u q_f - nu''_mj u q_r) + C_m (sum_j w_j (1 + listed
+            // eff_mj - 1))
+            R g = 0, t = 0;
+            for (int q = mv.sd_ptr[k]; q < mv.sd_ptr[k + 1]; ++q) {
+                const int j = mv.sd_rxn[q];
+                g += R(mv.sd_nuf[q]) * sP[j] - R(mv.sd_nur[q]) * sQ[j];
+            }
+            for (int q = mv.ts_ptr[k]; q < mv.ts_ptr[k + 1]; ++q) t += R(mv.ts_e[q]) * sV[mv.ts_rxn[q]];
+            a.glnC[i * a.ldC + k] = g + (t + Wtb) * sC[k];
+        }
+    }
+    if (MODE == kVjp && lane == 0) a.gT[i] = gT;
+}
+
 template <typename R, int MODE>
 static chem_status launch_tan(const chem_mech *m, const TanArgs<R> &a, cudaStream_t s,
                               const char *name)
@@ -189,12 +332,39 @@ static chem_status launch_tan(const chem_mech *m, const TanArgs<R> &a, cudaStrea
     return set_error(CHEM_EUNSUPPORTED, "%s: %d species exceed the SIMT kernel", name, m->ns);
 }
 
+// Warp-per-cell launch; false in *used when the per-warp arrays do not fit in shared memory.
+template <typename R, int MODE>
+static chem_status launch_tan_w(const chem_mech *m, const TanArgs<R> &a, cudaStream_t s,
+                                const char *name, bool *used)
+{
+    static SmemOptIn done;
+    const size_t per = sizeof(R) * (3 * (size_t)m->ns + 3 * (size_t)m->nr);
+    const int wpb = (int)std::min<size_t>((size_t)kTanWarps, (size_t)(227 * 1024) / per);
+    *used = wpb >= 1;
+    if (!*used) return CHEM_OK;
+    const int64_t blocks = (a.n + wpb - 1) / wpb;
+    chem_status st = launch_opted(done, (const void *)k_tangent_w<R, MODE>, 227 * 1024, name, [&] {
+        k_tangent_w<R, MODE><<<(unsigned)blocks, 32 * wpb, per * wpb, s>>>(m->v64, m->vint, a);
+    });
+    if (st == CHEM_OK) g_launches.fetch_add(1);
+    return st;
+}
+
+// jvp and vjp take the warp-per-cell kernel (it needs the kind-grouped reaction order, built
+// when every reaction has at most kIntMax species, and its per-warp arrays in shared memory);
+// the dense Jacobian, and mechanisms beyond those limits, the thread-per-cell one.
 template <typename R>
 chem_status tangent_dispatch(const chem_mech *m, int mode, const TanArgs<R> &a, cudaStream_t s)
 {
+    bool used = false;
+    chem_status st = CHEM_OK;
     switch (mode) {
-    case kJvp: return launch_tan<R, kJvp>(m, a, s, "jvp");
-    case kVjp: return launch_tan<R, kVjp>(m, a, s, "vjp");
+    case kJvp:
+        if (m->vint.ok) st = launch_tan_w<R, kJvp>(m, a, s, "jvp", &used);
+        return used ? st : launch_tan<R, kJvp>(m, a, s, "jvp");
+    case kVjp:
+        if (m->vint.ok) st = launch_tan_w<R, kVjp>(m, a, s, "vjp", &used);
+        return used ? st : launch_tan<R, kVjp>(m, a, s, "vjp");
     default: return launch_tan<R, kJac>(m, a, s, "jacobian");
     }
 }

@@ -79,6 +79,35 @@ def test_vjp(setup, prec):
     assert cellrel(both, np.concatenate([eC, eT[:, None]], 1)) <= TOL[prec]
 
 
+@pytest.mark.parametrize("prec", [chem.FP64, chem.FP32])
+def test_jvp_vjp_large_mechanism(setup, prec):
+    """jvp and vjp at 160 species / 1000 reactions (90 third-body, 75 Troe) against the
+    oracle's analytic Jacobian, and a batch (2 * 64 + 5 cells) that ends in a partial block."""
+    dev = setup["dev"]
+    m = synth.make_mechanism("heavy_160_1000", seed=1)
+    h, om = chem.Mechanism(m), O.OracleMechanism(m)
+    n = 2 * 64 + 5
+    T, P, Y = synth.make_states(m, n, seed=41, T_range=(700.0, 2600.0))
+    C = np.stack([O.concentrations(om, T[i], P[i], Y[i]) for i in range(n)])
+    J = np.zeros((n, m.n_species, m.n_species + 1))
+    for i in range(n):
+        Jc, dTc = O.jacobian_tc(om, T[i], C[i])
+        J[i, :, :-1], J[i, :, -1] = Jc, dTc
+    rng = np.random.default_rng(8)
+    dT, dl, g = rng.normal(size=n) * 10.0, rng.normal(size=C.shape), rng.normal(size=C.shape)
+    Tt, lt = tens(T, prec, dev), tens(np.log(C), prec, dev)
+    _, dom = chem.source_term_jvp(h, Tt, lt, tens(dT, prec, dev), tens(dl, prec, dev), prec)
+    gT, gl = chem.source_term_vjp(h, Tt, lt, tens(g, prec, dev), prec)
+    torch.cuda.synchronize()
+    expect = np.einsum("ikm,im->ik", J[:, :, :-1], dl) + J[:, :, -1] * dT[:, None]
+    assert cellrel(dom.double().cpu().numpy(), expect) <= TOL[prec]
+    eT = np.einsum("ik,ik->i", J[:, :, -1], g)
+    eC = np.einsum("ikm,ik->im", J[:, :, :-1], g)
+    both = np.concatenate([gl.double().cpu().numpy(), gT.double().cpu().numpy()[:, None]], 1)
+    assert cellrel(both, np.concatenate([eC, eT[:, None]], 1)) <= TOL[prec]
+    h.close()
+
+
 def test_adjoint_identity(setup):
     """<g, J v> = <J^T g, v> between the two kernels, per cell."""
     s = setup
