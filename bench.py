@@ -662,13 +662,13 @@ def extras_kc_ann(line, dev, stream, n=100_000):
     line["kc_ann"] = res
 
 
-def extras_serving(line, n_ranks=64, seed=42, budget=8 << 30, src_per_rank=16, mix_per_rank=3):
+def extras_serving(line, n_ranks=64, seed=42, budget=8 << 30, src_per_rank=16, mix_per_rank=2):
     """Serving: 64 simulated detonation-channel ranks (host threads, one submitter and one
     poller each) offload requests of cells ~ logU[64, 65536] with a mechanism from {9/21,
     53/325}; a request is a contiguous segment of a ZND-like channel profile (T 300 -> 3000 K,
     P 1 -> 30 atm, unburnt -> products).  Two request pools:
       source : 16 source-term requests (split BF16) per rank (1024);
-      mixed  : 3 requests per rank (192), half source terms, half integrations over
+      mixed  : 2 requests per rank (128), half source terms, half integrations over
                dt = 1e-8 s (adaptive Rodas3, FP64, rtol 1e-6, atol 1e-10).
     Each pool runs once with every request at once (saturated cells/s), then with Poisson
     arrivals offering a fraction of that rate.  Latency is submit -> results in the caller's
