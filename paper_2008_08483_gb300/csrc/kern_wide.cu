@@ -16,7 +16,10 @@
 //   - the third-body sums M / c_tot = 1 + sum_k (eff_k - 1) z_k / sum z (Sec. 2.4) are
 //     formed in the epilogue from the listed species (at most kWMaxEff per reaction), with
 //     z_k = 2^(log2 z_k) rebuilt from A1's two terms;
-//   - T, P and Y are read and omega written directly by the epilogue threads.
+//   - T, P and Y are read by the epilogue threads (16-byte loads of three blocks at a time);
+//     at the end of a tile omega goes from tensor memory into A1's shared memory (free once
+//     every chunk has been evaluated), one odd-strided row per cell, and out to global memory
+//     a row per warp instruction, before the next tile's prologue rewrites A1.
 // Tensor memory: Gibbs features (16 columns), two S buffers (2 x 96), two q_net buffers
 // (2 x 48) and omega (NOUT = 16-padded species count <= 192).
 // Roles (480 threads): warp 0 copies the resident tables (share records, third-body lists,
@@ -78,7 +81,8 @@ struct WideParams {
 enum {
     WB_BTAB, WB_A1FULL, WB_D1FULL0, WB_D1FULL1, WB_D1EMPTY0, WB_D1EMPTY1, WB_A2FULL0, WB_A2FULL1,
     WB_A2EMPTY0, WB_A2EMPTY1, WB_B1FULL0, WB_B1FULL1, WB_B1FREE0, WB_B1FREE1, WB_B2FULL0,
-    WB_B2FULL1, WB_B2FREE0, WB_B2FREE1, WB_D2FULL, WB_D2EMPTY, WB_XREADY, WB_DRAIN, WB_COUNT
+    WB_B2FULL1, WB_B2FREE0, WB_B2FREE1, WB_D2FULL, WB_D2EMPTY, WB_XREADY, WB_DRAIN, WB_OSTAGED,
+    WB_OCOPIED, WB_COUNT
 };
 
 // bulk copy of `bytes` (a multiple of 16) in pieces of at most 16 KiB, completing on `bar`
@@ -112,7 +116,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_wide(const WideParams p)
     if (tid == 0) {
         constexpr uint32_t E = kEpiWarps;
         const uint32_t cnt[WB_COUNT] = {1, E, 1, 1, E, E, E, E, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1,
-                                        1, E, E, 2};
+                                        1, E, E, 2, E, E};
         for (int i = 0; i < WB_COUNT; ++i) tc::mbar_init(BAR(i), cnt[i]);
         tc::mbar_fence_init();
         ctl->abort = 0;
@@ -265,26 +269,53 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_wide(const WideParams p)
             cf.T = Tc;
             cf.lgct = log2f(Pc) - p.lg2R - cf.lg2T;
             float psum = 0.0f;
-            for (int blk = g; blk < NB; blk += NQ) {
-                float lx[8];
+            // rows that start on a 16-byte boundary are read 16 bytes at a time
+            const bool yvec = yrow && (((uintptr_t)yrow) & 15) == 0;
+            // the Y values of three of this thread's blocks at a time, so that their loads
+            // are in flight together
+            constexpr int kBMax = (kWMaxOut + 2 + kArrRows + 15) / 16 * 2 / NQ + 1;
+            for (int b0 = 0; b0 < kBMax; b0 += 3) {
+                float yv[3][8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int k = 8 * blk + e;
-                    const float z = yrow ? fmaxf(__ldg(yrow + min(k, ns - 1)), 0.0f) * iW[k] : 0.0f;
-                    psum += z;
-                    const float lz = fmaxf(tc::lg2(z), kLog2Floor);
-                    const int cc = ccode[k];
-                    lx[e] = cc == kColSpecies ? lz : cc == kColLgct ? cf.lgct
-                          : cc == kColOne ? 1.0f : cc == kColLg2T ? cf.lg2T
-                          : cc == kColItau ? cf.itau : 0.0f;
+                for (int bi = 0; bi < 3; ++bi) {
+                    const int blk = g + NQ * (b0 + bi);
+                    if (yvec && 8 * blk + 8 <= ns) {
+                        // a block inside the row: two 16-byte loads
+                        const float4 v0 = __ldg((const float4 *)(yrow + 8 * blk));
+                        const float4 v1 = __ldg((const float4 *)(yrow + 8 * blk + 4));
+                        yv[bi][0] = v0.x; yv[bi][1] = v0.y; yv[bi][2] = v0.z; yv[bi][3] = v0.w;
+                        yv[bi][4] = v1.x; yv[bi][5] = v1.y; yv[bi][6] = v1.z; yv[bi][7] = v1.w;
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            yv[bi][e] = (yrow && blk < NB) ? __ldg(yrow + min(8 * blk + e, ns - 1)) : 0.0f;
+                    }
                 }
-                uint4 wh, wl;
-                split2h(lx[0], lx[1], wh.x, wl.x);
-                split2h(lx[2], lx[3], wh.y, wl.y);
-                split2h(lx[4], lx[5], wh.z, wl.z);
-                split2h(lx[6], lx[7], wh.w, wl.w);
-                *(uint4 *)(a1h + rowoff + (uint32_t)blk * 128u) = wh;
-                *(uint4 *)(a1l + rowoff + (uint32_t)blk * 128u) = wl;
+#pragma unroll
+                for (int bi = 0; bi < 3; ++bi) {
+                    const int blk = g + NQ * (b0 + bi);
+                    if (blk < NB) {
+                        float lx[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int k = 8 * blk + e;
+                            const float z = fmaxf(yv[bi][e], 0.0f) * iW[k];
+                            psum += z;
+                            const float lz = fmaxf(tc::lg2(z), kLog2Floor);
+                            const int cc = ccode[k];
+                            lx[e] = cc == kColSpecies ? lz : cc == kColLgct ? cf.lgct
+                                  : cc == kColOne ? 1.0f : cc == kColLg2T ? cf.lg2T
+                                  : cc == kColItau ? cf.itau : 0.0f;
+                        }
+                        uint4 wh, wl;
+                        split2h(lx[0], lx[1], wh.x, wl.x);
+                        split2h(lx[2], lx[3], wh.y, wl.y);
+                        split2h(lx[4], lx[5], wh.z, wl.z);
+                        split2h(lx[6], lx[7], wh.w, wl.w);
+                        *(uint4 *)(a1h + rowoff + (uint32_t)blk * 128u) = wh;
+                        *(uint4 *)(a1l + rowoff + (uint32_t)blk * 128u) = wl;
+                    }
+                }
             }
             Psum[g * 128 + row] = psum;
             __syncwarp();
@@ -344,7 +375,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_wide(const WideParams p)
         uint32_t u = 0;
         if ((int)blockIdx.x < p.ntiles) ok = ok && prologue(blockIdx.x, 0, cf);
         for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x, ++it) {
-            const int64_t ci = (int64_t)t * 128 + row;
             const int t_next = t + gridDim.x;
             const bool has_next = t_next < p.ntiles;
             uint32_t sf[RH], sr[RH];
@@ -423,31 +453,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_source_wide(const WideParams p)
                 tc::fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(BAR(WB_A2FULL0 + ab));
-                if (c == nch - 1 && has_next) {
-                    // every warp has finished reading A1 (third-body z) for this tile before
-                    // the next tile's prologue rewrites it
+                if (c == nch - 1) {
+                    // every warp has finished reading A1 (third-body z) for this tile: omega
+                    // goes out through A1's shared memory (one padded row per cell, copied
+                    // to global memory a row per warp instruction), then the next tile's
+                    // prologue rewrites A1
                     if (!(ok = wait_bar(BAR(WB_A2FULL0 + ab), (u >> 1) & 1, ctl, p.status, 3))) break;
-                    if (!(ok = prologue(t_next, it + 1, cfn))) break;
+                    if (!(ok = wait_bar(BAR(WB_D2FULL), it & 1, ctl, p.status, 3))) break;
+                    tc::fence_after();
+                    float *Ws = (float *)a1h;
+                    const int ldw = ns | 1;           // odd: conflict-free columns and rows
+                    for (int blk = g; blk < p.nout / 8; blk += NQ) {
+                        uint32_t w[8];
+                        tc::tmem_ld8(tmem + lane_off + kWD2 + 8 * blk, w);
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            if (8 * blk + e < ns) Ws[row * ldw + 8 * blk + e] = __uint_as_float(w[e]);
+                    }
+                    tc::fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tc::mbar_arrive(BAR(WB_D2EMPTY));
+                        tc::mbar_arrive(BAR(WB_OSTAGED));
+                    }
+                    if (!(ok = wait_bar(BAR(WB_OSTAGED), it & 1, ctl, p.status, 3))) break;
+                    const int64_t i0 = (int64_t)t * 128;
+                    for (int r = warp - kEpiWarp0; r < 128; r += kEpiWarps) {
+                        if (i0 + r >= n) break;
+                        float *orow = p.om + (i0 + r) * p.ldO;
+                        for (int k = lane; k < ns; k += 32) orow[k] = Ws[r * ldw + k];
+                    }
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(BAR(WB_OCOPIED));
+                    if (!(ok = wait_bar(BAR(WB_OCOPIED), it & 1, ctl, p.status, 3))) break;
+                    if (has_next && !(ok = prologue(t_next, it + 1, cfn))) break;
                 }
                 if (c + 1 < nch) release_s(c + 1, u + 1);
             }
             if (!ok) break;
-            // ---- omega of the tile: tensor memory -> registers -> global memory
-            if (!(ok = wait_bar(BAR(WB_D2FULL), it & 1, ctl, p.status, 3))) break;
-            tc::fence_after();
-            for (int blk = g; blk < p.nout / 8; blk += NQ) {
-                uint32_t w[8];
-                tc::tmem_ld8(tmem + lane_off + kWD2 + 8 * blk, w);
-                if (ci < n) {
-                    float *orow = p.om + ci * p.ldO;
-#pragma unroll
-                    for (int e = 0; e < 8; ++e)
-                        if (8 * blk + e < ns) orow[8 * blk + e] = __uint_as_float(w[e]);
-                }
-            }
-            tc::fence_before();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(BAR(WB_D2EMPTY));
             cf = cfn;
         }
     }
