@@ -468,7 +468,18 @@ bool Server::admit(Lane &l)
     const BatchKey key = key_of((*head)->r);
     const chem_mech *m = mechs[key.mech];
     const int64_t limit = key.kind == CHEM_REQ_INTEGRATE ? kIntegBatch : kSourceBatch;
-    const size_t room = arena.largest_free();
+    // the oldest request already waiting for memory keeps its bytes reserved: other batches
+    // only use what the largest free block holds beyond them, so that a steady stream of
+    // small batches on other lanes cannot hold it off
+    size_t room = arena.largest_free();
+    for (const auto &q : queue) {
+        if (!q->mem_wait) continue;
+        if (q.get() != head->get()) {
+            const size_t need = layout_of(mechs[q->r.mech_index], key_of(q->r), q->r.n_cells).total;
+            room = room > need ? room - need : 0;
+        }
+        break;
+    }
     if (layout_of(m, key, (*head)->r.n_cells).total > room) {
         if (!(*head)->mem_wait) {
             (*head)->mem_wait = true;
