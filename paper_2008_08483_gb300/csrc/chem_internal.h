@@ -142,6 +142,53 @@ struct MechViewF32 {
     int32_t n_slots;
 };
 
+// Tables of the thread-per-cell FP32 kernel (kern_f32t.cu).  Exponents are kept as a head H
+// on the grid of multiples of 2^-8 (sums of heads are exact in FP32) and a small remainder L.
+// Temperature terms are centred on T0 = 1000 K: d1 = log2 T - log2 T0, d2 = 1/T - 1/T0.
+// A reaction record of the kernel (128 bytes).  Entries are (byte offset of the species' row
+// in the warp's shared tables, coefficient as float bits) pairs, in the order
+//   reactant 0, 1 | product 0, 1 | net 0, 1 | net 2, 3 | reactant 2, product 2 | net 4, 5
+// so that a reaction with at most two species per side reads six 16-byte words; unused
+// entries point at a zero row past the last species with coefficient 0.
+constexpr int kTSide = 3;                 // reactant and product slots per reaction
+constexpr int kTNet = 6;                  // net-change slots per reaction
+struct alignas(16) RxnT {
+    float4 kf;                   // log2 k_inf(T0) as (H, L); coefficient of d2 (-E/R log2 e)
+                                 // as double-float (hi, lo)
+    float b;                     // coefficient of d1 (temperature exponent)
+    uint32_t meta;               // group type | falloff index << 8
+    uint32_t tb;                 // listed third-body efficiencies: first | end << 16
+    float rb;                    // added to the reverse exponent: 0, or -2000 if irreversible
+    int32_t ent[24];
+};
+__host__ __device__ constexpr int rxnt_react(int s) { return s < 2 ? s : 8; }
+__host__ __device__ constexpr int rxnt_prod(int s) { return s < 2 ? 2 + s : 9; }
+__host__ __device__ constexpr int rxnt_net(int s) { return s < 4 ? 4 + s : 6 + s; }
+// Per falloff reaction: low-pressure limit as kf; (b0, 1 - alpha, alpha, -log2 e / T***);
+// (-log2 e / T*, -T** log2 e, 1 if the T** term is present else 0, 0)
+struct alignas(16) FallT {
+    float4 k0;
+    float4 t0;
+    float4 t1;
+};
+struct alignas(16) SpecT {
+    float4 ga[2];                // per T range: G(T0) as (H, L); coefficient of d1 (hi, lo)
+    float4 gb[2];                // coefficient of d2 (hi, lo); e1, e2 of the centred polynomial
+    float4 gc[2];                // e3, e4; 1 / W_k; 0
+};
+struct F32TView {
+    int ns, n_rec;               // species; records (groups padded to pairs)
+    int n_tb, n_fall;
+    const RxnT *rxn;
+    const SpecT *spec;
+    const int2 *tb;              // (row offset, efficiency - 1 as float bits)
+    const FallT *fall;
+    double t_mid;
+    // double-float (hi, lo) constants: log2 T0, 1/T0, log2 R, log2(p_ref / R), log2 e
+    float2 lg2T0, invT0, lg2R, lg2_pref_R, log2e;
+    bool ok;                     // the mechanism fits the kernel (else the warp-per-cell kernel)
+};
+
 }  // namespace chem
 
 // The opaque handle of the C ABI.
@@ -153,6 +200,8 @@ struct chem_mech {
     chem::MechViewF64 v64;
     chem::MechViewF32 v32;
     chem::IntView vint;
+    chem::F32TView vt;           // thread-per-cell FP32 tables (vt.ok false: not built)
+    void *d_f32t;
     bool have_bf16;
     bool bf16_wide;              // the tables are those of the large-mechanism kernel
     void *bf16;                  // split-BF16 tables (tensor-core path): kern_bf16.cu, or
@@ -232,5 +281,13 @@ chem_status launch_source_fp32_ann(const chem_mech *m, const KcAnnView &av, int6
                                    float *om, int64_t ldO, cudaStream_t s);
 chem_status launch_log_kc(const chem_mech *m, int64_t n, const double *T, double *lnkc,
                           int64_t ldK, cudaStream_t s);
+
+// Thread-per-cell FP32 source term (kern_f32t.cu): tables built at load (a mechanism the
+// kernel does not take leaves m->vt.ok false) and the launch, used by launch_source_fp32.
+chem_status f32t_build_tables(chem_mech *m, const chem_mech_desc *d);
+void f32t_free_tables(chem_mech *m);
+chem_status launch_source_fp32_t(const chem_mech *m, int64_t n, const float *T, const float *P,
+                                 const float *Y, int64_t ldY, float *om, int64_t ldO,
+                                 cudaStream_t s);
 
 }  // namespace chem

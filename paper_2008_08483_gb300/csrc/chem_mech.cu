@@ -479,6 +479,8 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
     m->have_bf16 = false;
     m->bf16_wide = false;
     m->bf16 = nullptr;
+    m->vt.ok = false;
+    m->d_f32t = nullptr;
     if (cudaGetDevice(&m->device) != cudaSuccess) {
         delete m;
         return set_error(CHEM_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(cudaGetLastError()));
@@ -547,6 +549,13 @@ extern "C" chem_status chem_mechanism_load(const chem_mech_desc *d, chem_mech **
         delete m;
         return st;
     }
+    st = f32t_build_tables(m, d);
+    if (st != CHEM_OK) {
+        bf16_free_tables(m);
+        cudaFree(m->d_blob);
+        delete m;
+        return st;
+    }
     clear_error();
     *out = m;
     return CHEM_OK;
@@ -561,6 +570,7 @@ extern "C" chem_status chem_mechanism_free(chem_mech *m)
     if (cur != m->device) cudaSetDevice(m->device);
     cudaDeviceSynchronize();
     bf16_free_tables(m);
+    f32t_free_tables(m);
     cudaError_t e = cudaFree(m->d_blob);
     if (cur >= 0 && cur != m->device) cudaSetDevice(cur);
     delete m;

@@ -1,0 +1,862 @@
+// kern_f32t.cu -- FP32 source term, one thread per cell (Eqs. 2-11, Sec. 2.4).
+//
+// A warp takes 32 cells, one per lane, and walks the mechanism's reactions with all lanes on
+// the same reaction: every table read is a broadcast and every branch on the reaction's kind
+// is warp-uniform.  Per cell and species, shared memory holds
+//   P_k = log2 C_k                                  (Eq. 3 in log2 units)
+//   F_k = -g_k/(R T) log2 e + log2(p_ref / (R T))   (the Gibbs layer, Eqs. 8-11)
+// so that for reaction j, with log2 K_c = sum_k nu_kj F_k,
+//   x_f = log2 k_f + fac + sum_k nu'_kj P_k
+//   x_r = log2 k_f + fac + sum_k nu''_kj (P_k - F_k) + sum_k nu'_kj F_k
+//   q_net = 2^x_f - 2^x_r,   omega_k += (nu''_kj - nu'_kj) q_net      (Eqs. 2-4, 7)
+// where fac is log2 of the third-body concentration or of the falloff factor (Sec. 2.4).
+//
+// Precision: every exponent is a pair (H, L), H a multiple of 2^-8 and L small.  Heads of
+// the per-species terms and of the products of a reaction's temperature coefficients with
+// the cell's centred temperature features are put on that grid, so the sums of heads with
+// small integer stoichiometric coefficients are exact in FP32; only L carries rounding, at
+// the magnitude of L.  The exponent is rounded once, at the magnitude of the result, before
+// the exp2.  Per-cell temperature features are computed in FP64 once per cell.
+//
+// Layout: one block of W warps per SM-sized share of the batch.  The block stages the species
+// table, the third-body lists and the falloff parameters once, and the reaction records in
+// double-buffered chunks of 16 (loaded one chunk ahead); each warp owns its P/F rows and its
+// omega tile.  Reactions are grouped by kind and shape (at most two or three species per
+// side) and taken four at a time with fixed-shape code, so that their exponent chains
+// overlap.
+#include <math.h>
+#include <stddef.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "chem_internal.h"
+
+namespace chem {
+
+namespace {
+
+constexpr int kTMaxSpecies = 64;
+constexpr double kT0 = 1000.0;               // centre of the temperature features (K)
+constexpr float kGridAdd = 49152.0f;         // 1.5 * 2^15: (x + it) - it rounds x to 2^-8
+constexpr double kGridLimit = 4096.0;        // |head| of a table value (exact sums to 2^15)
+constexpr float kAbsentLog2 = -1000.0f;      // log2 C of an absent species (2^x flushes to 0)
+constexpr float kOff = -2000.0f;             // exponent bias of padding and irreversible rates
+constexpr int kChunk = 16;                   // reaction records per staged chunk
+constexpr int kOmStride = 33;                // omega tile row (odd: conflict-free both ways)
+constexpr int kPfRow = 32 * 16;              // bytes of one species row of P/F (32 lanes)
+constexpr int kOmRow = kOmStride * 4;        // bytes of one omega tile row
+// group types, in processing order
+enum { kGSmall = 0, kGBig = 1, kGThird = 2, kGLind = 3, kGTroe = 4, kGroups = 5 };
+
+inline double grid_head(double x) { return rint(x * 256.0) / 256.0; }
+
+// (hi, lo) float pair of a double
+inline void dsplit2(double x, float &h, float &l)
+{
+    h = (float)x;
+    l = (float)(x - (double)h);
+}
+
+constexpr int kQuad = 4;                     // reactions taken together (groups padded to it)
+
+void put_entry(RxnT &r, int pair, int off, float nu)
+{
+    r.ent[2 * pair] = off;
+    memcpy(&r.ent[2 * pair + 1], &nu, 4);
+}
+// every entry at the zero row with coefficient 0
+void clear_entries(RxnT &r, int ns)
+{
+    for (int s = 0; s < kTSide; ++s) {
+        put_entry(r, rxnt_react(s), ns * kPfRow, 0.0f);
+        put_entry(r, rxnt_prod(s), ns * kPfRow, 0.0f);
+    }
+    for (int s = 0; s < kTNet; ++s) put_entry(r, rxnt_net(s), ns * kOmRow, 0.0f);
+}
+
+// log2 k(T) = log2 k(T0) + b d1 - (E/R) log2 e d2 (Eq. 6) as (H, L, coefficient of d2)
+bool centred(const double *a, float4 &out, float &b)
+{
+    const double at0 = (a[0] + a[1] * log(kT0) - a[2] / kT0) * kLog2e;
+    const double h = grid_head(at0);
+    if (!(fabs(h) < kGridLimit)) return false;
+    float th, tl;
+    dsplit2(-a[2] * kLog2e, th, tl);
+    out = make_float4((float)h, (float)(at0 - h), th, tl);
+    b = (float)a[1];
+    return true;
+}
+
+__host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
+// shared memory of one warp: P/F rows (+ the zero row of unused entries) and the omega tile
+// (at least 32 rows: it first stages the Y rows of the warp's cells)
+__host__ __device__ inline size_t warp_pf_bytes(int ns) { return (size_t)(ns + 1) * kPfRow; }
+__host__ __device__ inline size_t warp_om_bytes(int ns)
+{
+    return a16((size_t)(ns + 1 > 32 ? ns + 1 : 32) * kOmRow);
+}
+// shared memory of the block's staged tables: species, third-body lists, falloff, two chunks
+__host__ __device__ inline size_t block_fixed_bytes(const F32TView &v)
+{
+    return a16(sizeof(SpecT) * v.ns) + a16(sizeof(int2) * v.n_tb) + a16(sizeof(FallT) * v.n_fall) +
+           2 * kChunk * sizeof(RxnT);
+}
+constexpr size_t kTSmemMax = 227 * 1024;
+
+}  // namespace
+
+// Tables of the kernel from the descriptor; a mechanism outside the kernel's limits keeps
+// m->vt.ok false and the FP32 source term then runs the warp-per-cell kernel.
+chem_status f32t_build_tables(chem_mech *m, const chem_mech_desc *d)
+{
+    m->vt = F32TView{};
+    m->d_f32t = nullptr;
+    const int ns = d->n_species, nr = d->n_reactions;
+    if (ns > kTMaxSpecies) return CHEM_OK;
+    std::vector<RxnT> rx;
+    std::vector<int> type_of(nr);
+    std::vector<int2> tb;
+    std::vector<FallT> fall;
+    std::vector<RxnT> one(nr);
+    for (int j = 0; j < nr; ++j) {
+        RxnT &r = one[j];
+        memset(&r, 0, sizeof r);
+        if (!centred(d->arrh + (size_t)j * 3, r.kf, r.b)) return CHEM_OK;
+        const int kind = d->kind[j];
+        int nf = 0, nrr = 0, nnet = 0;
+        clear_entries(r, ns);
+        for (int k = 0; k < ns; ++k) {
+            const int f = d->nu_f[(size_t)j * ns + k], p = d->nu_r[(size_t)j * ns + k];
+            if (f) {
+                if (nf >= kTSide) return CHEM_OK;
+                put_entry(r, rxnt_react(nf++), k * kPfRow, (float)f);
+            }
+            if (p) {
+                if (nrr >= kTSide) return CHEM_OK;
+                put_entry(r, rxnt_prod(nrr++), k * kPfRow, (float)p);
+            }
+            if (p != f) {
+                if (nnet >= kTNet) return CHEM_OK;
+                put_entry(r, rxnt_net(nnet++), k * kOmRow, (float)(p - f));
+            }
+        }
+        r.rb = d->reversible[j] ? 0.0f : kOff;
+        const int type = kind == 0 ? (nf <= 2 && nrr <= 2 && nnet <= 4 ? kGSmall : kGBig)
+                                   : kind == 1 ? kGThird : kind == 2 ? kGLind : kGTroe;
+        type_of[j] = type;
+        uint32_t fidx = 0;
+        if (kind >= 2) {
+            FallT f;
+            memset(&f, 0, sizeof f);
+            float b0;
+            if (!centred(d->arrh_low + (size_t)j * 3, f.k0, b0)) return CHEM_OK;
+            f.t0.x = b0;
+            if (kind == 3) {
+                const double *t = d->troe + (size_t)j * 4;
+                // F_cent = (1 - alpha) 2^(T t0.w) + alpha 2^(T t1.x) + t1.z 2^(t1.y / T)
+                f.t0.y = (float)(1.0 - t[0]);
+                f.t0.z = (float)t[0];
+                f.t0.w = (float)(-kLog2e / t[1]);
+                f.t1.x = (float)(-kLog2e / t[2]);
+                f.t1.y = t[3] > 0.0 ? (float)(-t[3] * kLog2e) : 0.0f;
+                f.t1.z = t[3] > 0.0 ? 1.0f : 0.0f;
+            }
+            fidx = (uint32_t)fall.size();
+            fall.push_back(f);
+        }
+        r.meta = (uint32_t)type | (fidx << 8);
+        const size_t t0 = tb.size();
+        if (kind >= 1)
+            for (int k = 0; k < ns; ++k) {
+                const double e = d->eff ? d->eff[(size_t)j * ns + k] : 1.0;
+                if (e != 1.0) {
+                    const float ef = (float)(e - 1.0);
+                    int bits;
+                    memcpy(&bits, &ef, 4);
+                    tb.push_back(make_int2(k * kPfRow, bits));
+                }
+            }
+        if (tb.size() > 65535) return CHEM_OK;
+        r.tb = (uint32_t)t0 | ((uint32_t)tb.size() << 16);
+    }
+    // records grouped by type, in quads: greedily packed so that a quad's net species are
+    // pairwise distinct (meta bit 3: one omega round trip), the rest in order; the last quad
+    // of a type is padded with zero-rate records of its type
+    auto net_mask = [&](int j) {
+        std::vector<bool> mk(ns, false);
+        for (int k = 0; k < ns; ++k) mk[k] = d->nu_r[(size_t)j * ns + k] != d->nu_f[(size_t)j * ns + k];
+        return mk;
+    };
+    for (int g = 0; g < kGroups; ++g) {
+        std::vector<std::vector<int>> quads;
+        std::vector<std::vector<bool>> used;
+        for (int j = 0; j < nr; ++j) {
+            if (type_of[j] != g) continue;
+            const std::vector<bool> mk = net_mask(j);
+            size_t qi = 0;
+            for (; qi < quads.size(); ++qi) {
+                if (quads[qi].size() >= (size_t)kQuad) continue;
+                bool clash = false;
+                for (int k = 0; k < ns && !clash; ++k) clash = mk[k] && used[qi][k];
+                if (!clash) break;
+            }
+            if (qi == quads.size()) {
+                quads.emplace_back();
+                used.emplace_back(ns, false);
+            }
+            quads[qi].push_back(j);
+            for (int k = 0; k < ns; ++k) used[qi][k] = used[qi][k] || mk[k];
+        }
+        std::vector<int> order, rest;
+        std::vector<bool> disjoint;
+        for (auto &q : quads) {
+            if (q.size() == (size_t)kQuad) {
+                order.insert(order.end(), q.begin(), q.end());
+                disjoint.push_back(true);
+            } else {
+                rest.insert(rest.end(), q.begin(), q.end());
+            }
+        }
+        for (size_t a = 0; a < rest.size(); a += kQuad) {
+            bool dis = true;
+            std::vector<bool> u(ns, false);
+            for (size_t b = a; b < a + kQuad && b < rest.size(); ++b) {
+                const std::vector<bool> mk = net_mask(rest[b]);
+                for (int k = 0; k < ns; ++k) {
+                    dis = dis && !(mk[k] && u[k]);
+                    u[k] = u[k] || mk[k];
+                }
+            }
+            order.insert(order.end(), rest.begin() + a, rest.begin() + std::min(rest.size(), a + kQuad));
+            disjoint.push_back(dis);
+        }
+        for (size_t qn = 0; qn < disjoint.size(); ++qn) {
+            const size_t first = rx.size();
+            for (size_t b = qn * kQuad; b < (qn + 1) * kQuad; ++b) {
+                if (b < order.size()) {
+                    rx.push_back(one[order[b]]);
+                } else {
+                    RxnT pad = rx.back();
+                    pad.kf = make_float4(kOff, 0.0f, 0.0f, 0.0f);
+                    pad.b = 0.0f;
+                    pad.tb = (pad.tb & 0xFFFFu) * 0x10001u;     // no third-body entries
+                    clear_entries(pad, ns);
+                    rx.push_back(pad);
+                }
+            }
+            if (disjoint[qn]) rx[first].meta |= 8u;
+        }
+    }
+    while (rx.size() % kChunk) {
+        RxnT pad;
+        memset(&pad, 0, sizeof pad);
+        pad.kf = make_float4(kOff, 0.0f, 0.0f, 0.0f);
+        pad.meta = kGSmall;
+        clear_entries(pad, ns);
+        rx.push_back(pad);
+    }
+    // Gibbs layer per species and T range, centred on T0 (Eq. 10 with NASA-7 a0..a6):
+    //   G(T) = -g/(RT) log2 e = a0 log2 T + log2 e (a6 - a0 + a1 T/2 + a2 T^2/6 + a3 T^3/12
+    //          + a4 T^4/20 - a5 / T)
+    //        = G(T0) + a0 d1 - a5 log2 e d2 + sum_p e_p u^p,  u = T/1000 - 1
+    std::vector<SpecT> sp(ns);
+    const double lg2T0 = log2(kT0);
+    for (int k = 0; k < ns; ++k) {
+        SpecT &s = sp[k];
+        memset(&s, 0, sizeof s);
+        for (int rg = 0; rg < 2; ++rg) {
+            const double *a = d->nasa7 + (size_t)k * 14 + (size_t)rg * 7;
+            const double c[5] = {0.0, a[1] / 2.0 * 1e3, a[2] / 6.0 * 1e6, a[3] / 12.0 * 1e9,
+                                 a[4] / 20.0 * 1e12};        // on tau^m, tau = T / 1000
+            const double g0 = a[0] * lg2T0 +
+                              kLog2e * (a[6] - a[0] + c[1] + c[2] + c[3] + c[4] - a[5] / kT0);
+            const double h = grid_head(g0);
+            if (!(fabs(h) < kGridLimit)) return CHEM_OK;
+            // tau^m - 1 in powers of u = tau - 1 (binomial expansion about tau = 1)
+            const double e1 = c[1] + 2 * c[2] + 3 * c[3] + 4 * c[4];
+            const double e2 = c[2] + 3 * c[3] + 6 * c[4];
+            const double e3 = c[3] + 4 * c[4];
+            const double e4 = c[4];
+            float a0h, a0l, a5h, a5l;
+            dsplit2(a[0], a0h, a0l);
+            dsplit2(-a[5] * kLog2e, a5h, a5l);
+            s.ga[rg] = make_float4((float)h, (float)(g0 - h), a0h, a0l);
+            s.gb[rg] = make_float4(a5h, a5l, (float)(e1 * kLog2e), (float)(e2 * kLog2e));
+            s.gc[rg] = make_float4((float)(e3 * kLog2e), (float)(e4 * kLog2e),
+                                   (float)(1.0 / d->mol_weight[k]), 0.0f);
+        }
+    }
+    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t ntb = tb.empty() ? 1 : tb.size(), nfa = fall.empty() ? 1 : fall.size();
+    const size_t o_rx = 0, o_sp = align(sizeof(RxnT) * rx.size()),
+                 o_tb = align(o_sp + sizeof(SpecT) * ns), o_fa = align(o_tb + sizeof(int2) * ntb),
+                 total = align(o_fa + sizeof(FallT) * nfa);
+    std::vector<unsigned char> h(total, 0);
+    memcpy(h.data() + o_rx, rx.data(), sizeof(RxnT) * rx.size());
+    memcpy(h.data() + o_sp, sp.data(), sizeof(SpecT) * ns);
+    if (!tb.empty()) memcpy(h.data() + o_tb, tb.data(), sizeof(int2) * tb.size());
+    if (!fall.empty()) memcpy(h.data() + o_fa, fall.data(), sizeof(FallT) * fall.size());
+    F32TView v{};
+    v.ns = ns;
+    v.n_rec = (int)rx.size();
+    v.n_tb = (int)tb.size();
+    v.n_fall = (int)fall.size();
+    v.t_mid = d->t_mid;
+    auto df2c = [](double x) {
+        float h, l;
+        dsplit2(x, h, l);
+        return make_float2(h, l);
+    };
+    v.lg2T0 = df2c(log2(kT0));
+    v.invT0 = df2c(1.0 / kT0);
+    v.lg2R = df2c(log2(kR));
+    v.lg2_pref_R = df2c(log2(d->p_ref / kR));
+    v.log2e = df2c(kLog2e);
+    // the kernel needs one warp's tables and the block's staged tables in shared memory
+    if (block_fixed_bytes(v) + warp_pf_bytes(ns) + warp_om_bytes(ns) > kTSmemMax) return CHEM_OK;
+    void *dp = nullptr;
+    cudaError_t e = cudaMalloc(&dp, total);
+    if (e != cudaSuccess) return set_error(CHEM_ENOMEM, "cudaMalloc(%zu): %s", total, cudaGetErrorString(e));
+    e = cudaMemcpy(dp, h.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(dp);
+        return set_error(CHEM_ECUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
+    }
+    unsigned char *base = (unsigned char *)dp;
+    v.rxn = (const RxnT *)(base + o_rx);
+    v.spec = (const SpecT *)(base + o_sp);
+    v.tb = (const int2 *)(base + o_tb);
+    v.fall = (const FallT *)(base + o_fa);
+    v.ok = true;
+    m->vt = v;
+    m->d_f32t = dp;
+    m->device_bytes += total;
+    return CHEM_OK;
+}
+
+void f32t_free_tables(chem_mech *m)
+{
+    if (m->d_f32t) cudaFree(m->d_f32t);
+    m->d_f32t = nullptr;
+    m->vt.ok = false;
+}
+
+namespace {
+
+__device__ __forceinline__ float grid8(float x) { return __fsub_rn(__fadd_rn(x, kGridAdd), kGridAdd); }
+
+// 2^x, flushed to zero below the normal range (MUFU exp2)
+__device__ __forceinline__ float ex2_ftz(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// log2 x (MUFU log2) for the bounded factors of the third-body and falloff terms
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// (H, L) += c d for a double-float coefficient c and a double-float cell feature d: the
+// rounded product goes to the 2^-8 grid in H, its remainder and rounding error to L.
+__device__ __forceinline__ void acc_prod(float &H, float &L, float ch, float cl, float dh, float dl)
+{
+    const float p = __fmul_rn(ch, dh);
+    const float e = fmaf(ch, dl, fmaf(cl, dh, fmaf(ch, dh, -p)));
+    const float ph = grid8(p);
+    H = __fadd_rn(H, ph);
+    L = __fadd_rn(L, __fadd_rn(__fsub_rn(p, ph), e));
+}
+
+// double-float arithmetic (Knuth two-sum, Dekker fast two-sum, FMA two-product); the
+// explicit _rn forms keep the compiler from contracting them
+struct dflt {
+    float h, l;
+};
+__device__ __forceinline__ dflt two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ dflt fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dflt df_add(dflt a, dflt b)
+{
+    const dflt s = two_sum(a.h, b.h);
+    return fast_two_sum(s.h, __fadd_rn(__fadd_rn(a.l, b.l), s.l));
+}
+__device__ __forceinline__ dflt df_mul(dflt a, dflt b)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    return fast_two_sum(p, fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p))));
+}
+__device__ __forceinline__ dflt df_neg(dflt a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ dflt df_of(float2 v) { return {v.x, v.y}; }
+
+// log2 of a positive normal float as a double-float: x = 2^e m with m in [0.75, 1.5),
+// ln m = 2 atanh(s) = 2 (s + s^3/3 + s^5/5 + ...), s = (m - 1) / (m + 1), |s| <= 1/5; the
+// series to s^13 leaves < 1e-11, s carries its division residual
+__device__ __forceinline__ dflt df_log2f(float x, dflt log2e)
+{
+    const int bits = __float_as_int(x);
+    int e = ((bits >> 23) & 0xFF) - 127;
+    float m = __int_as_float((bits & 0x007FFFFF) | 0x3F800000);      // [1, 2)
+    if (m >= 1.5f) {
+        m *= 0.5f;
+        e += 1;
+    }
+    const float num = __fsub_rn(m, 1.0f);                               // exact
+    const dflt den = two_sum(m, 1.0f);
+    const float sh = __fdiv_rn(num, den.h);
+    const float sl = __fdiv_rn(__fsub_rn(fmaf(-sh, den.h, num), __fmul_rn(sh, den.l)), den.h);
+    const float s2 = __fmul_rn(sh, sh);
+    float t = fmaf(s2, 1.0f / 13.0f, 1.0f / 11.0f);
+    t = fmaf(s2, t, 1.0f / 9.0f);
+    t = fmaf(s2, t, 1.0f / 7.0f);
+    t = fmaf(s2, t, 1.0f / 5.0f);
+    t = fmaf(s2, t, 1.0f / 3.0f);
+    t = __fmul_rn(t, s2);                                               // s^2/3 + s^4/5 + ...
+    const dflt lnm = fast_two_sum(2.0f * sh, fmaf(2.0f * sh, t, 2.0f * sl));
+    return df_add({(float)e, 0.0f}, df_mul(lnm, log2e));
+}
+
+// Split a double-float onto the grid: head exact in float, remainder rounded.
+__device__ __forceinline__ void grid_split(dflt x, float &h, float &r)
+{
+    h = grid8(x.h);
+    r = __fadd_rn(__fsub_rn(x.h, h), x.l);
+}
+
+struct CellF {
+    float d1h, d2h, d2l;                     // centred log2 T and 1/T
+    float ctH, ctR;                          // log2 c_tot on the grid
+    float Tf, invT;
+};
+
+// q_net of one reaction for the lane's cell; NF / NR reactant / product slots, KIND 0-3.
+// pf: this lane's column of the warp's P/F rows.
+template <int NF, int NR, int KIND>
+__device__ __forceinline__ float rate(const RxnT &R, const char *pf, const int2 *tb,
+                                      const FallT *fall, const CellF &c)
+{
+    const float4 kf = R.kf;
+    float H = kf.x, L = fmaf(R.b, c.d1h, kf.y);              // log2 k_inf (Eq. 6)
+    acc_prod(H, L, kf.z, kf.w, c.d2h, c.d2l);
+    float fH = 0.0f, fL = 0.0f;
+    bool live = true;
+    if (KIND != 0) {
+        // M / c_tot = 1 + sum_k (eff_k - 1) X_k, X_k = 2^(P_k - log2 c_tot)      (Sec. 2.4)
+        float s = 1.0f;
+        const uint32_t tw = R.tb;
+        const int t1 = (int)(tw >> 16);
+        for (int t = (int)(tw & 0xFFFFu); t < t1; ++t) {
+            const int2 e = tb[t];
+            const float2 p = *(const float2 *)(pf + e.x);
+            s = fmaf(__int_as_float(e.y), ex2_ftz(__fsub_rn(p.x, c.ctH) + __fsub_rn(p.y, c.ctR)), s);
+        }
+        live = s > 0.0f;
+        const float ls = lg2_approx(s);
+        if (KIND == 1) {
+            fH = c.ctH;
+            fL = __fadd_rn(c.ctR, ls);
+        } else {
+            const FallT &F = fall[R.meta >> 8];
+            const float4 k0 = F.k0, t0 = F.t0;
+            float H0 = k0.x, L0 = fmaf(t0.x, c.d1h, k0.y);
+            acc_prod(H0, L0, k0.z, k0.w, c.d2h, c.d2l);
+            // log2 Pr = log2 k0 - log2 k_inf + log2 M
+            const float pH = __fadd_rn(__fsub_rn(H0, H), c.ctH);
+            const float pL = __fadd_rn(__fadd_rn(__fsub_rn(L0, L), c.ctR), ls);
+            const float lPr = pH + pL;
+            // log2(Pr / (1 + Pr)) without cancellation on either side of Pr = 1
+            const bool low = lPr < 0.0f;
+            const float t1p = lg2_approx(1.0f + ex2_ftz(low ? lPr : -lPr));
+            fH = low ? pH : 0.0f;
+            fL = low ? __fsub_rn(pL, t1p) : -t1p;
+            if (KIND == 3) {
+                // Troe broadening (Gilbert-Luther-Troe form), log10 F from log2 units
+                const float4 tx = F.t1;
+                const float Fc = fmaf(t0.y, ex2_ftz(c.Tf * t0.w),
+                                      fmaf(t0.z, ex2_ftz(c.Tf * tx.x), tx.z * ex2_ftz(tx.y * c.invT)));
+                const float lFc = lg2_approx(Fc) * 0.30102999566398120f;
+                const float c1 = -0.4f - 0.67f * lFc, nn = 0.75f - 1.27f * lFc;
+                const float xx = lPr * 0.30102999566398120f + c1;
+                const float f1 = __fdividef(xx, nn - 0.14f * xx);
+                fL = __fadd_rn(fL, __fdividef(lFc, 1.0f + f1 * f1) * 3.3219280948873623f);
+            }
+        }
+    }
+    float xfH = H, xfL = L;
+    if (KIND != 0) {
+        xfH = __fadd_rn(H, fH);
+        xfL = __fadd_rn(L, fL);
+    }
+    float xrH = __fadd_rn(xfH, R.rb), xrL = xfL;
+    const int4 *E = (const int4 *)R.ent;
+#pragma unroll
+    for (int t = 0; t < NF; ++t) {
+        const int4 w = E[rxnt_react(t) / 2];
+        const int off = rxnt_react(t) % 2 ? w.z : w.x;
+        const float nu = __int_as_float(rxnt_react(t) % 2 ? w.w : w.y);
+        const float4 p = *(const float4 *)(pf + off);
+        xfH = fmaf(nu, p.x, xfH);
+        xfL = fmaf(nu, p.y, xfL);
+        xrH = fmaf(nu, p.z, xrH);
+        xrL = fmaf(nu, p.w, xrL);
+    }
+#pragma unroll
+    for (int t = 0; t < NR; ++t) {
+        const int4 w = E[rxnt_prod(t) / 2];
+        const int off = rxnt_prod(t) % 2 ? w.z : w.x;
+        const float nu = __int_as_float(rxnt_prod(t) % 2 ? w.w : w.y);
+        const float4 p = *(const float4 *)(pf + off);
+        xrH = fmaf(nu, __fsub_rn(p.x, p.z), xrH);
+        xrL = fmaf(nu, __fsub_rn(p.y, p.w), xrL);
+    }
+    const float q = ex2_ftz(xfH + xfL) - ex2_ftz(xrH + xrL);
+    return live ? q : 0.0f;
+}
+
+// omega_k += (nu''_kj - nu'_kj) q_net,j (Eq. 2); om: this lane's column of the omega tile.
+// A reaction's net species are distinct (unused entries add 0 to the zero row), so all its
+// values are read before any is written: one shared-memory round trip per reaction.
+template <int NN>
+__device__ __forceinline__ void scatter(const RxnT &R, char *om, float q)
+{
+    const int4 *E = (const int4 *)R.ent;
+    int off[NN];
+    float nu[NN], v[NN];
+#pragma unroll
+    for (int t = 0; t < NN; ++t) {
+        const int4 w = E[rxnt_net(t) / 2];
+        off[t] = rxnt_net(t) % 2 ? w.z : w.x;
+        nu[t] = __int_as_float(rxnt_net(t) % 2 ? w.w : w.y);
+        v[t] = *(const float *)(om + off[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < NN; ++t) *(float *)(om + off[t]) = fmaf(nu[t], q, v[t]);
+}
+
+// entry (offset, coefficient) of pair index `pair` of record R
+__device__ __forceinline__ void entry(const RxnT &R, int pair, int &off, float &nu)
+{
+    const int4 w = ((const int4 *)R.ent)[pair / 2];
+    off = pair % 2 ? w.z : w.x;
+    nu = __int_as_float(pair % 2 ? w.w : w.y);
+}
+
+// omega update of a quad: one round when the quad's net species are pairwise distinct (meta
+// bit 3), else one round per reaction
+template <int NN>
+__device__ __forceinline__ void scatter_quad(const RxnT *R, char *om, const float *q)
+{
+    if (R[0].meta & 8u) {
+        int off[kQuad][NN];
+        float nu[kQuad][NN], v[kQuad][NN];
+#pragma unroll
+        for (int u = 0; u < kQuad; ++u)
+#pragma unroll
+            for (int t = 0; t < NN; ++t) {
+                entry(R[u], rxnt_net(t), off[u][t], nu[u][t]);
+                v[u][t] = *(const float *)(om + off[u][t]);
+            }
+#pragma unroll
+        for (int u = 0; u < kQuad; ++u)
+#pragma unroll
+            for (int t = 0; t < NN; ++t) *(float *)(om + off[u][t]) = fmaf(nu[u][t], q[u], v[u][t]);
+    } else {
+#pragma unroll
+        for (int u = 0; u < kQuad; ++u) scatter<NN>(R[u], om, q[u]);
+    }
+}
+
+// kQuad reactions of one group with third-body or falloff factors: rates, then omega
+template <int NF, int NR, int NN, int KIND>
+__device__ __forceinline__ void quad(const RxnT *R, const char *pf, char *om, const int2 *tb,
+                                     const FallT *fall, const CellF &c)
+{
+    float q[kQuad];
+#pragma unroll
+    for (int u = 0; u < kQuad; ++u) q[u] = rate<NF, NR, KIND>(R[u], pf, tb, fall, c);
+    scatter_quad<NN>(R, om, q);
+}
+
+// kQuad elementary reactions, the arithmetic of rate<NF, NR, 0> written step by step across
+// the four so that consecutive instructions are independent
+template <int NF, int NR, int NN>
+__device__ __forceinline__ void quad0(const RxnT *R, const char *pf, char *om, const CellF &c)
+{
+    constexpr int U = kQuad;
+    float4 kf[U];
+    float b[U], rb[U], p[U], e[U], ph[U], xfH[U], xfL[U], xrH[U], xrL[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        kf[u] = R[u].kf;
+        const float4 hd = *(const float4 *)&R[u].b;
+        b[u] = hd.x;
+        rb[u] = hd.w;
+    }
+    // log2 k_inf (Eq. 6): head of (-E/R log2 e) d2 on the grid, the rest in L
+#pragma unroll
+    for (int u = 0; u < U; ++u) p[u] = __fmul_rn(kf[u].z, c.d2h);
+#pragma unroll
+    for (int u = 0; u < U; ++u) e[u] = fmaf(kf[u].z, c.d2h, -p[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) e[u] = fmaf(kf[u].w, c.d2h, e[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) e[u] = fmaf(kf[u].z, c.d2l, e[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) ph[u] = __fadd_rn(p[u], kGridAdd);
+#pragma unroll
+    for (int u = 0; u < U; ++u) ph[u] = __fsub_rn(ph[u], kGridAdd);
+#pragma unroll
+    for (int u = 0; u < U; ++u) xfL[u] = fmaf(b[u], c.d1h, kf[u].y);
+#pragma unroll
+    for (int u = 0; u < U; ++u) xfH[u] = __fadd_rn(kf[u].x, ph[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) e[u] = __fadd_rn(__fsub_rn(p[u], ph[u]), e[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) xfL[u] = __fadd_rn(xfL[u], e[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        xrH[u] = __fadd_rn(xfH[u], rb[u]);
+        xrL[u] = xfL[u];
+    }
+    // species terms (heads exact on the grid)
+#pragma unroll
+    for (int t = 0; t < NF; ++t) {
+        float4 P[U];
+        float nu[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            int off;
+            entry(R[u], rxnt_react(t), off, nu[u]);
+            P[u] = *(const float4 *)(pf + off);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            xfH[u] = fmaf(nu[u], P[u].x, xfH[u]);
+            xfL[u] = fmaf(nu[u], P[u].y, xfL[u]);
+            xrH[u] = fmaf(nu[u], P[u].z, xrH[u]);
+            xrL[u] = fmaf(nu[u], P[u].w, xrL[u]);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < NR; ++t) {
+        float4 P[U];
+        float nu[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            int off;
+            entry(R[u], rxnt_prod(t), off, nu[u]);
+            P[u] = *(const float4 *)(pf + off);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            xrH[u] = fmaf(nu[u], __fsub_rn(P[u].x, P[u].z), xrH[u]);
+            xrL[u] = fmaf(nu[u], __fsub_rn(P[u].y, P[u].w), xrL[u]);
+        }
+    }
+    float q[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) q[u] = ex2_ftz(xfH[u] + xfL[u]) - ex2_ftz(xrH[u] + xrL[u]);
+    scatter_quad<NN>(R, om, q);
+}
+
+__device__ __forceinline__ void copy16(void *dst, const void *src, size_t bytes)
+{
+    for (size_t o = threadIdx.x * 16; o < bytes; o += (size_t)blockDim.x * 16)
+        *(float4 *)((char *)dst + o) = __ldg((const float4 *)((const char *)src + o));
+}
+
+constexpr int kMaxWarps = 8;
+constexpr int kPieces = kChunk * (int)sizeof(RxnT) / 16;          // float4 pieces per chunk
+
+__global__ void __launch_bounds__(32 * kMaxWarps, 1)
+k_source_f32t(F32TView v, int64_t n, const float *__restrict__ T, const float *__restrict__ P,
+              const float *__restrict__ Y, int64_t ldY, float *__restrict__ om, int64_t ldO)
+{
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    const int ns = v.ns, lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    // block tables
+    SpecT *s_spec = (SpecT *)s_raw;
+    size_t off = a16(sizeof(SpecT) * ns);
+    int2 *s_tb = (int2 *)(s_raw + off);
+    off += a16(sizeof(int2) * v.n_tb);
+    FallT *s_fall = (FallT *)(s_raw + off);
+    off += a16(sizeof(FallT) * v.n_fall);
+    RxnT *s_rec = (RxnT *)(s_raw + off);
+    off += 2 * kChunk * sizeof(RxnT);
+    unsigned char *wbase = s_raw + off + (size_t)w * (warp_pf_bytes(ns) + warp_om_bytes(ns));
+    float4 *s_pf = (float4 *)wbase;
+    float *s_om = (float *)(wbase + warp_pf_bytes(ns));
+    copy16(s_spec, v.spec, sizeof(SpecT) * ns);
+    for (int t = threadIdx.x; t < v.n_tb; t += blockDim.x) s_tb[t] = __ldg(v.tb + t);
+    copy16(s_fall, v.fall, sizeof(FallT) * v.n_fall);
+    copy16(s_rec, v.rxn, sizeof(RxnT) * kChunk);
+    __syncthreads();
+
+    // the warp's cells; a warp past the batch redoes the last cell and stores nothing
+    const int64_t i0 = ((int64_t)blockIdx.x * wpb + w) * 32;
+    const int nc = i0 < n ? (int)(n - i0 < 32 ? n - i0 : 32) : 0;
+    const int64_t ib = i0 < n ? i0 : n - 1;
+    const int ncl = nc > 0 ? nc : 1;
+    const int me = lane < ncl ? lane : ncl - 1;
+    const int64_t i = ib + me;
+
+    // ---- per-cell features in double-float arithmetic
+    CellF c;
+    c.Tf = T[i];
+    const dflt log2e = df_of(v.log2e);
+    const dflt lT = df_log2f(c.Tf, log2e);
+    const dflt d1 = df_add(lT, df_neg(df_of(v.lg2T0)));                 // log2 T - log2 T0
+    c.d1h = d1.h;
+    const float d1l = d1.l;
+    c.invT = __fdiv_rn(1.0f, c.Tf);
+    const dflt rT = {c.invT, __fmul_rn(c.invT, fmaf(-c.Tf, c.invT, 1.0f))};   // 1/T
+    const dflt d2 = df_add(rT, df_neg(df_of(v.invT0)));                 // 1/T - 1/T0
+    c.d2h = d2.h;
+    c.d2l = d2.l;
+    const float u = __fmul_rn(__fsub_rn(c.Tf, 1000.0f), 1e-3f);         // T/1000 - 1
+    const int rg = (double)c.Tf >= v.t_mid ? 1 : 0;
+    // log2 c_tot = log2(P / (R T)); log2(p_ref / (R T))
+    grid_split(df_add(df_add(df_log2f(P[i], log2e), df_neg(df_of(v.lg2R))), df_neg(lT)), c.ctH, c.ctR);
+    float gpH, gpR;
+    grid_split(df_add(df_of(v.lg2_pref_R), df_neg(lT)), gpH, gpR);
+
+    // ---- species: z_k = Y_k / W_k, log2 z_k (exact exponent + grid head of the mantissa's
+    // log2), sum_k z_k (double-float), F_k; Y staged 32 species at a time (coalesced rows)
+    float zh = 0.0f, zl = 0.0f;
+    for (int k0 = 0; k0 < ns; k0 += 32) {
+        const int kn = ns - k0 < 32 ? ns - k0 : 32;
+        __syncwarp();
+        if (lane < kn)
+            for (int cc = 0; cc < ncl; ++cc) s_om[cc * kOmStride + lane] = Y[(ib + cc) * ldY + k0 + lane];
+        __syncwarp();
+#pragma unroll 2
+        for (int kk = 0; kk < kn; ++kk) {
+            const int k = k0 + kk;
+            const float4 ga = s_spec[k].ga[rg], gb = s_spec[k].gb[rg], gc = s_spec[k].gc[rg];
+            const float z = fmaxf(s_om[me * kOmStride + kk], 0.0f) * gc.z;
+            {   // two-sum into (zh, zl)
+                const float s = __fadd_rn(zh, z), bb = __fsub_rn(s, zh);
+                zl = __fadd_rn(zl, __fadd_rn(__fsub_rn(zh, __fsub_rn(s, bb)), __fsub_rn(z, bb)));
+                zh = s;
+            }
+            // z = m 2^ex, m in [0.5, 1) (subnormal z scaled by 2^24 first)
+            const bool sub = z < 1.17549435e-38f;
+            const int bits = __float_as_int(sub ? z * 16777216.0f : z);
+            const int ex = ((bits >> 23) & 0xFF) - 126 - (sub ? 24 : 0);
+            const float lm = log2f(__int_as_float((bits & 0x007FFFFF) | 0x3F000000));
+            const float lmh = grid8(lm);
+            const float Ph = z > 0.0f ? __fadd_rn((float)ex, lmh) : kAbsentLog2;
+            const float Pl = z > 0.0f ? __fsub_rn(lm, lmh) : 0.0f;
+            // F_k = G_k(T) + log2(p_ref/RT)
+            float FH = __fadd_rn(ga.x, gpH), FL = __fadd_rn(ga.y, gpR);
+            acc_prod(FH, FL, ga.z, ga.w, c.d1h, d1l);
+            acc_prod(FH, FL, gb.x, gb.y, c.d2h, c.d2l);
+            FL = __fadd_rn(FL, u * fmaf(u, fmaf(u, fmaf(u, gc.y, gc.x), gb.w), gb.z));
+            s_pf[k * 32 + lane] = make_float4(Ph, Pl, FH, FL);
+        }
+    }
+    // log2 C_k = log2 z_k + log2(c_tot / sum z): add the cell's shift to every P_k
+    float cnH = c.ctH, cnR = c.ctR;
+    if (zh > 0.0f) {
+        const dflt ls = df_log2f(zh, log2e);
+        float lsH, lsR;
+        grid_split({ls.h, __fadd_rn(ls.l, __fmul_rn(__fdiv_rn(zl, zh), log2e.h))}, lsH, lsR);
+        cnH = __fsub_rn(cnH, lsH);
+        cnR = __fsub_rn(cnR, lsR);
+    }
+    __syncwarp();
+    for (int k = 0; k < ns; ++k) {
+        float2 *p = (float2 *)&s_pf[k * 32 + lane];
+        const float2 t = *p;
+        *p = make_float2(__fadd_rn(t.x, cnH), __fadd_rn(t.y, cnR));
+        s_om[k * kOmStride + lane] = 0.0f;
+    }
+    s_pf[ns * 32 + lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);       // the zero row
+    s_om[ns * kOmStride + lane] = 0.0f;
+
+    // ---- reactions: chunks of records staged one ahead, pairs of one group type
+    const char *pf = (const char *)s_pf + lane * 16;
+    char *omc = (char *)s_om + lane * 4;
+    const int nch = v.n_rec / kChunk;
+    const float4 *src = (const float4 *)v.rxn;
+    for (int ch = 0; ch < nch; ++ch) {
+        float4 pre[kPieces / 32];
+        const bool more = ch + 1 < nch;
+        if (more) {
+#pragma unroll
+            for (int r = 0; r < kPieces / 32; ++r) {
+                const int p = threadIdx.x + r * blockDim.x;
+                if (p < kPieces) pre[r] = __ldg(src + (size_t)(ch + 1) * kPieces + p);
+            }
+        }
+        const RxnT *rc = s_rec + (ch & 1) * kChunk;
+#pragma unroll 1
+        for (int r = 0; r < kChunk; r += kQuad) {
+            const RxnT *R = rc + r;
+            switch (R->meta & 7u) {
+            case kGSmall: quad0<2, 2, 4>(R, pf, omc, c); break;
+            case kGBig: quad0<3, 3, 6>(R, pf, omc, c); break;
+            case kGThird: quad<3, 3, 6, 1>(R, pf, omc, s_tb, s_fall, c); break;
+            case kGLind: quad<3, 3, 6, 2>(R, pf, omc, s_tb, s_fall, c); break;
+            default: quad<3, 3, 6, 3>(R, pf, omc, s_tb, s_fall, c); break;
+            }
+        }
+        if (more) {
+            float4 *dst = (float4 *)(s_rec + ((ch + 1) & 1) * kChunk);
+#pragma unroll
+            for (int r = 0; r < kPieces / 32; ++r) {
+                const int p = threadIdx.x + r * blockDim.x;
+                if (p < kPieces) dst[p] = pre[r];
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- omega rows out, lanes over species
+    __syncwarp();
+    for (int cc = 0; cc < nc; ++cc)
+        for (int k = lane; k < ns; k += 32) om[(i0 + cc) * ldO + k] = s_om[k * kOmStride + cc];
+}
+
+}  // namespace
+
+chem_status launch_source_fp32_t(const chem_mech *m, int64_t n, const float *T, const float *P,
+                                 const float *Y, int64_t ldY, float *om, int64_t ldO,
+                                 cudaStream_t s)
+{
+    static SmemOptIn opt;
+    if (n <= 0) return CHEM_OK;
+    if (!m->vt.ok) return set_error(CHEM_EUNSUPPORTED, "fp32: no thread-per-cell tables");
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+    const size_t fixed = block_fixed_bytes(m->vt), per_warp = warp_pf_bytes(m->ns) + warp_om_bytes(m->ns);
+    int wmax = (int)((kTSmemMax - fixed) / per_warp);
+    wmax = wmax < 1 ? 1 : wmax > kMaxWarps ? kMaxWarps : wmax;
+    // warps per block: enough blocks to cover every SM before blocks grow
+    const int64_t warps = (n + 31) / 32;
+    int64_t wpb = (warps + nsm - 1) / nsm;
+    wpb = wpb < 1 ? 1 : wpb > wmax ? wmax : wpb;
+    const int64_t blocks = (warps + wpb - 1) / wpb;
+    const size_t smem = fixed + (size_t)wpb * per_warp;
+    chem_status st = launch_opted(opt, (const void *)k_source_f32t, (int)kTSmemMax, "fp32", [&] {
+        k_source_f32t<<<(unsigned)blocks, (unsigned)(32 * wpb), smem, s>>>(m->vt, n, T, P, Y, ldY, om, ldO);
+    });
+    if (st == CHEM_OK) g_launches.fetch_add(1);
+    return st;
+}
+
+}  // namespace chem

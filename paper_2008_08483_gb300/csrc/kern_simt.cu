@@ -571,6 +571,7 @@ chem_status launch_source_fp32(const chem_mech *m, int64_t n, const float *T, co
                                const float *Y, int64_t ldY, float *om, int64_t ldO,
                                cudaStream_t s)
 {
+    if (m->vt.ok) return launch_source_fp32_t(m, n, T, P, Y, ldY, om, ldO, s);
     KcAnnView none;
     memset(&none, 0, sizeof none);
     return launch_f32<false>(m, none, n, T, P, Y, ldY, om, ldO, s, "fp32");
