@@ -157,7 +157,8 @@ struct alignas(16) RxnT {
                                  // as double-float (hi, lo)
     float b;                     // coefficient of d1 (temperature exponent)
     uint32_t meta;               // group type | falloff index << 8
-    uint32_t tb;                 // listed third-body efficiencies: first | end << 16
+    uint32_t tb;                 // first record of a quad: its efficiency lists in the
+                                 // staged table, first | entries per reaction << 16
     float rb;                    // added to the reverse exponent: 0, or -2000 if irreversible
     int32_t ent[24];
 };

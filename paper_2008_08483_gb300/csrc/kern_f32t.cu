@@ -15,8 +15,10 @@
 // the per-species terms and of the products of a reaction's temperature coefficients with
 // the cell's centred temperature features are put on that grid, so the sums of heads with
 // small integer stoichiometric coefficients are exact in FP32; only L carries rounding, at
-// the magnitude of L.  The exponent is rounded once, at the magnitude of the result, before
-// the exp2.  Per-cell temperature features are computed in FP64 once per cell.
+// the magnitude of L, and 2^(H + L) is taken as 2^H 2^L.  The per-cell temperature features
+// are double-float (log2 by an atanh series, 1/T with its Newton residual); the bounded
+// third-body and falloff factors use the MUFU exp2 / log2.  omega accumulates in FP32 in
+// the processing order (per-cell error ~2e-6 of max |omega| at 53/325).
 //
 // Layout: one block of W warps per SM-sized share of the batch.  The block stages the species
 // table, the third-body lists and the falloff parameters once, and the reaction records in
@@ -120,6 +122,7 @@ chem_status f32t_build_tables(chem_mech *m, const chem_mech_desc *d)
     std::vector<int2> tb;
     std::vector<FallT> fall;
     std::vector<RxnT> one(nr);
+    std::vector<std::vector<int2>> lists(nr);      // listed efficiencies (row offset, eff - 1)
     for (int j = 0; j < nr; ++j) {
         RxnT &r = one[j];
         memset(&r, 0, sizeof r);
@@ -167,7 +170,6 @@ chem_status f32t_build_tables(chem_mech *m, const chem_mech_desc *d)
             fall.push_back(f);
         }
         r.meta = (uint32_t)type | (fidx << 8);
-        const size_t t0 = tb.size();
         if (kind >= 1)
             for (int k = 0; k < ns; ++k) {
                 const double e = d->eff ? d->eff[(size_t)j * ns + k] : 1.0;
@@ -175,11 +177,9 @@ chem_status f32t_build_tables(chem_mech *m, const chem_mech_desc *d)
                     const float ef = (float)(e - 1.0);
                     int bits;
                     memcpy(&bits, &ef, 4);
-                    tb.push_back(make_int2(k * kPfRow, bits));
+                    lists[j].push_back(make_int2(k * kPfRow, bits));
                 }
             }
-        if (tb.size() > 65535) return CHEM_OK;
-        r.tb = (uint32_t)t0 | ((uint32_t)tb.size() << 16);
     }
     // records grouped by type, in quads: greedily packed so that a quad's net species are
     // pairwise distinct (meta bit 3: one omega round trip), the rest in order; the last quad
@@ -234,18 +234,28 @@ chem_status f32t_build_tables(chem_mech *m, const chem_mech_desc *d)
         }
         for (size_t qn = 0; qn < disjoint.size(); ++qn) {
             const size_t first = rx.size();
+            size_t nit = 0;
             for (size_t b = qn * kQuad; b < (qn + 1) * kQuad; ++b) {
                 if (b < order.size()) {
                     rx.push_back(one[order[b]]);
+                    nit = std::max(nit, lists[order[b]].size());
                 } else {
                     RxnT pad = rx.back();
                     pad.kf = make_float4(kOff, 0.0f, 0.0f, 0.0f);
                     pad.b = 0.0f;
-                    pad.tb = (pad.tb & 0xFFFFu) * 0x10001u;     // no third-body entries
                     clear_entries(pad, ns);
                     rx.push_back(pad);
                 }
             }
+            // the quad's efficiency lists as [entry][reaction], padded with zero entries
+            if (tb.size() + nit * kQuad > 65535 || nit > 65535) return CHEM_OK;
+            const size_t base = tb.size();
+            for (size_t it = 0; it < nit; ++it)
+                for (size_t b = qn * kQuad; b < (qn + 1) * kQuad; ++b) {
+                    const bool real = b < order.size() && it < lists[order[b]].size();
+                    tb.push_back(real ? lists[order[b]][it] : make_int2(ns * kPfRow, 0));
+                }
+            rx[first].tb = (uint32_t)base | ((uint32_t)nit << 16);
             if (disjoint[qn]) rx[first].meta |= 8u;
         }
     }
@@ -441,90 +451,6 @@ struct CellF {
     float Tf, invT;
 };
 
-// q_net of one reaction for the lane's cell; NF / NR reactant / product slots, KIND 0-3.
-// pf: this lane's column of the warp's P/F rows.
-template <int NF, int NR, int KIND>
-__device__ __forceinline__ float rate(const RxnT &R, const char *pf, const int2 *tb,
-                                      const FallT *fall, const CellF &c)
-{
-    const float4 kf = R.kf;
-    float H = kf.x, L = fmaf(R.b, c.d1h, kf.y);              // log2 k_inf (Eq. 6)
-    acc_prod(H, L, kf.z, kf.w, c.d2h, c.d2l);
-    float fH = 0.0f, fL = 0.0f;
-    bool live = true;
-    if (KIND != 0) {
-        // M / c_tot = 1 + sum_k (eff_k - 1) X_k, X_k = 2^(P_k - log2 c_tot)      (Sec. 2.4)
-        float s = 1.0f;
-        const uint32_t tw = R.tb;
-        const int t1 = (int)(tw >> 16);
-        for (int t = (int)(tw & 0xFFFFu); t < t1; ++t) {
-            const int2 e = tb[t];
-            const float2 p = *(const float2 *)(pf + e.x);
-            s = fmaf(__int_as_float(e.y), ex2_ftz(__fsub_rn(p.x, c.ctH) + __fsub_rn(p.y, c.ctR)), s);
-        }
-        live = s > 0.0f;
-        const float ls = lg2_approx(s);
-        if (KIND == 1) {
-            fH = c.ctH;
-            fL = __fadd_rn(c.ctR, ls);
-        } else {
-            const FallT &F = fall[R.meta >> 8];
-            const float4 k0 = F.k0, t0 = F.t0;
-            float H0 = k0.x, L0 = fmaf(t0.x, c.d1h, k0.y);
-            acc_prod(H0, L0, k0.z, k0.w, c.d2h, c.d2l);
-            // log2 Pr = log2 k0 - log2 k_inf + log2 M
-            const float pH = __fadd_rn(__fsub_rn(H0, H), c.ctH);
-            const float pL = __fadd_rn(__fadd_rn(__fsub_rn(L0, L), c.ctR), ls);
-            const float lPr = pH + pL;
-            // log2(Pr / (1 + Pr)) without cancellation on either side of Pr = 1
-            const bool low = lPr < 0.0f;
-            const float t1p = lg2_approx(1.0f + ex2_ftz(low ? lPr : -lPr));
-            fH = low ? pH : 0.0f;
-            fL = low ? __fsub_rn(pL, t1p) : -t1p;
-            if (KIND == 3) {
-                // Troe broadening (Gilbert-Luther-Troe form), log10 F from log2 units
-                const float4 tx = F.t1;
-                const float Fc = fmaf(t0.y, ex2_ftz(c.Tf * t0.w),
-                                      fmaf(t0.z, ex2_ftz(c.Tf * tx.x), tx.z * ex2_ftz(tx.y * c.invT)));
-                const float lFc = lg2_approx(Fc) * 0.30102999566398120f;
-                const float c1 = -0.4f - 0.67f * lFc, nn = 0.75f - 1.27f * lFc;
-                const float xx = lPr * 0.30102999566398120f + c1;
-                const float f1 = __fdividef(xx, nn - 0.14f * xx);
-                fL = __fadd_rn(fL, __fdividef(lFc, 1.0f + f1 * f1) * 3.3219280948873623f);
-            }
-        }
-    }
-    float xfH = H, xfL = L;
-    if (KIND != 0) {
-        xfH = __fadd_rn(H, fH);
-        xfL = __fadd_rn(L, fL);
-    }
-    float xrH = __fadd_rn(xfH, R.rb), xrL = xfL;
-    const int4 *E = (const int4 *)R.ent;
-#pragma unroll
-    for (int t = 0; t < NF; ++t) {
-        const int4 w = E[rxnt_react(t) / 2];
-        const int off = rxnt_react(t) % 2 ? w.z : w.x;
-        const float nu = __int_as_float(rxnt_react(t) % 2 ? w.w : w.y);
-        const float4 p = *(const float4 *)(pf + off);
-        xfH = fmaf(nu, p.x, xfH);
-        xfL = fmaf(nu, p.y, xfL);
-        xrH = fmaf(nu, p.z, xrH);
-        xrL = fmaf(nu, p.w, xrL);
-    }
-#pragma unroll
-    for (int t = 0; t < NR; ++t) {
-        const int4 w = E[rxnt_prod(t) / 2];
-        const int off = rxnt_prod(t) % 2 ? w.z : w.x;
-        const float nu = __int_as_float(rxnt_prod(t) % 2 ? w.w : w.y);
-        const float4 p = *(const float4 *)(pf + off);
-        xrH = fmaf(nu, __fsub_rn(p.x, p.z), xrH);
-        xrL = fmaf(nu, __fsub_rn(p.y, p.w), xrL);
-    }
-    const float q = ex2_ftz(xfH + xfL) - ex2_ftz(xrH + xrL);
-    return live ? q : 0.0f;
-}
-
 // omega_k += (nu''_kj - nu'_kj) q_net,j (Eq. 2); om: this lane's column of the omega tile.
 // A reaction's net species are distinct (unused entries add 0 to the zero row), so all its
 // values are read before any is written: one shared-memory round trip per reaction.
@@ -578,21 +504,11 @@ __device__ __forceinline__ void scatter_quad(const RxnT *R, char *om, const floa
     }
 }
 
-// kQuad reactions of one group with third-body or falloff factors: rates, then omega
+// kQuad reactions of one group (KIND 0 elementary, 1 third-body, 2 Lindemann, 3 Troe),
+// written step by step across the four so that consecutive instructions are independent
 template <int NF, int NR, int NN, int KIND>
 __device__ __forceinline__ void quad(const RxnT *R, const char *pf, char *om, const int2 *tb,
                                      const FallT *fall, const CellF &c)
-{
-    float q[kQuad];
-#pragma unroll
-    for (int u = 0; u < kQuad; ++u) q[u] = rate<NF, NR, KIND>(R[u], pf, tb, fall, c);
-    scatter_quad<NN>(R, om, q);
-}
-
-// kQuad elementary reactions, the arithmetic of rate<NF, NR, 0> written step by step across
-// the four so that consecutive instructions are independent
-template <int NF, int NR, int NN>
-__device__ __forceinline__ void quad0(const RxnT *R, const char *pf, char *om, const CellF &c)
 {
     constexpr int U = kQuad;
     float4 kf[U];
@@ -625,6 +541,79 @@ __device__ __forceinline__ void quad0(const RxnT *R, const char *pf, char *om, c
     for (int u = 0; u < U; ++u) e[u] = __fadd_rn(__fsub_rn(p[u], ph[u]), e[u]);
 #pragma unroll
     for (int u = 0; u < U; ++u) xfL[u] = __fadd_rn(xfL[u], e[u]);
+    bool live[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) live[u] = true;
+    if (KIND != 0) {
+        // M / c_tot = 1 + sum_k (eff_k - 1) X_k, X_k = 2^(P_k - log2 c_tot)      (Sec. 2.4);
+        // the quad's lists interleaved [entry][reaction], padded with zero entries
+        float s[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) s[u] = 1.0f;
+        const uint32_t tw = R[0].tb;
+        const int2 *te = tb + (tw & 0xFFFFu);
+        const int nit = (int)(tw >> 16);
+        for (int it = 0; it < nit; ++it) {
+            int2 en[U];
+            float2 pp[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) en[u] = te[it * U + u];
+#pragma unroll
+            for (int u = 0; u < U; ++u) pp[u] = *(const float2 *)(pf + en[u].x);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                s[u] = fmaf(__int_as_float(en[u].y),
+                            ex2_ftz(__fsub_rn(pp[u].x, c.ctH) + __fsub_rn(pp[u].y, c.ctR)), s[u]);
+        }
+        float ls[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            live[u] = s[u] > 0.0f;
+            ls[u] = lg2_approx(s[u]);
+        }
+        if (KIND == 1) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                xfH[u] = __fadd_rn(xfH[u], c.ctH);
+                xfL[u] = __fadd_rn(xfL[u], __fadd_rn(c.ctR, ls[u]));
+            }
+        } else {
+            float4 k0[U], t0[U], t1[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const FallT &F = fall[R[u].meta >> 8];
+                k0[u] = F.k0;
+                t0[u] = F.t0;
+                t1[u] = F.t1;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                float H0 = k0[u].x, L0 = fmaf(t0[u].x, c.d1h, k0[u].y);
+                acc_prod(H0, L0, k0[u].z, k0[u].w, c.d2h, c.d2l);
+                // log2 Pr = log2 k0 - log2 k_inf + log2 M
+                const float pH = __fadd_rn(__fsub_rn(H0, xfH[u]), c.ctH);
+                const float pL = __fadd_rn(__fadd_rn(__fsub_rn(L0, xfL[u]), c.ctR), ls[u]);
+                const float lPr = pH + pL;
+                // log2(Pr / (1 + Pr)) without cancellation on either side of Pr = 1
+                const bool low = lPr < 0.0f;
+                const float t1p = lg2_approx(1.0f + ex2_ftz(low ? lPr : -lPr));
+                float fL = low ? __fsub_rn(pL, t1p) : -t1p;
+                if (KIND == 3) {
+                    // Troe broadening (Gilbert-Luther-Troe form), log10 F from log2 units
+                    const float Fc = fmaf(t0[u].y, ex2_ftz(c.Tf * t0[u].w),
+                                          fmaf(t0[u].z, ex2_ftz(c.Tf * t1[u].x),
+                                               t1[u].z * ex2_ftz(t1[u].y * c.invT)));
+                    const float lFc = lg2_approx(Fc) * 0.30102999566398120f;
+                    const float c1 = -0.4f - 0.67f * lFc, nn = 0.75f - 1.27f * lFc;
+                    const float xx = lPr * 0.30102999566398120f + c1;
+                    const float f1 = __fdividef(xx, nn - 0.14f * xx);
+                    fL = __fadd_rn(fL, __fdividef(lFc, 1.0f + f1 * f1) * 3.3219280948873623f);
+                }
+                xfH[u] = low ? __fadd_rn(xfH[u], pH) : xfH[u];
+                xfL[u] = __fadd_rn(xfL[u], fL);
+            }
+        }
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         xrH[u] = __fadd_rn(xfH[u], rb[u]);
@@ -667,7 +656,12 @@ __device__ __forceinline__ void quad0(const RxnT *R, const char *pf, char *om, c
     }
     float q[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) q[u] = ex2_ftz(xfH[u] + xfL[u]) - ex2_ftz(xrH[u] + xrL[u]);
+    for (int u = 0; u < U; ++u) {
+        // 2^(H + L) as 2^H 2^L: H is exact, so the exponent is never rounded at its own
+        // magnitude
+        const float qn = ex2_ftz(xfH[u]) * ex2_ftz(xfL[u]) - ex2_ftz(xrH[u]) * ex2_ftz(xrL[u]);
+        q[u] = live[u] ? qn : 0.0f;
+    }
     scatter_quad<NN>(R, om, q);
 }
 
@@ -675,6 +669,72 @@ __device__ __forceinline__ void copy16(void *dst, const void *src, size_t bytes)
 {
     for (size_t o = threadIdx.x * 16; o < bytes; o += (size_t)blockDim.x * 16)
         *(float4 *)((char *)dst + o) = __ldg((const float4 *)((const char *)src + o));
+}
+
+// log2 m for m in [0.5, 1): m' = m or 2 m in [0.75, 1.5), ln m' = 2 atanh(s) with
+// s = (m' - 1) / (m' + 1), |s| <= 1/5, series to s^11 (truncation < 2e-10)
+__device__ __forceinline__ float log2_mant(float m)
+{
+    const bool lo = m < 0.75f;
+    const float mm = lo ? 2.0f * m : m;
+    const float s = __fdividef(__fsub_rn(mm, 1.0f), __fadd_rn(mm, 1.0f));
+    const float s2 = s * s;
+    float t = fmaf(s2, 1.0f / 11.0f, 1.0f / 9.0f);
+    t = fmaf(s2, t, 1.0f / 7.0f);
+    t = fmaf(s2, t, 1.0f / 5.0f);
+    t = fmaf(s2, t, 1.0f / 3.0f);
+    return fmaf(2.0f * fmaf(s * s2, t, s), 1.4426950408889634f, lo ? -1.0f : 0.0f);
+}
+
+// U consecutive species of the lane's cell: z_k = Y_k / W_k into the double-float sum (in
+// species order), P_k = log2 z_k as exact exponent + grid head of the mantissa's log2 (the
+// cell's shift to log2 C_k is added later), F_k = G_k(T) + log2(p_ref/RT); out: P/F rows
+template <int U>
+__device__ __forceinline__ void species_block(const SpecT *sp, const float *yrow, int rg,
+                                              const CellF &c, float d1l, float u, float gpH,
+                                              float gpR, float &zh, float &zl, float4 *out)
+{
+    float4 ga[U], gb[U], gc[U];
+    float z[U], Ph[U], Pl[U], FH[U], FL[U];
+#pragma unroll
+    for (int v = 0; v < U; ++v) {
+        ga[v] = sp[v].ga[rg];
+        gb[v] = sp[v].gb[rg];
+        gc[v] = sp[v].gc[rg];
+    }
+#pragma unroll
+    for (int v = 0; v < U; ++v) z[v] = fmaxf(yrow[v], 0.0f) * gc[v].z;
+#pragma unroll
+    for (int v = 0; v < U; ++v) {                // two-sum into (zh, zl), species order
+        const float s = __fadd_rn(zh, z[v]), bb = __fsub_rn(s, zh);
+        zl = __fadd_rn(zl, __fadd_rn(__fsub_rn(zh, __fsub_rn(s, bb)), __fsub_rn(z[v], bb)));
+        zh = s;
+    }
+#pragma unroll
+    for (int v = 0; v < U; ++v) {
+        // z = m 2^ex, m in [0.5, 1) (subnormal z scaled by 2^24 first)
+        const bool sub = z[v] < 1.17549435e-38f;
+        const int bits = __float_as_int(sub ? z[v] * 16777216.0f : z[v]);
+        const int ex = ((bits >> 23) & 0xFF) - 126 - (sub ? 24 : 0);
+        const float lm = log2_mant(__int_as_float((bits & 0x007FFFFF) | 0x3F000000));
+        const float lmh = grid8(lm);
+        Ph[v] = z[v] > 0.0f ? __fadd_rn((float)ex, lmh) : kAbsentLog2;
+        Pl[v] = z[v] > 0.0f ? __fsub_rn(lm, lmh) : 0.0f;
+    }
+#pragma unroll
+    for (int v = 0; v < U; ++v) {
+        FH[v] = __fadd_rn(ga[v].x, gpH);
+        FL[v] = __fadd_rn(ga[v].y, gpR);
+    }
+#pragma unroll
+    for (int v = 0; v < U; ++v) acc_prod(FH[v], FL[v], ga[v].z, ga[v].w, c.d1h, d1l);
+#pragma unroll
+    for (int v = 0; v < U; ++v) acc_prod(FH[v], FL[v], gb[v].x, gb[v].y, c.d2h, c.d2l);
+#pragma unroll
+    for (int v = 0; v < U; ++v)
+        FL[v] = __fadd_rn(FL[v], u * fmaf(u, fmaf(u, fmaf(u, gc[v].y, gc[v].x), gb[v].w), gb[v].z));
+#pragma unroll
+    for (int v = 0; v < U; ++v) out[v * 32] = make_float4(Ph[v], Pl[v], FH[v], FL[v]);
 }
 
 constexpr int kMaxWarps = 8;
@@ -741,31 +801,14 @@ k_source_f32t(F32TView v, int64_t n, const float *__restrict__ T, const float *_
         if (lane < kn)
             for (int cc = 0; cc < ncl; ++cc) s_om[cc * kOmStride + lane] = Y[(ib + cc) * ldY + k0 + lane];
         __syncwarp();
-#pragma unroll 2
-        for (int kk = 0; kk < kn; ++kk) {
-            const int k = k0 + kk;
-            const float4 ga = s_spec[k].ga[rg], gb = s_spec[k].gb[rg], gc = s_spec[k].gc[rg];
-            const float z = fmaxf(s_om[me * kOmStride + kk], 0.0f) * gc.z;
-            {   // two-sum into (zh, zl)
-                const float s = __fadd_rn(zh, z), bb = __fsub_rn(s, zh);
-                zl = __fadd_rn(zl, __fadd_rn(__fsub_rn(zh, __fsub_rn(s, bb)), __fsub_rn(z, bb)));
-                zh = s;
-            }
-            // z = m 2^ex, m in [0.5, 1) (subnormal z scaled by 2^24 first)
-            const bool sub = z < 1.17549435e-38f;
-            const int bits = __float_as_int(sub ? z * 16777216.0f : z);
-            const int ex = ((bits >> 23) & 0xFF) - 126 - (sub ? 24 : 0);
-            const float lm = log2f(__int_as_float((bits & 0x007FFFFF) | 0x3F000000));
-            const float lmh = grid8(lm);
-            const float Ph = z > 0.0f ? __fadd_rn((float)ex, lmh) : kAbsentLog2;
-            const float Pl = z > 0.0f ? __fsub_rn(lm, lmh) : 0.0f;
-            // F_k = G_k(T) + log2(p_ref/RT)
-            float FH = __fadd_rn(ga.x, gpH), FL = __fadd_rn(ga.y, gpR);
-            acc_prod(FH, FL, ga.z, ga.w, c.d1h, d1l);
-            acc_prod(FH, FL, gb.x, gb.y, c.d2h, c.d2l);
-            FL = __fadd_rn(FL, u * fmaf(u, fmaf(u, fmaf(u, gc.y, gc.x), gb.w), gb.z));
-            s_pf[k * 32 + lane] = make_float4(Ph, Pl, FH, FL);
-        }
+        const float *yrow = s_om + me * kOmStride;
+        int kk = 0;
+        for (; kk + kQuad <= kn; kk += kQuad)
+            species_block<kQuad>(s_spec + k0 + kk, yrow + kk, rg, c, d1l, u, gpH, gpR, zh, zl,
+                                 s_pf + (k0 + kk) * 32 + lane);
+        for (; kk < kn; ++kk)
+            species_block<1>(s_spec + k0 + kk, yrow + kk, rg, c, d1l, u, gpH, gpR, zh, zl,
+                             s_pf + (k0 + kk) * 32 + lane);
     }
     // log2 C_k = log2 z_k + log2(c_tot / sum z): add the cell's shift to every P_k
     float cnH = c.ctH, cnR = c.ctR;
@@ -806,8 +849,8 @@ k_source_f32t(F32TView v, int64_t n, const float *__restrict__ T, const float *_
         for (int r = 0; r < kChunk; r += kQuad) {
             const RxnT *R = rc + r;
             switch (R->meta & 7u) {
-            case kGSmall: quad0<2, 2, 4>(R, pf, omc, c); break;
-            case kGBig: quad0<3, 3, 6>(R, pf, omc, c); break;
+            case kGSmall: quad<2, 2, 4, 0>(R, pf, omc, s_tb, s_fall, c); break;
+            case kGBig: quad<3, 3, 6, 0>(R, pf, omc, s_tb, s_fall, c); break;
             case kGThird: quad<3, 3, 6, 1>(R, pf, omc, s_tb, s_fall, c); break;
             case kGLind: quad<3, 3, 6, 2>(R, pf, omc, s_tb, s_fall, c); break;
             default: quad<3, 3, 6, 3>(R, pf, omc, s_tb, s_fall, c); break;

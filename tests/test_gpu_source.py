@@ -230,8 +230,9 @@ def test_bf16_species_padding(dev, size, extra):
 
 @pytest.mark.parametrize("n", [3 * 4864 + 17, 70001])
 def test_fp32_intermediate_cells_per_warp(dev, n):
-    """Batch sizes for which the FP32 kernel gives each warp between 2 and 31 cells, with a
-    ragged last warp: sampled cells and the tail against the oracle."""
+    """Batch sizes for which the FP32 kernel's blocks are neither one warp nor the widest
+    (here 4 and 6 warps of 32 cells, with a ragged last warp): sampled cells and the tail
+    against the oracle."""
     m, h, om = loaded("gri_53_325")
     T, P, Y = states(m, "gri_53_325", n, seed=31)
     T, P, Y = (as_prec(x, chem.FP32) for x in (T, P, Y))
@@ -239,3 +240,26 @@ def test_fp32_intermediate_cells_per_warp(dev, n):
     idx = np.concatenate([synth.subset_indices(n, 512), np.arange(n - 40, n)])
     ref = O.source_term(om, T[idx], P[idx], Y[idx])
     assert cell_err(w[idx], ref).max() <= TOL[chem.FP32]
+
+
+def test_fp32_extreme_states(dev):
+    """FP32 at the edges of its arithmetic: T at the NASA-7 range switch (t_mid and the
+    floats either side of it) and at 300 K and 3500 K, pressures from 0.01 to 100 atm, and
+    mass fractions down to the FP32 subnormal range (1e-40) next to ordinary ones."""
+    m, h, om = loaded("gri_53_325")
+    ns = m.n_species
+    T0, P0, Y0 = states(m, "gri_53_325", 96, seed=77)
+    tm = np.float32(m.t_mid)
+    Ts = np.array([300.0, 3500.0, tm, np.nextafter(tm, np.float32(0)),
+                   np.nextafter(tm, np.float32(1e9))], np.float64)
+    T = Ts[np.arange(96) % len(Ts)]
+    P = np.where(np.arange(96) % 2 == 0, 0.01, 100.0) * 1.01325e6
+    Y = Y0.copy()
+    Y[1::3, 5] = 1e-40                 # subnormal in FP32
+    Y[2::3, 7] = 1e-30
+    Y[::5, 9] = 3e-39
+    T, P, Y = (as_prec(x, chem.FP32) for x in (T, P, Y))
+    ref = O.source_term(om, T, P, Y)
+    w, _ = run(h, T, P, Y, chem.FP32, dev)
+    assert np.all(np.isfinite(w))
+    assert cell_err(w, ref).max() <= TOL[chem.FP32]
