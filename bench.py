@@ -624,10 +624,11 @@ def extras_heavy(line, dev, stream, n=1 << 18):
 
 
 def extras_kc_ann(line, dev, stream, n=100_000):
-    """Approximate-ANN ln K_c (Sec. 2.3, the paper's Fig. 10 comparison at N_C = 1e5): the FP32
-    source term with the exact ln K_c against the same kernel with ln K_c from LF (1 x 8) and
-    HF (3 x 32) ELU networks trained on a temperature sweep of the exact ln K_c (1e6 samples);
-    errors against the FP64 path on the same inputs."""
+    """Approximate-ANN ln K_c (Sec. 2.3, the paper's Fig. 10 comparison at N_C = 1e5): the
+    warp-per-cell FP32 kernel with the exact ln K_c against the same kernel with ln K_c from
+    LF (1 x 8) and HF (3 x 32) ELU networks trained on a temperature sweep of the exact ln K_c
+    (1e6 samples), beside the FP32 source term's own (thread-per-cell) kernel; errors against
+    the FP64 path on the same inputs."""
     import torch
     from paper_2008_08483_gb300 import chem, kc_ann, synth
     res = {"cells": n}
@@ -637,13 +638,18 @@ def extras_kc_ann(line, dev, stream, n=100_000):
         T, P, Y = synth.make_states(mech, n, seed=STATE_SEED)
         din = [torch.as_tensor(a, dtype=torch.float32, device=dev) for a in (T, P, Y)]
         o = torch.empty((n, mech.n_species), dtype=torch.float32, device=dev)
-        ms_exact = time_device(lambda: chem.source_term(h, *din, chem.FP32, out=o, stream=stream),
+        # the reference of the speed-up: the network's own kernel with the exact Gibbs layer
+        ms_exact = time_device(lambda: chem.source_term_kc_ann(h, None, *din, out=o, stream=stream),
                                20, 3, stream, 1, dev)
+        ms_fp32 = time_device(lambda: chem.source_term(h, *din, chem.FP32, out=o, stream=stream),
+                              20, 3, stream, 1, dev)
         ref = chem.source_term(h, *[t.double() for t in din], chem.FP64)
         scale = ref.abs().max(1).values
         Ts = torch.linspace(400.0, 3000.0, 1001, dtype=torch.float64, device=dev)
         exact_kc = chem.log_kc(h, Ts).cpu().numpy()
-        r = {"fp32_exact": {"ms": ms_exact, "cells_per_s": n / (ms_exact * 1e-3)}}
+        r = {"fp32_exact": {"ms": ms_exact, "cells_per_s": n / (ms_exact * 1e-3),
+                            "kernel": "warp per cell, exact Gibbs layer"},
+             "fp32_source_term": {"ms": ms_fp32, "cells_per_s": n / (ms_fp32 * 1e-3)}}
         for name, (nl, nh) in (("LF_1x8", (1, 8)), ("HF_3x32", (3, 32))):
             params, hist = kc_ann.train_kc_ann(h, nl, nh, "elu", steps=2000)
             ann = chem.KcAnn(h, params)

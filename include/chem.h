@@ -229,10 +229,14 @@ chem_status chem_kc_ann_load(const chem_mech *mech, const chem_kc_ann_desc *desc
 chem_status chem_kc_ann_free(chem_kc_ann *ann);
 
 /*
- * chem_source_term's CHEM_FP32 path (float arrays, same layouts) with ln K_c of every
+ * The FP32 source term (float arrays, chem_source_term's layouts) with ln K_c of every
  * reversible reaction taken from the network instead of the Gibbs layer: an approximation
- * (its error is the network's), evaluated once per cell before the reaction loop.
- * Errors: as chem_source_term, plus CHEM_EINVAL for a network of another mechanism.
+ * (its error is the network's), evaluated once per cell before the reaction loop.  It runs
+ * the warp-per-cell FP32 kernel (one warp per cell, lanes over reactions).  ann == NULL
+ * runs that same kernel with the exact Gibbs layer: the reference against which the
+ * network's speed-up is measured (chem_source_term's CHEM_FP32 path may use another
+ * kernel).  Errors: as chem_source_term, plus CHEM_EINVAL for a network of another
+ * mechanism.
  */
 chem_status chem_source_term_kc_ann(const chem_mech *mech, const chem_kc_ann *ann,
                                     int64_t n_cells, const float *T, const float *P,

@@ -560,8 +560,9 @@ class KcAnn:
             pass
 
 
-def source_term_kc_ann(mech: Mechanism, ann: KcAnn, T, P, Y, out=None, stream=None):
-    """omega [n, ns] (float32) on the FP32 path with ln K_c from the network."""
+def source_term_kc_ann(mech: Mechanism, ann, T, P, Y, out=None, stream=None):
+    """omega [n, ns] (float32) from the warp-per-cell FP32 kernel with ln K_c from the
+    network; ann=None runs the same kernel with the exact Gibbs layer."""
     import torch
     for name, t in (("T", T), ("P", P), ("Y", Y)):
         if not t.is_cuda or t.dtype != torch.float32:
@@ -569,7 +570,8 @@ def source_term_kc_ann(mech: Mechanism, ann: KcAnn, T, P, Y, out=None, stream=No
     n = T.shape[0]
     if out is None:
         out = torch.empty((n, mech.n_species), dtype=torch.float32, device=T.device)
-    _check(lib().chem_source_term_kc_ann(mech.handle, ann.handle, n, T.data_ptr(), P.data_ptr(),
+    _check(lib().chem_source_term_kc_ann(mech.handle, ann.handle if ann is not None else None, n,
+                                         T.data_ptr(), P.data_ptr(),
                                          Y.data_ptr(), Y.stride(0), out.data_ptr(), out.stride(0),
                                          _stream_ptr(stream)))
     return out

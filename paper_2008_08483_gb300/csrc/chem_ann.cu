@@ -138,13 +138,14 @@ extern "C" chem_status chem_source_term_kc_ann(const chem_mech *m, const chem_kc
                                                void *stream)
 {
     clear_error();
-    if (!m || !a) return set_error(CHEM_EINVAL, "NULL mechanism or network");
-    if (a->mech != m) return set_error(CHEM_EINVAL, "the network was built for another mechanism");
+    if (!m) return set_error(CHEM_EINVAL, "NULL mechanism");
+    if (a && a->mech != m) return set_error(CHEM_EINVAL, "the network was built for another mechanism");
     if (n < 0) return set_error(CHEM_EINVAL, "n_cells < 0");
     if (ldY < m->ns || ldO < m->ns) return set_error(CHEM_EINVAL, "ldY / ldO below n_species");
     if (n == 0) return CHEM_OK;
     if (!T || !P || !Y || !omega) return set_error(CHEM_EINVAL, "NULL array with n_cells > 0");
     chem_status st = check_dev(m);
     if (st != CHEM_OK) return st;
+    if (!a) return launch_source_fp32_warp(m, n, T, P, Y, ldY, omega, ldO, (cudaStream_t)stream);
     return launch_source_fp32_ann(m, a->view, n, T, P, Y, ldY, omega, ldO, (cudaStream_t)stream);
 }

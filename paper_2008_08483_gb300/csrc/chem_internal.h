@@ -277,6 +277,11 @@ chem_status launch_source_fp64(const chem_mech *m, int64_t n, const double *T, c
 chem_status launch_source_fp32(const chem_mech *m, int64_t n, const float *T, const float *P,
                                const float *Y, int64_t ldY, float *om, int64_t ldO,
                                cudaStream_t s);
+// the warp-per-cell FP32 kernel with the exact Gibbs layer, whatever the mechanism's size
+// (the structure the network variant shares)
+chem_status launch_source_fp32_warp(const chem_mech *m, int64_t n, const float *T, const float *P,
+                                    const float *Y, int64_t ldY, float *om, int64_t ldO,
+                                    cudaStream_t s);
 chem_status launch_source_fp32_ann(const chem_mech *m, const KcAnnView &av, int64_t n,
                                    const float *T, const float *P, const float *Y, int64_t ldY,
                                    float *om, int64_t ldO, cudaStream_t s);

@@ -577,6 +577,15 @@ chem_status launch_source_fp32(const chem_mech *m, int64_t n, const float *T, co
     return launch_f32<false>(m, none, n, T, P, Y, ldY, om, ldO, s, "fp32");
 }
 
+chem_status launch_source_fp32_warp(const chem_mech *m, int64_t n, const float *T, const float *P,
+                                    const float *Y, int64_t ldY, float *om, int64_t ldO,
+                                    cudaStream_t s)
+{
+    KcAnnView none;
+    memset(&none, 0, sizeof none);
+    return launch_f32<false>(m, none, n, T, P, Y, ldY, om, ldO, s, "fp32 warp per cell");
+}
+
 chem_status launch_source_fp32_ann(const chem_mech *m, const KcAnnView &av, int64_t n,
                                    const float *T, const float *P, const float *Y, int64_t ldY,
                                    float *om, int64_t ldO, cudaStream_t s)

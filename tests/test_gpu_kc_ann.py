@@ -95,3 +95,20 @@ def test_network_load_validation(dev, mech9):
     Y = torch.full((4, 9), 1.0 / 9, device=dev, dtype=torch.float32)
     with pytest.raises(chem.ChemError):
         chem.source_term_kc_ann(other, ann, T, T * 1000, Y)
+
+
+def test_exact_reference_of_the_network_kernel(dev, mech53):
+    """No network: the network variant's kernel with the exact Gibbs layer (the reference of
+    the speed-up), against the oracle at the FP32 bar and against the FP32 source term."""
+    h = chem.Mechanism(mech53)
+    om = O.OracleMechanism(mech53)
+    n = 3 * 64 + 11
+    T, P, Y = synth.make_states(mech53, n, seed=43)
+    T32, P32, Y32 = (a.astype(np.float32) for a in (T, P, Y))
+    t = [torch.as_tensor(a, device=dev) for a in (T32, P32, Y32)]
+    w = chem.source_term_kc_ann(h, None, *t).cpu().numpy().astype(float)
+    ref = O.source_term(om, *(a.astype(float) for a in (T32, P32, Y32)))
+    err = np.abs(w - ref).max(1) / np.abs(ref).max(1)
+    assert err.max() <= 1e-5, err.max()
+    w32 = chem.source_term(h, *t, chem.FP32).cpu().numpy().astype(float)
+    assert (np.abs(w - w32).max(1) / np.abs(ref).max(1)).max() <= 2e-5
