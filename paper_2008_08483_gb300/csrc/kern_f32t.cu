@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "chem_internal.h"
+#include "chem_quads.h"
 
 namespace chem {
 
@@ -181,83 +182,39 @@ chem_status f32t_build_tables(chem_mech *m, const chem_mech_desc *d)
                 }
             }
     }
-    // records grouped by type, in quads: greedily packed so that a quad's net species are
-    // pairwise distinct (meta bit 3: one omega round trip), the rest in order; the last quad
-    // of a type is padded with zero-rate records of its type
-    auto net_mask = [&](int j) {
-        std::vector<bool> mk(ns, false);
-        for (int k = 0; k < ns; ++k) mk[k] = d->nu_r[(size_t)j * ns + k] != d->nu_f[(size_t)j * ns + k];
-        return mk;
-    };
-    for (int g = 0; g < kGroups; ++g) {
-        std::vector<std::vector<int>> quads;
-        std::vector<std::vector<bool>> used;
-        for (int j = 0; j < nr; ++j) {
-            if (type_of[j] != g) continue;
-            const std::vector<bool> mk = net_mask(j);
-            size_t qi = 0;
-            for (; qi < quads.size(); ++qi) {
-                if (quads[qi].size() >= (size_t)kQuad) continue;
-                bool clash = false;
-                for (int k = 0; k < ns && !clash; ++k) clash = mk[k] && used[qi][k];
-                if (!clash) break;
-            }
-            if (qi == quads.size()) {
-                quads.emplace_back();
-                used.emplace_back(ns, false);
-            }
-            quads[qi].push_back(j);
-            for (int k = 0; k < ns; ++k) used[qi][k] = used[qi][k] || mk[k];
-        }
-        std::vector<int> order, rest;
-        std::vector<bool> disjoint;
-        for (auto &q : quads) {
-            if (q.size() == (size_t)kQuad) {
-                order.insert(order.end(), q.begin(), q.end());
-                disjoint.push_back(true);
+    // records in quads of one type, net species pairwise distinct where the greedy packing
+    // allows (chem_quads.h; meta bit 3: one omega round trip), zero-rate padding records
+    std::vector<std::vector<int>> net(nr);
+    for (int j = 0; j < nr; ++j)
+        for (int k = 0; k < ns; ++k)
+            if (d->nu_r[(size_t)j * ns + k] != d->nu_f[(size_t)j * ns + k]) net[j].push_back(k);
+    const QuadPlan plan = plan_quads(kGroups, type_of, net, kQuad);
+    for (size_t qn = 0; qn < plan.type.size(); ++qn) {
+        const size_t first = rx.size();
+        const int *js = &plan.slot[qn * kQuad];
+        size_t nit = 0;
+        for (int u = 0; u < kQuad; ++u) {
+            if (js[u] >= 0) {
+                rx.push_back(one[js[u]]);
+                nit = std::max(nit, lists[js[u]].size());
             } else {
-                rest.insert(rest.end(), q.begin(), q.end());
+                RxnT pad = rx.back();                  // same type, zero rate
+                pad.kf = make_float4(kOff, 0.0f, 0.0f, 0.0f);
+                pad.b = 0.0f;
+                clear_entries(pad, ns);
+                rx.push_back(pad);
             }
         }
-        for (size_t a = 0; a < rest.size(); a += kQuad) {
-            bool dis = true;
-            std::vector<bool> u(ns, false);
-            for (size_t b = a; b < a + kQuad && b < rest.size(); ++b) {
-                const std::vector<bool> mk = net_mask(rest[b]);
-                for (int k = 0; k < ns; ++k) {
-                    dis = dis && !(mk[k] && u[k]);
-                    u[k] = u[k] || mk[k];
-                }
+        // the quad's efficiency lists as [entry][reaction], padded with zero entries
+        if (tb.size() + nit * kQuad > 65535 || nit > 65535) return CHEM_OK;
+        const size_t base = tb.size();
+        for (size_t it = 0; it < nit; ++it)
+            for (int u = 0; u < kQuad; ++u) {
+                const bool real = js[u] >= 0 && it < lists[js[u]].size();
+                tb.push_back(real ? lists[js[u]][it] : make_int2(ns * kPfRow, 0));
             }
-            order.insert(order.end(), rest.begin() + a, rest.begin() + std::min(rest.size(), a + kQuad));
-            disjoint.push_back(dis);
-        }
-        for (size_t qn = 0; qn < disjoint.size(); ++qn) {
-            const size_t first = rx.size();
-            size_t nit = 0;
-            for (size_t b = qn * kQuad; b < (qn + 1) * kQuad; ++b) {
-                if (b < order.size()) {
-                    rx.push_back(one[order[b]]);
-                    nit = std::max(nit, lists[order[b]].size());
-                } else {
-                    RxnT pad = rx.back();
-                    pad.kf = make_float4(kOff, 0.0f, 0.0f, 0.0f);
-                    pad.b = 0.0f;
-                    clear_entries(pad, ns);
-                    rx.push_back(pad);
-                }
-            }
-            // the quad's efficiency lists as [entry][reaction], padded with zero entries
-            if (tb.size() + nit * kQuad > 65535 || nit > 65535) return CHEM_OK;
-            const size_t base = tb.size();
-            for (size_t it = 0; it < nit; ++it)
-                for (size_t b = qn * kQuad; b < (qn + 1) * kQuad; ++b) {
-                    const bool real = b < order.size() && it < lists[order[b]].size();
-                    tb.push_back(real ? lists[order[b]][it] : make_int2(ns * kPfRow, 0));
-                }
-            rx[first].tb = (uint32_t)base | ((uint32_t)nit << 16);
-            if (disjoint[qn]) rx[first].meta |= 8u;
-        }
+        rx[first].tb = (uint32_t)base | ((uint32_t)nit << 16);
+        if (plan.disjoint[qn]) rx[first].meta |= 8u;
     }
     while (rx.size() % kChunk) {
         RxnT pad;
