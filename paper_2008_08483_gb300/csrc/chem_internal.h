@@ -143,7 +143,7 @@ struct MechViewF32 {
 };
 
 // Tables of the thread-per-cell FP32 kernel (kern_f32t.cu).  Exponents are kept as a head H
-// on the grid of multiples of 2^-8 (sums of heads are exact in FP32) and a small remainder L.
+// on the grid of multiples of 2^-12 (sums of heads are exact in FP32) and a small remainder L.
 // Temperature terms are centred on T0 = 1000 K: d1 = log2 T - log2 T0, d2 = 1/T - 1/T0.
 // A reaction record of the kernel (128 bytes).  Entries are (byte offset of the species' row
 // in the warp's shared tables, coefficient as float bits) pairs, in the order

@@ -11,7 +11,7 @@
 //   q_net = 2^x_f - 2^x_r,   omega_k += (nu''_kj - nu'_kj) q_net      (Eqs. 2-4, 7)
 // where fac is log2 of the third-body concentration or of the falloff factor (Sec. 2.4).
 //
-// Precision: every exponent is a pair (H, L), H a multiple of 2^-8 and L small.  Heads of
+// Precision: every exponent is a pair (H, L), H a multiple of 2^-12 and L small.  Heads of
 // the per-species terms and of the products of a reaction's temperature coefficients with
 // the cell's centred temperature features are put on that grid, so the sums of heads with
 // small integer stoichiometric coefficients are exact in FP32; only L carries rounding, at
@@ -22,8 +22,9 @@
 //
 // Layout: one block of W warps per SM-sized share of the batch.  The block stages the species
 // table, the third-body lists and the falloff parameters once, and the reaction records in
-// double-buffered chunks of 16 (loaded one chunk ahead); each warp owns its P/F rows and its
-// omega tile.  Reactions are grouped by kind and shape (at most two or three species per
+// double-buffered chunks of 16 (loaded one chunk ahead); each warp owns its P/F rows (12
+// bytes per species and cell: the heads in FP32, the remainders, below 2^-12, in FP16) and
+// its omega tile.  Reactions are grouped by kind and shape (at most two or three species per
 // side) and taken four at a time with fixed-shape code, so that their exponent chains
 // overlap.
 #include <math.h>
@@ -32,6 +33,8 @@
 
 #include <algorithm>
 #include <vector>
+
+#include <cuda_fp16.h>
 
 #include "chem_internal.h"
 #include "chem_quads.h"
@@ -42,18 +45,22 @@ namespace {
 
 constexpr int kTMaxSpecies = 64;
 constexpr double kT0 = 1000.0;               // centre of the temperature features (K)
-constexpr float kGridAdd = 49152.0f;         // 1.5 * 2^15: (x + it) - it rounds x to 2^-8
-constexpr double kGridLimit = 4096.0;        // |head| of a table value (exact sums to 2^15)
+constexpr float kGridAdd = 3072.0f;          // 1.5 * 2^11: (x + it) - it rounds x to 2^-12
+                                             // for |x| < 2^10
+constexpr double kGridLimit = 1024.0;        // |head| of a table value (exact sums to 2^11)
 constexpr float kAbsentLog2 = -1000.0f;      // log2 C of an absent species (2^x flushes to 0)
 constexpr float kOff = -2000.0f;             // exponent bias of padding and irreversible rates
 constexpr int kChunk = 16;                   // reaction records per staged chunk
 constexpr int kOmStride = 33;                // omega tile row (odd: conflict-free both ways)
-constexpr int kPfRow = 32 * 16;              // bytes of one species row of P/F (32 lanes)
+// one species row of the P/F table: 32 lanes of (P_h, F_h) as float2, then 32 lanes of
+// (P_l, F_l) as half2 (remainders below 2^-12: FP16 keeps them to ~6e-8)
+constexpr int kPfHead = 32 * 8;
+constexpr int kPfRow = kPfHead + 32 * 4;
 constexpr int kOmRow = kOmStride * 4;        // bytes of one omega tile row
 // group types, in processing order
 enum { kGSmall = 0, kGBig = 1, kGThird = 2, kGLind = 3, kGTroe = 4, kGroups = 5 };
 
-inline double grid_head(double x) { return rint(x * 256.0) / 256.0; }
+inline double grid_head(double x) { return rint(x * 4096.0) / 4096.0; }
 
 // (hi, lo) float pair of a double
 inline void dsplit2(double x, float &h, float &l)
@@ -312,7 +319,16 @@ void f32t_free_tables(chem_mech *m)
 
 namespace {
 
-__device__ __forceinline__ float grid8(float x) { return __fsub_rn(__fadd_rn(x, kGridAdd), kGridAdd); }
+__device__ __forceinline__ float grid12(float x) { return __fsub_rn(__fadd_rn(x, kGridAdd), kGridAdd); }
+
+// (P_h, P_l, F_h, F_l) of the species row at byte offset off; pfh / pfl: this lane's
+// float2 / half2 columns of row 0
+__device__ __forceinline__ float4 load_pf(const char *pfh, const char *pfl, int off)
+{
+    const float2 h = *(const float2 *)(pfh + off);
+    const float2 l = __half22float2(*(const __half2 *)(pfl + off));
+    return make_float4(h.x, l.x, h.y, l.y);
+}
 
 // 2^x, flushed to zero below the normal range (MUFU exp2)
 __device__ __forceinline__ float ex2_ftz(float x)
@@ -330,12 +346,12 @@ __device__ __forceinline__ float lg2_approx(float x)
 }
 
 // (H, L) += c d for a double-float coefficient c and a double-float cell feature d: the
-// rounded product goes to the 2^-8 grid in H, its remainder and rounding error to L.
+// rounded product goes to the 2^-12 grid in H, its remainder and rounding error to L.
 __device__ __forceinline__ void acc_prod(float &H, float &L, float ch, float cl, float dh, float dl)
 {
     const float p = __fmul_rn(ch, dh);
     const float e = fmaf(ch, dl, fmaf(cl, dh, fmaf(ch, dh, -p)));
-    const float ph = grid8(p);
+    const float ph = grid12(p);
     H = __fadd_rn(H, ph);
     L = __fadd_rn(L, __fadd_rn(__fsub_rn(p, ph), e));
 }
@@ -398,7 +414,7 @@ __device__ __forceinline__ dflt df_log2f(float x, dflt log2e)
 // Split a double-float onto the grid: head exact in float, remainder rounded.
 __device__ __forceinline__ void grid_split(dflt x, float &h, float &r)
 {
-    h = grid8(x.h);
+    h = grid12(x.h);
     r = __fadd_rn(__fsub_rn(x.h, h), x.l);
 }
 
@@ -464,8 +480,8 @@ __device__ __forceinline__ void scatter_quad(const RxnT *R, char *om, const floa
 // kQuad reactions of one group (KIND 0 elementary, 1 third-body, 2 Lindemann, 3 Troe),
 // written step by step across the four so that consecutive instructions are independent
 template <int NF, int NR, int NN, int KIND>
-__device__ __forceinline__ void quad(const RxnT *R, const char *pf, char *om, const int2 *tb,
-                                     const FallT *fall, const CellF &c)
+__device__ __forceinline__ void quad(const RxnT *R, const char *pfh, const char *pfl, char *om,
+                                     const int2 *tb, const FallT *fall, const CellF &c)
 {
     constexpr int U = kQuad;
     float4 kf[U];
@@ -516,7 +532,9 @@ __device__ __forceinline__ void quad(const RxnT *R, const char *pf, char *om, co
 #pragma unroll
             for (int u = 0; u < U; ++u) en[u] = te[it * U + u];
 #pragma unroll
-            for (int u = 0; u < U; ++u) pp[u] = *(const float2 *)(pf + en[u].x);
+            for (int u = 0; u < U; ++u)
+                pp[u] = make_float2(((const float2 *)(pfh + en[u].x))->x,
+                                    __low2float(*(const __half2 *)(pfl + en[u].x)));
 #pragma unroll
             for (int u = 0; u < U; ++u)
                 s[u] = fmaf(__int_as_float(en[u].y),
@@ -585,7 +603,7 @@ __device__ __forceinline__ void quad(const RxnT *R, const char *pf, char *om, co
         for (int u = 0; u < U; ++u) {
             int off;
             entry(R[u], rxnt_react(t), off, nu[u]);
-            P[u] = *(const float4 *)(pf + off);
+            P[u] = load_pf(pfh, pfl, off);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -603,7 +621,7 @@ __device__ __forceinline__ void quad(const RxnT *R, const char *pf, char *om, co
         for (int u = 0; u < U; ++u) {
             int off;
             entry(R[u], rxnt_prod(t), off, nu[u]);
-            P[u] = *(const float4 *)(pf + off);
+            P[u] = load_pf(pfh, pfl, off);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -649,7 +667,8 @@ __device__ __forceinline__ float log2_mant(float m)
 template <int U>
 __device__ __forceinline__ void species_block(const SpecT *sp, const float *yrow, int rg,
                                               const CellF &c, float d1l, float u, float gpH,
-                                              float gpR, float &zh, float &zl, float4 *out)
+                                              float gpR, float &zh, float &zl, char *out_h,
+                                              char *out_l)
 {
     float4 ga[U], gb[U], gc[U];
     float z[U], Ph[U], Pl[U], FH[U], FL[U];
@@ -674,7 +693,7 @@ __device__ __forceinline__ void species_block(const SpecT *sp, const float *yrow
         const int bits = __float_as_int(sub ? z[v] * 16777216.0f : z[v]);
         const int ex = ((bits >> 23) & 0xFF) - 126 - (sub ? 24 : 0);
         const float lm = log2_mant(__int_as_float((bits & 0x007FFFFF) | 0x3F000000));
-        const float lmh = grid8(lm);
+        const float lmh = grid12(lm);
         Ph[v] = z[v] > 0.0f ? __fadd_rn((float)ex, lmh) : kAbsentLog2;
         Pl[v] = z[v] > 0.0f ? __fsub_rn(lm, lmh) : 0.0f;
     }
@@ -691,7 +710,12 @@ __device__ __forceinline__ void species_block(const SpecT *sp, const float *yrow
     for (int v = 0; v < U; ++v)
         FL[v] = __fadd_rn(FL[v], u * fmaf(u, fmaf(u, fmaf(u, gc[v].y, gc[v].x), gb[v].w), gb[v].z));
 #pragma unroll
-    for (int v = 0; v < U; ++v) out[v * 32] = make_float4(Ph[v], Pl[v], FH[v], FL[v]);
+    for (int v = 0; v < U; ++v) {
+        // F's remainder back under 2^-12 (its polynomial part is not small), for FP16
+        const float fh = grid12(FL[v]);
+        *(float2 *)(out_h + v * kPfRow) = make_float2(Ph[v], __fadd_rn(FH[v], fh));
+        *(__half2 *)(out_l + v * kPfRow) = __floats2half2_rn(Pl[v], __fsub_rn(FL[v], fh));
+    }
 }
 
 constexpr int kMaxWarps = 8;
@@ -713,7 +737,8 @@ k_source_f32t(F32TView v, int64_t n, const float *__restrict__ T, const float *_
     RxnT *s_rec = (RxnT *)(s_raw + off);
     off += 2 * kChunk * sizeof(RxnT);
     unsigned char *wbase = s_raw + off + (size_t)w * (warp_pf_bytes(ns) + warp_om_bytes(ns));
-    float4 *s_pf = (float4 *)wbase;
+    char *pfh_w = (char *)wbase + lane * 8;                   // this lane's P/F columns
+    char *pfl_w = (char *)wbase + kPfHead + lane * 4;
     float *s_om = (float *)(wbase + warp_pf_bytes(ns));
     copy16(s_spec, v.spec, sizeof(SpecT) * ns);
     for (int t = threadIdx.x; t < v.n_tb; t += blockDim.x) s_tb[t] = __ldg(v.tb + t);
@@ -762,10 +787,10 @@ k_source_f32t(F32TView v, int64_t n, const float *__restrict__ T, const float *_
         int kk = 0;
         for (; kk + kQuad <= kn; kk += kQuad)
             species_block<kQuad>(s_spec + k0 + kk, yrow + kk, rg, c, d1l, u, gpH, gpR, zh, zl,
-                                 s_pf + (k0 + kk) * 32 + lane);
+                                 pfh_w + (k0 + kk) * kPfRow, pfl_w + (k0 + kk) * kPfRow);
         for (; kk < kn; ++kk)
             species_block<1>(s_spec + k0 + kk, yrow + kk, rg, c, d1l, u, gpH, gpR, zh, zl,
-                             s_pf + (k0 + kk) * 32 + lane);
+                             pfh_w + (k0 + kk) * kPfRow, pfl_w + (k0 + kk) * kPfRow);
     }
     // log2 C_k = log2 z_k + log2(c_tot / sum z): add the cell's shift to every P_k
     float cnH = c.ctH, cnR = c.ctR;
@@ -778,16 +803,19 @@ k_source_f32t(F32TView v, int64_t n, const float *__restrict__ T, const float *_
     }
     __syncwarp();
     for (int k = 0; k < ns; ++k) {
-        float2 *p = (float2 *)&s_pf[k * 32 + lane];
-        const float2 t = *p;
-        *p = make_float2(__fadd_rn(t.x, cnH), __fadd_rn(t.y, cnR));
+        float *ph = (float *)(pfh_w + k * kPfRow);
+        __half2 *pl = (__half2 *)(pfl_w + k * kPfRow);
+        *ph = __fadd_rn(*ph, cnH);
+        const float2 l = __half22float2(*pl);
+        *pl = __floats2half2_rn(__fadd_rn(l.x, cnR), l.y);
         s_om[k * kOmStride + lane] = 0.0f;
     }
-    s_pf[ns * 32 + lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);       // the zero row
+    *(float2 *)(pfh_w + ns * kPfRow) = make_float2(0.0f, 0.0f);       // the zero row
+    *(__half2 *)(pfl_w + ns * kPfRow) = __floats2half2_rn(0.0f, 0.0f);
     s_om[ns * kOmStride + lane] = 0.0f;
 
-    // ---- reactions: chunks of records staged one ahead, pairs of one group type
-    const char *pf = (const char *)s_pf + lane * 16;
+    // ---- reactions: chunks of records staged one ahead, quads of one group type
+    const char *pfh = pfh_w, *pfl = pfl_w;
     char *omc = (char *)s_om + lane * 4;
     const int nch = v.n_rec / kChunk;
     const float4 *src = (const float4 *)v.rxn;
@@ -806,11 +834,11 @@ k_source_f32t(F32TView v, int64_t n, const float *__restrict__ T, const float *_
         for (int r = 0; r < kChunk; r += kQuad) {
             const RxnT *R = rc + r;
             switch (R->meta & 7u) {
-            case kGSmall: quad<2, 2, 4, 0>(R, pf, omc, s_tb, s_fall, c); break;
-            case kGBig: quad<3, 3, 6, 0>(R, pf, omc, s_tb, s_fall, c); break;
-            case kGThird: quad<3, 3, 6, 1>(R, pf, omc, s_tb, s_fall, c); break;
-            case kGLind: quad<3, 3, 6, 2>(R, pf, omc, s_tb, s_fall, c); break;
-            default: quad<3, 3, 6, 3>(R, pf, omc, s_tb, s_fall, c); break;
+            case kGSmall: quad<2, 2, 4, 0>(R, pfh, pfl, omc, s_tb, s_fall, c); break;
+            case kGBig: quad<3, 3, 6, 0>(R, pfh, pfl, omc, s_tb, s_fall, c); break;
+            case kGThird: quad<3, 3, 6, 1>(R, pfh, pfl, omc, s_tb, s_fall, c); break;
+            case kGLind: quad<3, 3, 6, 2>(R, pfh, pfl, omc, s_tb, s_fall, c); break;
+            default: quad<3, 3, 6, 3>(R, pfh, pfl, omc, s_tb, s_fall, c); break;
             }
         }
         if (more) {
