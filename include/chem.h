@@ -63,7 +63,7 @@ typedef enum {
 typedef enum {
     CHEM_FP64 = 0,          /* double I/O and arithmetic (SIMT) */
     CHEM_FP32 = 1,          /* float I/O; SIMT float arithmetic, exponents assembled
-                               without rounding their large terms (exact 2^-8-grid heads
+                               without rounding their large terms (exact 2^-12-grid heads
                                plus remainders up to 64 species, double-float above) */
     CHEM_SPLIT_BF16 = 2     /* float I/O; the stoichiometric contractions on tcgen05
                                tensor cores with split 16-bit operands and FP32
