@@ -137,10 +137,13 @@ chem_status chem_mechanism_info(const chem_mech *mech, int32_t *n_species,
  * Errors: CHEM_EINVAL (NULL pointers with n_cells > 0, n_cells < 0,
  * ldY/ldO < n_species, mechanism loaded on another device), CHEM_EUNSUPPORTED
  * (precision not built for this mechanism size: CHEM_FP64 needs 2 n_species + n_reactions
- * <= 3440, CHEM_FP32 5 n_species + n_reactions <= 6752; CHEM_SPLIT_BF16 at most 53 species
- * (n_species + 11 contraction columns <= 64), at most 64 third-body / falloff reactions
- * (8 per multiplier share, at most 4 of them falloff), and tables that fit in shared
- * memory), CHEM_ECUDA (launch failure).
+ * <= 3440; CHEM_FP32 takes up to 64 species with at most three species a side and any
+ * reaction count (thread-per-cell kernel; its staged species, third-body and falloff tables
+ * must fit in shared memory), else needs 5 n_species + n_reactions <= 6752;
+ * CHEM_SPLIT_BF16 takes up to 192 species (tables resident in shared memory up to 53,
+ * streamed from L2 beyond), with the third-body / falloff reactions within the multiplier
+ * slots (8 per 16-reaction share, at most 4 of them falloff) and its shared-memory operands
+ * within 227 KB), CHEM_ECUDA (launch failure).
  * Asynchronous on `stream`.
  */
 chem_status chem_source_term(const chem_mech *mech, int64_t n_cells, const void *T,
