@@ -64,7 +64,7 @@ typedef enum {
     CHEM_FP64 = 0,          /* double I/O and arithmetic (SIMT) */
     CHEM_FP32 = 1,          /* float I/O; SIMT float arithmetic, exponents assembled
                                without rounding their large terms (exact 2^-12-grid heads
-                               plus remainders up to 64 species, double-float above) */
+                               plus remainders up to 192 species, double-float above) */
     CHEM_SPLIT_BF16 = 2     /* float I/O; the stoichiometric contractions on tcgen05
                                tensor cores with split 16-bit operands and FP32
                                accumulation in tensor memory: log2 X and the Arrhenius /
@@ -137,7 +137,7 @@ chem_status chem_mechanism_info(const chem_mech *mech, int32_t *n_species,
  * Errors: CHEM_EINVAL (NULL pointers with n_cells > 0, n_cells < 0,
  * ldY/ldO < n_species, mechanism loaded on another device), CHEM_EUNSUPPORTED
  * (precision not built for this mechanism size: CHEM_FP64 needs 2 n_species + n_reactions
- * <= 3440; CHEM_FP32 takes up to 64 species with at most three species a side and any
+ * <= 3440; CHEM_FP32 takes up to 192 species with at most three species a side and any
  * reaction count (thread-per-cell kernel; its staged species, third-body and falloff tables
  * must fit in shared memory), else needs 5 n_species + n_reactions <= 6752;
  * CHEM_SPLIT_BF16 takes up to 192 species (tables resident in shared memory up to 53,

@@ -43,7 +43,7 @@ namespace chem {
 
 namespace {
 
-constexpr int kTMaxSpecies = 64;
+constexpr int kTMaxSpecies = 192;
 constexpr double kT0 = 1000.0;               // centre of the temperature features (K)
 constexpr float kGridAdd = 3072.0f;          // 1.5 * 2^11: (x + it) - it rounds x to 2^-12
                                              // for |x| < 2^10

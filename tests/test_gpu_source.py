@@ -177,17 +177,18 @@ def test_full_size_sampled(dev, prec):
     assert cell_err(w[idx], ref).max() <= TOL[prec]
 
 
-def test_full_size_sampled_160_1000(dev):
+@pytest.mark.parametrize("prec", [chem.SPLIT_BF16, chem.FP32])
+def test_full_size_sampled_160_1000(dev, prec):
     """160 species / 1000 reactions at 2^18 cells (the large-mechanism workload's launch) on
-    the split-precision path: sampled cells and the last cell against the oracle."""
+    the split-precision and FP32 paths: sampled cells and the last cell against the oracle."""
     m, h, om = loaded("heavy_160_1000")
     n = 1 << 18
     T, P, Y = states(m, "heavy_160_1000", n, seed=1234)
-    T, P, Y = (as_prec(x, chem.SPLIT_BF16) for x in (T, P, Y))
-    w, _ = run(h, T, P, Y, chem.SPLIT_BF16, dev)
+    T, P, Y = (as_prec(x, prec) for x in (T, P, Y))
+    w, _ = run(h, T, P, Y, prec, dev)
     idx = np.concatenate([synth.subset_indices(n, 1024), [0, n - 1]])
     ref = O.source_term(om, T[idx], P[idx], Y[idx])
-    assert cell_err(w[idx], ref).max() <= TOL[chem.SPLIT_BF16]
+    assert cell_err(w[idx], ref).max() <= TOL[prec]
 
 
 def with_inert_species(m, extra):
