@@ -479,11 +479,11 @@ __device__ __forceinline__ void scatter_quad(const RxnT *R, char *om, const floa
 
 // kQuad reactions of one group (KIND 0 elementary, 1 third-body, 2 Lindemann, 3 Troe),
 // written step by step across the four so that consecutive instructions are independent
-template <int NF, int NR, int NN, int KIND>
+template <int NF, int NR, int NN, int KIND, int U = kQuad>
 __device__ __forceinline__ void quad(const RxnT *R, const char *pfh, const char *pfl, char *om,
                                      const int2 *tb, const FallT *fall, const CellF &c)
 {
-    constexpr int U = kQuad;
+    static_assert(U % kQuad == 0 && (KIND == 0 || U == kQuad), "quads of elementary reactions pair up");
     float4 kf[U];
     float b[U], rb[U], p[U], e[U], ph[U], xfH[U], xfL[U], xrH[U], xrL[U];
 #pragma unroll
@@ -637,7 +637,8 @@ __device__ __forceinline__ void quad(const RxnT *R, const char *pfh, const char 
         const float qn = ex2_ftz(xfH[u]) * ex2_ftz(xfL[u]) - ex2_ftz(xrH[u]) * ex2_ftz(xrL[u]);
         q[u] = live[u] ? qn : 0.0f;
     }
-    scatter_quad<NN>(R, om, q);
+#pragma unroll
+    for (int g = 0; g < U; g += kQuad) scatter_quad<NN>(R + g, om, q + g);
 }
 
 __device__ __forceinline__ void copy16(void *dst, const void *src, size_t bytes)
@@ -831,15 +832,26 @@ k_source_f32t(F32TView v, int64_t n, const float *__restrict__ T, const float *_
         }
         const RxnT *rc = s_rec + (ch & 1) * kChunk;
 #pragma unroll 1
-        for (int r = 0; r < kChunk; r += kQuad) {
+        for (int r = 0; r < kChunk;) {
             const RxnT *R = rc + r;
-            switch (R->meta & 7u) {
+            const uint32_t ty = R->meta & 7u;
+            // two elementary quads of one type: eight rate chains at once, two omega rounds
+            if (ty <= kGBig && r + 2 * kQuad <= kChunk && (R[kQuad].meta & 7u) == ty) {
+                if (ty == kGSmall)
+                    quad<2, 2, 4, 0, 2 * kQuad>(R, pfh, pfl, omc, s_tb, s_fall, c);
+                else
+                    quad<3, 3, 6, 0, 2 * kQuad>(R, pfh, pfl, omc, s_tb, s_fall, c);
+                r += 2 * kQuad;
+                continue;
+            }
+            switch (ty) {
             case kGSmall: quad<2, 2, 4, 0>(R, pfh, pfl, omc, s_tb, s_fall, c); break;
             case kGBig: quad<3, 3, 6, 0>(R, pfh, pfl, omc, s_tb, s_fall, c); break;
             case kGThird: quad<3, 3, 6, 1>(R, pfh, pfl, omc, s_tb, s_fall, c); break;
             case kGLind: quad<3, 3, 6, 2>(R, pfh, pfl, omc, s_tb, s_fall, c); break;
             default: quad<3, 3, 6, 3>(R, pfh, pfl, omc, s_tb, s_fall, c); break;
             }
+            r += kQuad;
         }
         if (more) {
             float4 *dst = (float4 *)(s_rec + ((ch + 1) & 1) * kChunk);
