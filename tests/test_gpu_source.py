@@ -264,3 +264,25 @@ def test_fp32_extreme_states(dev):
     w, _ = run(h, T, P, Y, chem.FP32, dev)
     assert np.all(np.isfinite(w))
     assert cell_err(w, ref).max() <= TOL[chem.FP32]
+
+
+def test_fp32_warp_kernel_fallback(dev):
+    """A mechanism the thread-per-cell FP32 kernel does not take (a reaction with four
+    reactant species: a spectator added to both sides of a three-reactant reaction, which
+    keeps element balance and the net stoichiometry) runs the warp-per-cell kernel, at the
+    same bar against the oracle."""
+    import dataclasses
+    base, _, _ = loaded("gri_53_325")
+    nf = (base.nu_f > 0).sum(1)
+    j = int(np.nonzero(nf == 3)[0][0])
+    k = int(np.nonzero((base.nu_f[j] == 0) & (base.nu_r[j] == 0))[0][0])
+    nu_f, nu_r = base.nu_f.copy(), base.nu_r.copy()
+    nu_f[j, k] += 1
+    nu_r[j, k] += 1
+    m = dataclasses.replace(base, name=base.name + "+spectator", nu_f=nu_f, nu_r=nu_r)
+    h, om = chem.Mechanism(m), O.OracleMechanism(m)
+    T, P, Y = states(m, "gri_53_325", 2 * 32 + 9, seed=5)
+    T, P, Y = (as_prec(x, chem.FP32) for x in (T, P, Y))
+    ref = O.source_term(om, T, P, Y)
+    w, _ = run(h, T, P, Y, chem.FP32, dev)
+    assert cell_err(w, ref).max() <= TOL[chem.FP32]
