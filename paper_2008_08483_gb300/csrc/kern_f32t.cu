@@ -25,8 +25,9 @@
 // double-buffered chunks of 16 (loaded one chunk ahead); each warp owns its P/F rows (12
 // bytes per species and cell: the heads in FP32, the remainders, below 2^-12, in FP16) and
 // its omega tile.  Reactions are grouped by kind and shape (at most two or three species per
-// side) and taken four at a time with fixed-shape code, so that their exponent chains
-// overlap.
+// side) into quads whose net species are distinct where possible (chem_quads.h) and taken
+// four at a time, elementary ones eight at a time (two quads), with fixed-shape code, so
+// that their exponent chains overlap and each quad updates omega in one round trip.
 #include <math.h>
 #include <stddef.h>
 #include <string.h>
