@@ -33,6 +33,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include <cuda_fp16.h>
@@ -878,13 +879,20 @@ chem_status launch_source_fp32_t(const chem_mech *m, int64_t n, const float *T, 
                                  cudaStream_t s)
 {
     static SmemOptIn opt;
+    static std::atomic<int> sm_count[64];       // per device index (chem_source_term checks < 64)
     if (n <= 0) return CHEM_OK;
     if (!m->vt.ok) return set_error(CHEM_EUNSUPPORTED, "fp32: no thread-per-cell tables");
-    int dev = 0, nsm = 0;
+    int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (nsm <= 0) nsm = 1;
+    int nsm = dev >= 0 && dev < 64 ? sm_count[dev].load(std::memory_order_relaxed) : 0;
+    if (nsm <= 0) {
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (nsm <= 0) nsm = 1;
+        if (dev >= 0 && dev < 64) sm_count[dev].store(nsm, std::memory_order_relaxed);
+    }
     const size_t fixed = block_fixed_bytes(m->vt), per_warp = warp_pf_bytes(m->ns) + warp_om_bytes(m->ns);
+    if (fixed + per_warp > kTSmemMax)          // excluded when the tables were built
+        return set_error(CHEM_EUNSUPPORTED, "fp32: thread-per-cell tables exceed shared memory");
     int wmax = (int)((kTSmemMax - fixed) / per_warp);
     wmax = wmax < 1 ? 1 : wmax > kMaxWarps ? kMaxWarps : wmax;
     // warps per block: enough blocks to cover every SM before blocks grow
