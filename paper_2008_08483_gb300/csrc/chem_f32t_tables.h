@@ -217,12 +217,18 @@ inline bool build_tables(const chem_mech_desc *d, Tables &t)
         rx.push_back(pad);
         order.push_back(-1);
     }
-    // Gibbs layer per species and T range, centred on T0 (Eq. 10 with NASA-7 a0..a6):
+    // Gibbs layer per species and T range (Eq. 10 with NASA-7 a0..a6):
     //   G(T) = -g/(RT) log2 e = a0 log2 T + log2 e (a6 - a0 + a1 T/2 + a2 T^2/6 + a3 T^3/12
     //          + a4 T^4/20 - a5 / T)
-    //        = G(T0) + a0 d1 - a5 log2 e d2 + sum_p e_p u^p,  u = T/1000 - 1
+    //        = G_c + a0 d1 - a5 log2 e d2 + sum_p e_p u^p,  u = (T - T_c) / 1000,
+    // d1 and d2 centred on T0 as for the Arrhenius terms, the powers of T re-expanded about
+    // the range's own centre T_c (0.65 and 2.25 t_mid: |u| <= 1.25 up to 3.5 t_mid), and the
+    // constant of that expansion collected in G_c
     std::vector<SpecT> sp(ns);
     const double lg2T0 = log2(kT0);
+    const double Tc[2] = {rint(0.65 * d->t_mid), rint(2.25 * d->t_mid)};
+    static const double binom[5][5] = {{1, 0, 0, 0, 0}, {1, 1, 0, 0, 0}, {1, 2, 1, 0, 0},
+                                       {1, 3, 3, 1, 0}, {1, 4, 6, 4, 1}};
     for (int k = 0; k < ns; ++k) {
         SpecT &s = sp[k];
         memset(&s, 0, sizeof s);
@@ -230,15 +236,19 @@ inline bool build_tables(const chem_mech_desc *d, Tables &t)
             const double *a = d->nasa7 + (size_t)k * 14 + (size_t)rg * 7;
             const double c[5] = {0.0, a[1] / 2.0 * 1e3, a[2] / 6.0 * 1e6, a[3] / 12.0 * 1e9,
                                  a[4] / 20.0 * 1e12};        // on tau^m, tau = T / 1000
-            const double g0 = a[0] * lg2T0 +
-                              kLog2e * (a[6] - a[0] + c[1] + c[2] + c[3] + c[4] - a[5] / kT0);
+            // sum_m c_m (tau^m - 1) with tau = tc + u: the constant sum_m c_m (tc^m - 1), and
+            // e_p = sum_{m >= p} C(m, p) c_m tc^(m - p) on u^p (binomial expansion)
+            const double tc = Tc[rg] / 1000.0;
+            double e[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, cst = 0.0;
+            for (int m = 1; m <= 4; ++m) {
+                cst += c[m] * (pow(tc, m) - 1.0);
+                for (int q = 1; q <= m; ++q) e[q] += binom[m][q] * c[m] * pow(tc, m - q);
+            }
+            const double g0 = a[0] * lg2T0 + kLog2e * (a[6] - a[0] + c[1] + c[2] + c[3] + c[4] -
+                                                       a[5] / kT0 + cst);
             const double h = grid_head(g0);
             if (!(fabs(h) < kGridLimit)) return false;
-            // tau^m - 1 in powers of u = tau - 1 (binomial expansion about tau = 1)
-            const double e1 = c[1] + 2 * c[2] + 3 * c[3] + 4 * c[4];
-            const double e2 = c[2] + 3 * c[3] + 6 * c[4];
-            const double e3 = c[3] + 4 * c[4];
-            const double e4 = c[4];
+            const double e1 = e[1], e2 = e[2], e3 = e[3], e4 = e[4];
             float a0h, a0l, a5h, a5l;
             dsplit2(a[0], a0h, a0l);
             dsplit2(-a[5] * kLog2e, a5h, a5l);
@@ -265,6 +275,8 @@ inline bool build_tables(const chem_mech_desc *d, Tables &t)
     v.lg2R = df2c(log2(kR));
     v.lg2_pref_R = df2c(log2(d->p_ref / kR));
     v.log2e = df2c(kLog2e);
+    v.Tc[0] = (float)Tc[0];
+    v.Tc[1] = (float)Tc[1];
     // the kernel needs one warp's tables and the block's staged tables in shared memory
     if (block_fixed_bytes(v) + warp_pf_bytes(ns) + warp_om_bytes(ns) > kTSmemMax) return false;
     v.ok = false;

@@ -187,6 +187,7 @@ struct F32TView {
     double t_mid;
     // double-float (hi, lo) constants: log2 T0, 1/T0, log2 R, log2(p_ref / R), log2 e
     float2 lg2T0, invT0, lg2R, lg2_pref_R, log2e;
+    float Tc[2];                 // centre (K) of each T range's Gibbs polynomial
     bool ok;                     // the mechanism fits the kernel (else the warp-per-cell kernel)
 };
 

@@ -17,8 +17,9 @@
 // small integer stoichiometric coefficients are exact in FP32; only L carries rounding, at
 // the magnitude of L, and 2^(H + L) is taken as 2^H 2^L.  The per-cell temperature features
 // are double-float (log2 by an atanh series, 1/T with its Newton residual); the bounded
-// third-body and falloff factors use the MUFU exp2 / log2.  omega accumulates in FP32 in
-// the processing order (per-cell error ~2e-6 of max |omega| at 53/325).
+// third-body and falloff factors use the MUFU exp2 / log2; the Gibbs polynomial is expanded
+// about its T range's own centre.  omega accumulates in FP32 in the processing order
+// (per-cell error ~8e-7 of max |omega| at 53/325).
 //
 // Layout: one block of W warps per SM-sized share of the batch.  The block stages the species
 // table, the third-body lists and the falloff parameters once, and the reaction records in
@@ -546,8 +547,8 @@ k_source_f32t(F32TView v, int64_t n, const float *__restrict__ T, const float *_
     const dflt d2 = df_add(rT, df_neg(df_of(v.invT0)));                 // 1/T - 1/T0
     c.d2h = d2.h;
     c.d2l = d2.l;
-    const float u = __fmul_rn(__fsub_rn(c.Tf, 1000.0f), 1e-3f);         // T/1000 - 1
     const int rg = (double)c.Tf >= v.t_mid ? 1 : 0;
+    const float u = __fmul_rn(__fsub_rn(c.Tf, v.Tc[rg]), 1e-3f);        // (T - T_c) / 1000
     // log2 c_tot = log2(P / (R T)); log2(p_ref / (R T))
     grid_split(df_add(df_add(df_log2f(P[i], log2e), df_neg(df_of(v.lg2R))), df_neg(lT)), c.ctH, c.ctR);
     float gpH, gpR;

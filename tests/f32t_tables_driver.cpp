@@ -56,9 +56,9 @@ int main()
     const F32TView &v = t.v;
     printf("ok 1\n");
     printf("sizes %d %d %d %d\n", v.n_rec, v.n_tb, v.n_fall, (int)t.sp.size());
-    printf("const %.9g %.9g %.9g %.9g %.9g %.9g %.9g %.9g %.9g %.9g\n", v.lg2T0.x, v.lg2T0.y,
-           v.invT0.x, v.invT0.y, v.lg2R.x, v.lg2R.y, v.lg2_pref_R.x, v.lg2_pref_R.y, v.log2e.x,
-           v.log2e.y);
+    printf("const %.9g %.9g %.9g %.9g %.9g %.9g %.9g %.9g %.9g %.9g %.9g %.9g\n", v.lg2T0.x,
+           v.lg2T0.y, v.invT0.x, v.invT0.y, v.lg2R.x, v.lg2R.y, v.lg2_pref_R.x, v.lg2_pref_R.y,
+           v.log2e.x, v.log2e.y, v.Tc[0], v.Tc[1]);
     for (size_t i = 0; i < t.rx.size(); ++i) {
         const RxnT &r = t.rx[i];
         printf("rec %d %.9g %.9g %.9g %.9g %.9g %u %u %.9g", t.order[i], r.kf.x, r.kf.y, r.kf.z,
